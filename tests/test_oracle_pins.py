@@ -1,0 +1,381 @@
+"""Pins of the FP64 oracle against things other than itself.
+
+Each check is chosen so that a plausible slip in the oracle (a dropped term, a
+wrong sign, a transposed operand, the misprinted beta of App. A) makes it fail;
+``test_pins_catch_planted_mistakes`` plants such slips in copies of the oracle's
+data and asserts that the pins notice them.
+"""
+from types import SimpleNamespace
+
+import numpy as np
+import pytest
+
+import synth
+from oracle import (Tree, apg, cost_update, dense_dual_hessian, factor, jacobi_steps,
+                    lipschitz_dense, prox_box, prox_dist, solve_step, theta_sequence)
+from tests import dense_reference as dr
+
+
+def build(P):
+    tree = Tree(P["tree"]["parent"], P["tree"]["prob"])
+    fac = factor(P["net"], P["cost"])
+    cu = cost_update(fac, P["cost"], tree, P["alpha2"], P["dhat"], P["eps"], P["q"])
+    return tree, fac, cu
+
+
+def rand_w(rng, tree, fac, scale=1.0):
+    return (scale * rng.standard_normal((tree.n, fac.n_x)), scale * rng.standard_normal((tree.n, fac.n_x)),
+            scale * rng.standard_normal((tree.n, fac.n_u)))
+
+
+def relerr(a, b):
+    return np.abs(a - b).max() / (1.0 + np.abs(b).max())
+
+
+INSTANCES = [lambda: synth.tiny(0), lambda: synth.random_instance(1), lambda: synth.random_instance(2),
+             lambda: synth.custom(3, 2, 4, 2, 1, synth.make_tree([1], 6))]
+
+
+# ---------------------------------------------------------------- prox (App. C)
+def brute_prox_dist(v, P, gm):
+    """1-D brute force: the prox of gm * dist(.|C) lies on the segment [v, P(v)]."""
+    s = np.linspace(0.0, 1.0, 200001)
+    pts = v[None, :] + s[:, None] * (P - v)[None, :]
+    dist_to_C = (1.0 - s) * np.linalg.norm(P - v)            # P(pts) = P on that segment
+    obj = gm * dist_to_C + 0.5 * np.sum((pts - v[None, :]) ** 2, axis=1)
+    return pts[np.argmin(obj)]
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_prox_dist_matches_bruteforce(seed):
+    rng = np.random.default_rng(seed)
+    lo, hi = rng.uniform(-1, 0, 4), rng.uniform(0.5, 2, 4)
+    v = rng.uniform(-4, 4, 4)
+    P = prox_box(v, lo, hi)
+    for gm in (0.01, 0.5, 2.0, 50.0):
+        got = prox_dist(v[None, :], P[None, :], gm)[0]
+        ref = brute_prox_dist(v, P, gm)
+        assert np.abs(got - ref).max() < 1e-4 * (1 + np.linalg.norm(v))
+
+
+def test_prox_moreau_identity():
+    # prox_{g}(v) + prox_{g*}(v) = v with g = mu dist_C and g* = indicator of the mu-ball
+    # plus the support function of C; on the safety set the conjugate prox is the
+    # projection of v - P_C(v) onto the mu-ball when v - P_C(v) is the normal part.
+    rng = np.random.default_rng(7)
+    xs = rng.uniform(0, 1, 5)
+    for _ in range(20):
+        v = rng.uniform(-3, 3, 5)
+        P = np.maximum(v, xs)
+        mu = rng.uniform(0.1, 3)
+        t = prox_dist(v[None, :], P[None, :], mu)[0]
+        r = v - P
+        nr = np.linalg.norm(r)
+        y = r if nr <= mu else mu * r / nr                     # projection onto the mu-ball
+        assert np.abs(t + y - v).max() < 1e-12
+
+
+# ---------------------------------------------------------------- theta recursion
+def test_theta_identity_and_rate():
+    th = theta_sequence(2000)
+    for nu in range(1, len(th) - 1):
+        a, b = th[nu], th[nu + 1]
+        assert abs((1 - b) / b ** 2 - 1 / a ** 2) <= 1e-12 / a ** 2
+    nu = np.arange(1, 2001)
+    assert np.all(np.abs(th[2:] * (nu + 2) - 2) < 0.5)
+    assert abs(th[-1] * 2002 - 2) < 0.01
+
+
+# ---------------------------------------------------------------- factor and cost update (App. A, B)
+@pytest.mark.parametrize("mk", INSTANCES)
+def test_factor_identities(mk):
+    P = mk()
+    tree, fac, cu = build(P)
+    n_v = fac.n_v
+    assert np.abs(P["net"]["E"] @ fac.L).max() <= 1e-13 * max(1, np.abs(P["net"]["E"]).max())
+    assert np.abs(fac.L.T @ fac.L - np.eye(n_v)).max() < 1e-13
+    assert np.linalg.eigvalsh(fac.R_bar).min() > 0
+    assert np.abs(fac.Lam @ fac.R_bar + np.eye(n_v)).max() < 1e-10
+    assert np.abs(fac.Phi - fac.Lam @ fac.B_bar.T).max() < 1e-12 * (1 + np.abs(fac.Phi).max())
+    assert np.abs(fac.Psi - fac.Lam @ fac.L.T).max() < 1e-12 * (1 + np.abs(fac.Psi).max())
+    # u_hat satisfies the coupling at every node (eq. new:decision)
+    d = dr.demands(P)
+    assert np.abs(cu.u_hat @ P["net"]["E"].T + d @ P["net"]["Ed"].T).max() < 1e-12
+
+
+def v_form(P, tree, fac, cu, v):
+    """eq. new:stage:cost: sum p_bar v'R_bar v - 2 p v_pi' R_bar v + beta' v."""
+    val = 0.0
+    for m in range(tree.n):
+        vp = v[tree.parent[m]] if tree.parent[m] >= 0 else np.zeros(fac.n_v)
+        val += cu.p_bar[m] * v[m] @ fac.R_bar @ v[m] - 2 * tree.prob[m] * vp @ fac.R_bar @ v[m] + cu.beta[m] @ v[m]
+    return val
+
+
+def u_form(P, tree, fac, cu, v):
+    """sum p [l^w(u) + l^Delta(Delta u)] with u = L v + u_hat (eq. cost:temp, original form)."""
+    c = P["cost"]
+    u = v @ fac.L.T + cu.u_hat
+    val = 0.0
+    for m in range(tree.n):
+        up = u[tree.parent[m]] if tree.parent[m] >= 0 else P["q"]
+        du = u[m] - up
+        val += tree.prob[m] * (c["W_alpha"] * (c["alpha1"] + P["alpha2"][tree.stage[m]]) @ u[m] + du @ c["W_u"] @ du)
+    return val
+
+
+def beta_gap(P, tree, fac, cu, seed=0):
+    rng = np.random.default_rng(seed)
+    gaps = [u_form(P, tree, fac, cu, v) - v_form(P, tree, fac, cu, v)
+            for v in (rng.standard_normal((tree.n, fac.n_v)) for _ in range(4))]
+    return max(gaps) - min(gaps), max(abs(g) for g in gaps)
+
+
+@pytest.mark.parametrize("mk", INSTANCES)
+def test_beta_by_cost_expansion(mk):
+    # u-form minus v-form must not depend on v (eq. new:stage:cost expands eq. cost:delta)
+    P = mk()
+    tree, fac, cu = build(P)
+    spread, scale = beta_gap(P, tree, fac, cu)
+    assert spread < 1e-9 * (1 + scale)
+
+
+# ---------------------------------------------------------------- Algorithm 1 vs dense KKT
+@pytest.mark.parametrize("mk", INSTANCES)
+def test_solve_step_equals_dense_kkt(mk):
+    P = mk()
+    tree, fac, cu = build(P)
+    rng = np.random.default_rng(11)
+    for scale in (0.0, 1.0, 100.0):
+        w = rand_w(rng, tree, fac, scale)
+        x, u = solve_step(fac, tree, cu, *w, P["p"])
+        xr, ur = dr.kkt_solve(P, w)
+        assert relerr(x, xr) < 1e-10 and relerr(u, ur) < 1e-10
+
+
+def test_reduced_form_equals_three_term_form():
+    # delta_n = (Phi s + Psi psi + Lambda sigma)/(2p) = Lambda r_n / (2 p_n) with r_n as in Algorithm 1
+    P = synth.random_instance(5)
+    tree, fac, cu = build(P)
+    w = rand_w(np.random.default_rng(3), tree, fac)
+    _, _, inn = solve_step(fac, tree, cu, *w, P["p"], return_internals=True)
+    red = inn["r"] @ fac.Lam.T / (2 * tree.prob)[:, None]
+    assert relerr(red, inn["delta"]) < 1e-12
+
+
+@pytest.mark.parametrize("mk", INSTANCES)
+def test_invariants_dynamics_coupling_nonanticipativity(mk):
+    P = mk()
+    tree, fac, cu = build(P)
+    w = rand_w(np.random.default_rng(5), tree, fac, 10.0)
+    x, u = solve_step(fac, tree, cu, *w, P["p"])
+    net = P["net"]
+    d = dr.demands(P)
+    xpar = np.where(tree.parent[:, None] >= 0, x[np.maximum(tree.parent, 0)], P["p"][None, :])
+    dyn = x - xpar @ net["A"].T - u @ net["B"].T - d @ net["Gd"].T
+    assert np.abs(dyn).max() < 1e-12 * (1 + np.abs(x).max())
+    assert np.abs(u @ net["E"].T + d @ net["Ed"].T).max() < 1e-12 * (1 + np.abs(u).max())
+    # non-anticipativity: scenarios sharing the path to stage j share u up to stage j
+    paths = tree.scenario_paths()
+    U = [np.stack([u[m] for m in pth]) for pth in paths]
+    for a in range(len(paths)):
+        for b in range(a + 1, len(paths)):
+            k = 0
+            while k < len(paths[a]) and paths[a][k] == paths[b][k]:
+                assert np.array_equal(U[a][k], U[b][k])
+                k += 1
+
+
+def test_special_case_zero_dual_constant_uhat():
+    # w = 0, alpha = 0, constant demand at every node and q = u_hat: beta = 0, so delta = 0 and u = u_hat
+    P = synth.random_instance(6)
+    P["cost"]["alpha1"] = np.zeros_like(P["cost"]["alpha1"])
+    P["alpha2"] = np.zeros_like(P["alpha2"])
+    P["dhat"] = np.repeat(P["dhat"][:1], P["dhat"].shape[0], 0)
+    P["eps"] = np.zeros_like(P["eps"])
+    tree, fac, _ = build(P)
+    d0 = P["dhat"][0]
+    P["q"] = fac.P_u @ d0
+    cu = cost_update(fac, P["cost"], tree, P["alpha2"], P["dhat"], P["eps"], P["q"])
+    assert np.abs(cu.beta).max() < 1e-12
+    z = (np.zeros((tree.n, fac.n_x)), np.zeros((tree.n, fac.n_x)), np.zeros((tree.n, fac.n_u)))
+    x, u, inn = solve_step(fac, tree, cu, *z, P["p"], return_internals=True)
+    assert np.abs(inn["delta"]).max() < 1e-12
+    assert np.abs(u - cu.u_hat).max() < 1e-12
+
+
+def test_scalar_system_by_hand():
+    # n_x = n_u = n_v = 1, no coupling, chain of 2 nodes, p = 1: minimise
+    # w_u (u0 - q)^2 + w_u (u1 - u0)^2 + a (u0 + u1) + xi0 x0 + xi1 x1 + psi0 u0 + psi1 u1
+    # with x0 = p0 + b u0 + g d0, x1 = x0 + b u1 + g d1 (A = 1).
+    b_, g_, wu, a = 2.0, -1.0, 3.0, 0.5
+    P = {"net": {"n_x": 1, "n_u": 1, "n_d": 1, "n_e": 0, "A": np.eye(1), "B": np.array([[b_]]),
+                 "Gd": np.array([[g_]]), "E": np.zeros((0, 1)), "Ed": np.zeros((0, 1))},
+         "cost": {"W_alpha": 1.0, "alpha1": np.array([a]), "W_u": np.array([[wu]]), "W_x": 1.0, "gamma_d": 1.0},
+         "tree": {"parent": np.array([-1, 0]), "prob": np.array([1.0, 1.0]), "stage": np.array([0, 1])},
+         "alpha2": np.zeros((2, 1)), "p": np.array([1.0]), "q": np.array([0.4]),
+         "dhat": np.array([[0.3], [0.7]]), "eps": np.zeros((2, 1))}
+    tree, fac, cu = build(P)
+    xi = np.array([[0.2], [-0.1]]); psi = np.array([[0.05], [0.3]])
+    x, u = solve_step(fac, tree, cu, xi, np.zeros((2, 1)), psi, P["p"])
+    # stationarity in (u0, u1), x eliminated: hand-derived 2x2 system
+    # d/du0: 2wu(u0-q) - 2wu(u1-u0) + a + psi0 + b(xi0 + xi1) = 0
+    # d/du1: 2wu(u1-u0) + a + psi1 + b xi1 = 0
+    K = np.array([[4 * wu, -2 * wu], [-2 * wu, 2 * wu]])
+    rhs = np.array([2 * wu * 0.4 - a - psi[0, 0] - b_ * (xi[0, 0] + xi[1, 0]), -a - psi[1, 0] - b_ * xi[1, 0]])
+    uu = np.linalg.solve(K, rhs)
+    assert np.abs(u[:, 0] - uu).max() < 1e-13
+    x0 = 1.0 + b_ * uu[0] + g_ * 0.3
+    assert abs(x[0, 0] - x0) < 1e-13 and abs(x[1, 0] - (x0 + b_ * uu[1] + g_ * 0.7)) < 1e-13
+
+
+# ---------------------------------------------------------------- dual Hessian (Sec. IV-D)
+def closed_form_diagonal(fac, tree):
+    """Hand derivation for A = I: the response of x_n to xi_n sums, over ancestors a
+    of n (and n), k_a^2/(2 p_a) B_bar R_bar^{-1} B_bar' with k_a the number of path
+    nodes from a down to n; the response of u_n to psi_n sums 1/(2 p_a) L R_bar^{-1} L'."""
+    Rinv = np.linalg.inv(fac.R_bar)
+    dB = np.einsum("ij,jk,ik->i", fac.B_bar, Rinv, fac.B_bar)
+    dL = np.einsum("ij,jk,ik->i", fac.L, Rinv, fac.L)
+    cx, cu_ = np.zeros(tree.n), np.zeros(tree.n)
+    for m in range(tree.n):
+        path = tree.path(m)
+        for i, a in enumerate(path):
+            k = len(path) - i
+            cx[m] += k * k / (2 * tree.prob[a])
+            cu_[m] += 1.0 / (2 * tree.prob[a])
+    return cx[:, None] * dB[None, :], cu_[:, None] * dL[None, :]
+
+
+@pytest.mark.parametrize("mk", INSTANCES[:3])
+def test_dense_dual_hessian(mk):
+    P = mk()
+    tree, fac, cu = build(P)
+    M = dense_dual_hessian(fac, tree)
+    assert np.abs(M - M.T).max() < 1e-10 * np.abs(M).max()
+    assert np.linalg.eigvalsh(0.5 * (M + M.T)).min() > -1e-9 * np.abs(M).max()
+    dx, du = closed_form_diagonal(fac, tree)
+    blk = 2 * fac.n_x + fac.n_u
+    dg = np.diag(M).reshape(tree.n, blk)
+    assert relerr(dg[:, :fac.n_x], dx) < 1e-12
+    assert relerr(dg[:, fac.n_x:2 * fac.n_x], dx) < 1e-12
+    assert relerr(dg[:, 2 * fac.n_x:], du) < 1e-12
+    # the Hessian is the linear part of w -> -H z(w), also available from the dense KKT
+    rng = np.random.default_rng(2)
+    w = rand_w(rng, tree, fac)
+    x0, u0 = dr.kkt_solve(P, tuple(np.zeros_like(a) for a in w))
+    x1, u1 = dr.kkt_solve(P, w)
+    Mw = M @ np.concatenate([w[0], w[1], w[2]], axis=1).ravel()
+    ref = -np.concatenate([x1 - x0, x1 - x0, u1 - u0], axis=1).ravel()
+    assert relerr(Mw, ref) < 1e-9
+
+
+# ---------------------------------------------------------------- converged APG
+def micro_instance(seed):
+    return synth.custom(seed, n_x=1, n_u=2, n_d=1, n_e=1, tree=synth.make_tree([2], 2),
+                        weights=(1.0, 1.0, 4.0, 20.0))
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_apg_converges_to_bruteforce_optimum(seed):
+    P = micro_instance(seed)
+    # push the states against their bounds so several pieces are active
+    P["p"] = np.array([2.0 + seed])
+    tree, fac, cu = build(P)
+    best = dr.active_set_bruteforce(P)
+    assert best is not None
+    steps = jacobi_steps(fac, tree)
+    R = apg(fac, tree, cu, P["cost"], P["p"], steps, 20000)
+    assert np.abs(R.u - best[2]).max() < 1e-6 * (1 + np.abs(best[2]).max())
+    assert np.abs(R.x - best[1]).max() < 1e-6 * (1 + np.abs(best[1]).max())
+    assert abs(dr.objective(P, R.x, R.u) - best[0]) < 1e-7 * (1 + abs(best[0]))
+
+
+def test_apg_optimality_certificate_tiny():
+    """Converged APG output satisfies the optimality conditions of the problem:
+    z = argmin f + <Hz, y> (dense KKT) and y in the subdifferential of g at Hz."""
+    P = synth.tiny(0)
+    tree, fac, cu = build(P)
+    steps = jacobi_steps(fac, tree)
+    R = apg(fac, tree, cu, P["cost"], P["p"], steps, 6000)
+    assert R.rho_rel[-1] < 1e-5
+    c = P["cost"]
+    y_s, y_z, y_p = R.y
+    x, u = R.x, R.u
+    xr, ur = dr.kkt_solve(P, R.y)
+    assert relerr(x, xr) < 1e-4 and relerr(u, ur) < 1e-4
+    tol = 1e-4
+    ysc = 1 + np.abs(y_p).max()
+    for m in range(tree.n):
+        for i in range(fac.n_u):
+            if y_p[m, i] > tol * ysc:
+                assert u[m, i] > c["u_max"][i] - 1e-3
+            if y_p[m, i] < -tol * ysc:
+                assert u[m, i] < c["u_min"][i] + 1e-3
+        for yb, lo, hi, mu in ((y_s[m], c["x_s"], np.full(fac.n_x, np.inf), tree.prob[m] * c["W_x"]),
+                               (y_z[m], c["x_min"], c["x_max"], c["gamma_d"])):
+            r = x[m] - np.clip(x[m], lo, hi)
+            assert np.linalg.norm(yb) <= mu * (1 + 1e-6) + 1e-9
+            if np.linalg.norm(r) > 1e-3:
+                assert np.abs(yb - mu * r / np.linalg.norm(r)).max() < 1e-3 * mu
+            else:          # normal cone of C at x: zero on strictly inactive entries, outward sign elsewhere
+                inner = (x[m] > lo + 1e-3) & (x[m] < hi - 1e-3)
+                assert np.abs(yb[inner]).max(initial=0.0) < 1e-3 * mu
+                assert np.all(yb[x[m] <= lo + 1e-3] <= 1e-3 * mu)
+                assert np.all(yb[x[m] >= hi - 1e-3] >= -1e-3 * mu)
+
+
+def test_jacobi_lipschitz_bounds_step():
+    P = synth.tiny(0)
+    tree, fac, cu = build(P)
+    M = dense_dual_hessian(fac, tree)
+    L = lipschitz_dense(M)
+    v = np.random.default_rng(0).standard_normal(M.shape[0])
+    assert v @ M @ v <= L * (v @ v) * (1 + 1e-12)
+    st = jacobi_steps(fac, tree, M)
+    assert st["lambda"] > 0
+
+
+# ---------------------------------------------------------------- the pins notice planted mistakes
+def test_pins_catch_planted_mistakes():
+    P = synth.random_instance(2)         # branching tree: probabilities below one
+    tree, fac, cu = build(P)
+    w = rand_w(np.random.default_rng(9), tree, fac, 3.0)
+    xr, ur = dr.kkt_solve(P, w)
+
+    def kkt_err(f, c):
+        x, u = solve_step(f, tree, c, *w, P["p"])
+        return max(relerr(x, xr), relerr(u, ur))
+
+    assert kkt_err(fac, cu) < 1e-10
+    # printed eq. appendix:beta: extra p_n on the R_hat term and no p_n on u_hat_pi
+    d = dr.demands(P)
+    u_hat = cu.u_hat
+    u_par = np.vstack([P["q"][None, :], u_hat[tree.parent[1:]]])
+    child = np.zeros_like(u_hat)
+    for m in range(1, tree.n):
+        child[tree.parent[m]] += tree.prob[m] * u_hat[m]
+    p = tree.prob[:, None]
+    printed = p * cu.alpha_bar[tree.stage] + 2 * p * ((cu.p_bar[:, None] * u_hat - u_par - child) @ fac.R_hat)
+    assert kkt_err(fac, SimpleNamespace(**{**vars(cu), "beta": printed})) > 1e-6
+    assert beta_gap(P, tree, fac, SimpleNamespace(**{**vars(cu), "beta": printed}))[0] > 1e-6
+    # sign of Lambda flipped
+    bad = SimpleNamespace(**{**vars(fac), "Lam": -fac.Lam})
+    assert kkt_err(bad, cu) > 1e-6
+    # the Psi term dropped
+    bad = SimpleNamespace(**{**vars(fac), "Psi": 0 * fac.Psi})
+    assert kkt_err(bad, cu) > 1e-6
+    # u_{-1} = q forgotten (u_hat_pi(root) = 0)
+    cu0 = cost_update(fac, P["cost"], tree, P["alpha2"], P["dhat"], P["eps"], 0 * P["q"])
+    assert kkt_err(fac, cu0) > 1e-6
+    # e without the demand term
+    bad = SimpleNamespace(**{**vars(cu), "e": u_hat @ P["net"]["B"].T})
+    assert kkt_err(fac, bad) > 1e-6
+    # prox without the gamma*mu factor in the far branch fails the brute-force prox
+    v = np.array([3.0, -2.0, 0.5]); Pv = np.maximum(v, 1.0); gm = 0.7
+    far = v + (Pv - v) / np.linalg.norm(Pv - v)
+    assert np.abs(far - brute_prox_dist(v, Pv, gm)).max() > 1e-3
+    # theta with the wrong sign fails the identity
+    a = 0.5
+    b = 0.5 * (np.sqrt(a ** 4 + 4 * a ** 2) + a ** 2)
+    assert abs((1 - b) / b ** 2 - 1 / a ** 2) > 1e-3
