@@ -1,0 +1,452 @@
+"""Benchmark: SMPC solves/s to a 1e-3 relative primal-dual residual on the
+Barcelona-shaped synthetic network (n_x = 63, n_u = 114, n_d = 88, n_e = 17,
+horizon 24, branching [5, 5, 2, 2] -> 100 scenarios, 2081 nodes).
+
+One step = one SMPC solve: cost update on the device, then APG iterations until
+rho_rel <= 1e-3 (or the cap), cold start y^0 = 0, on one MPC step's synthetic
+inputs (state, forecast, prices differ from step to step).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line (rank 0).  Under torchrun every rank solves its own copy of
+the workload (replicas: scaling "weak"); the timed region is bracketed by a
+barrier and a device synchronize on both sides and the max time over ranks is used.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "SMPC solves/sec and ms per solve to 1e-3 primal-dual residual; APG iters/s; p50/p99"
+WORKLOAD = "Barcelona-shaped single tree: n_x=63, n_u=114, n_d=88, n_e=17, N=24, branching [5,5,2,2] -> 100 scenarios, 2081 nodes"
+PREC_NAMES = {0: "f64", 1: "f32", 2: "bf16"}
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        d = json.load(open(path))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+# Measured on a GB300 of this machine with a chain-of-FMA microbenchmark (152 SMs x 8
+# blocks x 256 threads, 8 independent chains per thread): float64 FMA throughput.
+FP64_FMA_TFLOPS = 1.157
+
+
+# --------------------------------------------------------------------- workload
+def make_problem(config, seed=0):
+    import synth
+    if config == "tiny":
+        return synth.tiny(seed)
+    if config == "large":
+        return synth.large(seed)
+    return synth.barcelona(seed)
+
+
+def step_inputs(P, k):
+    """Inputs of MPC step k: forecast and prices shifted by k hours, state perturbed."""
+    import synth
+    from synth.problems import day_night_price
+    N = P["tree"]["horizon"]
+    net = P["net"]
+    dhat = synth.demand_forecast(net, N, t0=k)
+    price = day_night_price(N, t0=k)
+    base = P["alpha2"] / np.maximum(day_night_price(N, 0)[:, None], 1e-300)
+    alpha2 = price[:, None] * base
+    rng = np.random.default_rng(1000 + k)
+    p = P["p"] * (1.0 + 0.02 * rng.standard_normal(P["p"].shape))
+    return {"p": p, "q": P["q"], "dhat": dhat, "alpha2": alpha2}
+
+
+def algorithmic_bytes_per_iteration(n, n_x, n_u, n_v, prec):
+    """Bytes one APG iteration must move: every pack entry once, plus the node vectors."""
+    ms = {0: 8, 1: 4, 2: 2}[prec]
+    vs = 8 if prec == 0 else 4
+    n_k = n_x + n_u
+    nd = 2 * n_x + n_u
+    mat = n_k * n_v + n_v * n_v
+    # forward+prox reads h, e, u_hat, y^nu-1, y^nu-2, steps (n_u + 2), mu; writes u, x, y^nu, w
+    # backward reads w, beta; writes h
+    vec_r = n_k + n_x + n_u + 2 * nd + n_u + 3 + n_k + n_v
+    vec_w = n_k + nd + n_k + n_k
+    return n * (mat * ms + (vec_r + vec_w) * vs), n * mat, n * 2 * (n_k * n_v + n_v * n_v + n_k * n_v)
+
+
+# --------------------------------------------------------------------- CPU oracle leg
+def oracle_sample(config, iters):
+    """Times the FP64 oracle (as it stands) for `iters` APG iterations; JSON to stdout."""
+    import oracle
+    P = make_problem(config)
+    tree = oracle.Tree(P["tree"]["parent"], P["tree"]["prob"])
+    fac = oracle.factor(P["net"], P["cost"])
+    cu = oracle.cost_update(fac, P["cost"], tree, P["alpha2"], P["dhat"], P["eps"], P["q"])
+    oracle.apg(fac, tree, cu, P["cost"], P["p"], 1e-9, 2)   # warm caches
+    t0 = time.perf_counter()
+    oracle.apg(fac, tree, cu, P["cost"], P["p"], 1e-9, iters)
+    dt = time.perf_counter() - t0
+    print(json.dumps({"ms_per_iter": 1e3 * dt / iters, "iters": iters, "seconds": dt}))
+
+
+def run_oracle_sample(config, iters, threads=1):
+    env = dict(os.environ)
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "NUMEXPR_NUM_THREADS"):
+        env[k] = str(threads)
+    env["CUDA_VISIBLE_DEVICES"] = ""
+    r = subprocess.run([sys.executable, os.path.abspath(__file__), "--oracle-sample", str(iters), "--config", config],
+                       capture_output=True, text=True, env=env, cwd=ROOT, timeout=600)
+    if r.returncode != 0:
+        raise RuntimeError(r.stderr[-2000:])
+    return json.loads(r.stdout.strip().splitlines()[-1])
+
+
+def oracle_iters_to_tol(config):
+    path = os.path.join(ROOT, "tests", "golden", "oracle_iters_to_tol.json")
+    if os.path.exists(path):
+        d = json.load(open(path))
+        if config in d:
+            return int(d[config]["iterations"]), d[config]
+    return None, None
+
+
+def cpu_baseline(config, iters_to_tol, budget_iters=None):
+    probe = run_oracle_sample(config, 3)
+    n = budget_iters or max(5, min(2000, int(15000.0 / max(probe["ms_per_iter"], 1e-3))))
+    s = run_oracle_sample(config, n)
+    ms_solve = s["ms_per_iter"] * iters_to_tol
+    return {"value": 1000.0 / ms_solve, "unit": "solves/s", "cores": 1, "kind": "oracle",
+            "sample": f"{n} FP64 APG iterations of the same workload timed ({s['seconds']:.1f} s), "
+                      f"scaled to {iters_to_tol} iterations per solve",
+            "ms_per_iter": s["ms_per_iter"], "iters_per_s": 1000.0 / s["ms_per_iter"]}
+
+
+# --------------------------------------------------------------------- clocks
+class ClockSampler:
+    def __init__(self, out_path):
+        self.path = out_path
+        self.proc = None
+
+    def __enter__(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.f = open(self.path, "w")
+            dev = os.environ.get("LOCAL_RANK", "0")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", dev, f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                                          "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        try:
+            rows = [r.split(",") for r in open(self.path).read().strip().splitlines() if r.strip()]
+        except Exception:
+            rows = []
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                mx = max(mx, float(r[2]))
+                for i, nm in enumerate(names):
+                    if r[5 + i].strip().lower() == "active":
+                        reasons.add(nm)
+            except Exception:
+                continue
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx or None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# --------------------------------------------------------------------- distributed helpers
+def dist_env():
+    return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("LOCAL_RANK", "0"))
+
+
+def aggregate(local_units, local_seconds, backend_device=None):
+    """Whole-job throughput: units summed over ranks / max time over ranks."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return local_units, local_seconds
+    dev = backend_device or torch.device("cpu")
+    t = torch.tensor([float(local_seconds)], dtype=torch.float64, device=dev)
+    u = torch.tensor([float(local_units)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(u.item()), float(t.item())
+
+
+# --------------------------------------------------------------------- our arm
+class Solver:
+    def __init__(self, P, precision, device):
+        import torch
+
+        import paper_1604_01074_gb300 as smpc
+        self.smpc, self.torch, self.P = smpc, torch, P
+        t, net = P["tree"], P["net"]
+        self.n, self.n_x, self.n_u = len(t["parent"]), net["n_x"], net["n_u"]
+        self.tree = smpc.smpc_tree_create(t["parent"], t["prob"])
+        self.info = smpc.smpc_tree_info_get(self.tree)
+        self.fac = smpc.smpc_factor(self.tree, net, P["cost"], precision=precision, precondition=1)
+        dt = torch.float64 if precision == 0 else torch.float32
+        self.u = torch.empty((self.n, self.n_u), dtype=dt, device=device)
+        self.x = torch.empty((self.n, self.n_x), dtype=dt, device=device)
+        self.eps_dev = torch.from_numpy(np.ascontiguousarray(P["eps"])).to(device)
+        self.device = device
+
+    def device_inputs(self, inp):
+        T = self.torch
+        return {k: T.from_numpy(np.ascontiguousarray(v, dtype=np.float64)).to(self.device) for k, v in inp.items()}
+
+    def pinned_inputs(self, inp):
+        T = self.torch
+        return {k: T.from_numpy(np.ascontiguousarray(v, dtype=np.float64)).pin_memory() for k, v in inp.items()}
+
+    def solve(self, inp, max_iters, tol, stream, eps=True, sync=0, u0=None):
+        ptr = lambda t: t.data_ptr() if hasattr(t, "data_ptr") else t  # noqa: E731
+        return self._raw_solve(ptr(inp["p"]), ptr(inp["q"]), ptr(inp["dhat"]), ptr(inp["alpha2"]),
+                               self.eps_dev.data_ptr() if eps else None, max_iters, tol, stream, sync, u0)
+
+    def _raw_solve(self, p, q, dhat, alpha2, eps, max_iters, tol, stream, sync, u0):
+        import ctypes
+        smpc = self.smpc
+        dp = ctypes.POINTER(ctypes.c_double)
+        cast = lambda a: None if a is None else ctypes.cast(ctypes.c_void_p(a), dp)  # noqa: E731
+        D = smpc.smpc_step_data(cast(p), cast(q), cast(dhat), cast(eps), cast(alpha2))
+        O = smpc.smpc_solve_opts(int(max_iters), float(tol), 0, 64, int(sync))
+        R = smpc.smpc_result(self.u.data_ptr(), self.x.data_ptr(), None,
+                             None if u0 is None else u0.ctypes.data_as(dp), None, -1, 0.0, 0.0, 0)
+        smpc._check(smpc.lib().smpc_solve(self.fac, ctypes.byref(D), ctypes.byref(O), ctypes.byref(R),
+                                          stream.cuda_stream), "smpc_solve")
+        return {"iterations": R.iterations, "rho_rel": R.rho_rel, "launches": R.launches}
+
+    def finish(self):
+        return self.smpc.smpc_solve_info(self.fac)
+
+    def close(self):
+        self.smpc.smpc_factor_destroy(self.fac)
+        self.smpc.smpc_tree_destroy(self.tree)
+
+
+def time_per_iteration(S, inp, stream, lo=100, hi=400, reps=3):
+    """Average duration of one iteration launch: events around fixed-length solves
+    (tol = 0) of two lengths; the difference removes the per-solve fixed cost."""
+    torch = S.torch
+    out = {}
+    for iters in (lo, hi):
+        ts = []
+        for _ in range(reps):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            S.solve(inp, iters, 0.0, stream)
+            e1.record(stream)
+            e1.synchronize()
+            S.finish()
+            ts.append(e0.elapsed_time(e1))
+        out[iters] = statistics.median(ts)
+    return (out[hi] - out[lo]) / (hi - lo)
+
+
+def run_ours(args, rank, world, local_rank):
+    import torch
+    import torch.distributed as dist
+    device = torch.device("cuda", local_rank)
+    torch.cuda.set_device(device)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=device)
+    prec = {"fp64": 0, "fp32": 1, "bf16": 2}[args.precision]
+    P = make_problem(args.config, seed=0)
+    S = Solver(P, prec, device)
+    stream = torch.cuda.current_stream(device)
+    n_steps = args.steps + args.warmup
+    inputs = [step_inputs(P, k) for k in range(n_steps)]
+    dev_in = [S.device_inputs(i) for i in inputs]
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=device)  # 256 MB > L2
+
+    # warm-up solves (untimed)
+    for k in range(args.warmup):
+        S.solve(dev_in[k], args.max_iters, args.tol, stream)
+        S.finish()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    times, iters, launches = [], [], 0
+    clk = ClockSampler(os.path.join(ROOT, "gpurun_out" if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else "_work",
+                                    f"clocks_rank{rank}.csv"))
+    with clk:
+        for k in range(args.warmup, n_steps):
+            flush.fill_(float(k))
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            r = S.solve(dev_in[k], args.max_iters, args.tol, stream)
+            e1.record(stream)
+            info = S.finish()
+            times.append(e0.elapsed_time(e1))
+            iters.append(info["iterations"])
+            launches += info["launches"]
+        torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    local_s = sum(times) / 1000.0
+    units, secs = aggregate(args.steps, local_s, device if world > 1 else None)
+    value = units / secs
+    ms_per_step = 1000.0 * local_s / args.steps
+    clocks = clk.summary()
+
+    # kernel roofline: one iteration launch, differential timing
+    t_iter_ms = time_per_iteration(S, dev_in[0], stream)
+    nbytes, mat_entries, flops = algorithmic_bytes_per_iteration(S.n, S.n_x, S.n_u, S.n_x + S.n_u - S.n_x - 17, prec)
+    # n_v from the network: n_u - rank(E)
+    n_v = S.n_u - np.linalg.matrix_rank(P["net"]["E"])
+    nbytes, mat_entries, flops = algorithmic_bytes_per_iteration(S.n, S.n_x, S.n_u, n_v, prec)
+    hbm, src = peaks()
+    if prec == 0:
+        achieved = flops / (t_iter_ms * 1e-3) / 1e12
+        roof = {"bound": "alu", "achieved": achieved, "peak": FP64_FMA_TFLOPS, "unit": "TFLOP/s",
+                "frac": achieved / FP64_FMA_TFLOPS, "traffic": None,
+                "peak_source": "measured FP64 FMA microbenchmark on this pool's GB300"}
+    else:
+        achieved = nbytes / (t_iter_ms * 1e-3) / 1e9
+        roof = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+                "traffic": None, "peak_source": f"{src} hbm_gbs"}
+    roof.update({"kernel": "apg_iter", "us_per_launch": 1000.0 * t_iter_ms, "bytes_per_launch": nbytes})
+
+    # end-to-end: host (pinned) inputs, device->host read of u_0 and the residual, wall clock
+    pin_in = [S.pinned_inputs(i) for i in inputs]
+    u0 = np.zeros(S.n_u)
+    torch.cuda.synchronize()
+    e2e_t = []
+    for k in range(args.warmup, n_steps):
+        flush.fill_(float(k))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        S.solve(pin_in[k], args.max_iters, args.tol, stream, sync=1, u0=u0)
+        e2e_t.append(time.perf_counter() - t0)
+    e2e_units, e2e_secs = aggregate(args.steps, sum(e2e_t), device if world > 1 else None)
+    h2d = sum(int(np.asarray(v).nbytes) for v in inputs[0].values())
+    d2h = 8 * S.n_u + 8 + 24
+
+    result = {
+        "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": PREC_NAMES[prec], "data": "synthetic",
+        "config": {"workload": WORKLOAD if args.config == "barcelona" else args.config, "solve": "cold start, tol 1e-3 on "
+                   "rho_rel", "tol": args.tol, "max_iters": args.max_iters, "precision": args.precision,
+                   "l2": "256 MB buffer written between timed solves (L2 flushed)", "parallelism": f"replicas x{world}"},
+        "iterations_mean": float(np.mean(iters)), "apg_iters_per_s": float(np.sum(iters)) / local_s * world,
+        "p50_ms": float(np.percentile(times, 50)), "p99_ms": float(np.percentile(times, 99)),
+        "roofline": roof, "clocks": clocks, "gpu_launches": launches,
+        "e2e": {"value": e2e_units / e2e_secs, "unit": "solves/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "tree": S.info,
+    }
+    S.close()
+    if args.fp64_leg and prec != 0 and rank == 0:
+        S64 = Solver(P, 0, device)
+        t64 = time_per_iteration(S64, dev_in[0], stream, lo=20, hi=60, reps=2)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        S64.solve(dev_in[0], args.max_iters, args.tol, stream)
+        e1.record(stream)
+        inf64 = S64.finish()
+        ms64 = e0.elapsed_time(e1)
+        _, _, fl = algorithmic_bytes_per_iteration(S64.n, S64.n_x, S64.n_u, n_v, 0)
+        result["fp64"] = {"solves_per_s": 1000.0 / ms64, "ms_per_solve": ms64, "iterations": inf64["iterations"],
+                          "us_per_iteration": 1000.0 * t64,
+                          "roofline": {"bound": "alu", "achieved": fl / (t64 * 1e-3) / 1e12, "peak": FP64_FMA_TFLOPS,
+                                       "unit": "TFLOP/s", "frac": fl / (t64 * 1e-3) / 1e12 / FP64_FMA_TFLOPS}}
+        S64.close()
+    if rank == 0 and not args.no_cpu_baseline:
+        it_ref = result["fp64"]["iterations"] if "fp64" in result else int(np.mean(iters))
+        stored, _ = oracle_iters_to_tol(args.config)
+        try:
+            result["cpu_baseline"] = cpu_baseline(args.config, stored or it_ref)
+        except Exception as exc:  # noqa: BLE001
+            result["cpu_baseline"] = {"error": str(exc)[-300:]}
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    return result
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return None
+    stored, meta = oracle_iters_to_tol(args.config)
+    iters_to_tol = stored
+    if iters_to_tol is None:
+        return {"impl": "reference", "unavailable": "no stored oracle iteration count for this workload"}
+    probe = run_oracle_sample(args.config, 3)
+    per = max(3, min(400, int(8000.0 / max(probe["ms_per_iter"], 1e-3))))  # ~8 s of CPU work per step
+    for _ in range(args.warmup):
+        run_oracle_sample(args.config, max(2, per // 10))
+    samples = [run_oracle_sample(args.config, per) for _ in range(args.steps)]
+    ms_iter = statistics.mean(s["ms_per_iter"] for s in samples)
+    ms_solve = ms_iter * iters_to_tol
+    value = 1000.0 / ms_solve
+    sample = f"{per} FP64 APG iterations per step, scaled to {iters_to_tol} iterations per solve (oracle's own count)"
+    return {"impl": "reference", "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_solve, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD if args.config == "barcelona" else args.config, "tol": args.tol,
+                       "implementation": "FP64 CPU oracle (numpy), single thread"},
+            "apg_iters_per_s": 1000.0 / ms_iter,
+            "cpu_baseline": {"value": value, "unit": "solves/s", "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--precision", choices=["fp64", "fp32", "bf16"], default="fp32")
+    ap.add_argument("--config", choices=["barcelona", "tiny", "large"], default="barcelona")
+    ap.add_argument("--tol", type=float, default=1e-3)
+    ap.add_argument("--max-iters", type=int, default=100000)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp64-leg", dest="fp64_leg", action="store_false")
+    ap.add_argument("--oracle-sample", type=int, default=0)
+    args = ap.parse_args()
+    if args.oracle_sample:
+        oracle_sample(args.config, args.oracle_sample)
+        return
+    rank, world, local_rank = dist_env()
+    if args.impl == "reference":
+        res = run_reference(args, rank, world)
+    else:
+        res = run_ours(args, rank, world, local_rank)
+    if rank == 0 and res is not None:
+        print(json.dumps(res))
+
+
+if __name__ == "__main__":
+    main()

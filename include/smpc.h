@@ -1,0 +1,190 @@
+/*
+ * smpc.h - C ABI of a GB300 (sm_103a) solver for scenario-tree stochastic MPC of
+ * drinking-water networks by the accelerated dual proximal gradient method
+ * (Sampathirao, Sopasakis, Bemporad, Patrinos, "GPU-accelerated stochastic
+ * predictive control of drinking water networks").
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ * - Matrices are dense, row-major, float64, in host memory unless stated.
+ * - A scenario tree (Sec. III-C) has n_nodes nodes in breadth-first order grouped
+ *   by stage: parent[0] = -1 is the root (stage 0); every other node's parent has a
+ *   smaller index and sits one stage up; the parents of the nodes of one stage are
+ *   non-decreasing, so the children of a node are contiguous; all leaves are at the
+ *   last stage N-1, where N (the horizon) is one more than the deepest stage.
+ * - Node n at stage j holds the input u_n = u_j, the demand d_n = d_j and the
+ *   state x_n = x_{j+1} of its branch; its dual block is
+ *   y_n = (vsigma_n, zeta_n, psi_n) of length 2 n_x + n_u (Sec. IV-A); this is the
+ *   layout that reproduces the variable counts of Table 1.
+ * - Device vectors use the "vector type" of a factor: float64 when the factor's
+ *   precision is SMPC_FP64, float32 for SMPC_FP32 and SMPC_BF16.
+ * - Every call returns an smpc_status; none throws.  On failure the message of
+ *   the calling thread's last error is available from smpc_last_error().
+ * - Objects are owned by the library and released by the matching *_destroy.
+ *   Device memory is allocated by the library with cudaMalloc on the device that
+ *   is current when the object is created; all later calls on the object must be
+ *   made with that device current.
+ */
+#ifndef SMPC_H
+#define SMPC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum smpc_status {
+  SMPC_OK = 0,
+  SMPC_EINVAL = 1,    /* bad argument: sizes, tree shape, probabilities, NaN, ... */
+  SMPC_ENOMEM = 2,    /* host or device allocation failed */
+  SMPC_ECUDA = 3,     /* a CUDA runtime call failed (includes "no device") */
+  SMPC_EBUSY = 4,     /* server: the request can never fit the memory budget or slots */
+  SMPC_ETIMEOUT = 5,  /* a bounded device wait gave up; results are not valid */
+  SMPC_EDIVERGED = 6, /* non-finite values in the iterates (e.g. infeasible coupling) */
+  SMPC_ENOTSUP = 7    /* valid request outside what this build implements (A != I) */
+} smpc_status;
+
+typedef enum smpc_precision {
+  SMPC_FP64 = 0, /* per-node matrices and vectors in float64 */
+  SMPC_FP32 = 1, /* per-node matrices and vectors in float32, float32 accumulation */
+  SMPC_BF16 = 2  /* per-node matrices in bfloat16, vectors and accumulation float32 */
+} smpc_precision;
+
+typedef struct smpc_tree smpc_tree;
+typedef struct smpc_factor_t smpc_factor_t;
+
+/* Flow-based network model x+ = A x + B u + G_d d, 0 = E u + E_d d (Sec. II-A,
+ * eqs. model and demand-control).  A may be NULL for the identity (tank mass
+ * balance); this build's GPU solve step requires A = I and returns SMPC_ENOTSUP
+ * otherwise.  E and Ed may be NULL when n_e = 0.  E must have full row rank. */
+typedef struct smpc_network {
+  int32_t n_x, n_u, n_d, n_e;
+  const double* A;  /* n_x * n_x or NULL (identity) */
+  const double* B;  /* n_x * n_u */
+  const double* Gd; /* n_x * n_d */
+  const double* E;  /* n_e * n_u */
+  const double* Ed; /* n_e * n_d */
+} smpc_network;
+
+/* Costs and bounds (Sec. III-A, eqs. cost:linear, cost:smooth, cost:non-smooth;
+ * soft state box of eq. cost:distance; input box of eq. Sc-MPC).
+ * The safety penalty of node n is mu_S,n dist(x_n | {x >= x_s}) with
+ * mu_S,n = p_n W_x (l^S sits inside the expectation of eq. Sc-MPC) unless
+ * safety_unweighted = 1, which uses mu_S,n = W_x as printed in eq. gzeta. */
+typedef struct smpc_cost {
+  double W_alpha;         /* economic scaling W_alpha */
+  const double* alpha1;   /* n_u production cost alpha_1 */
+  const double* W_u;      /* n_u * n_u symmetric positive definite smoothing weight */
+  double W_x;             /* safety weight */
+  double gamma_d;         /* soft state-box weight */
+  const double* x_min;    /* n_x */
+  const double* x_max;    /* n_x */
+  const double* x_s;      /* n_x safety level */
+  const double* u_min;    /* n_u */
+  const double* u_max;    /* n_u */
+  int32_t safety_unweighted;
+} smpc_cost;
+
+typedef struct smpc_factor_opts {
+  int32_t precision;      /* smpc_precision of the per-node matrix packs */
+  int32_t precondition;   /* 1: Jacobi diagonal scaling of the dual (Sec. IV-D); 0: none */
+  double lambda;          /* > 0: use this step; 0: estimate 1/L by power iteration */
+  int32_t power_iters;    /* power iterations for the estimate (0: default 200) */
+  double lambda_margin;   /* estimate is divided by (1 + margin) (0: default 0.02) */
+  /* Explicit per-entry steps (all three or none; host float64).  When given they
+   * replace lambda and the preconditioner: step_s[n], step_z[n] are the steps of
+   * node n's two distance blocks, step_p[n*n_u + i] of its input entries. */
+  const double* step_s;
+  const double* step_z;
+  const double* step_p;
+} smpc_factor_opts;
+
+/* Per-solve data (Alg. 2, steps 1-2).  float64; each pointer may address host or
+ * device memory (unified addressing decides the copy direction). */
+typedef struct smpc_step_data {
+  const double* p;      /* n_x measured state x_0 */
+  const double* q;      /* n_u previous input u_{-1} */
+  const double* dhat;   /* N * n_d nominal forecast of stage j (eq. demand:tree) */
+  const double* eps;    /* n_nodes * n_d forecast errors of the nodes, or NULL to
+                           keep those uploaded by the previous solve (zero at first) */
+  const double* alpha2; /* N * n_u time-varying price of stage j */
+} smpc_step_data;
+
+typedef struct smpc_solve_opts {
+  int32_t max_iters;    /* iteration cap (> 0) */
+  double tol;           /* stop at the first iterate with rho_rel <= tol (0: run max_iters) */
+  int32_t warm_start;   /* 1: start from the duals the previous solve left on the device */
+  int32_t check_every;  /* host polls the stop flag every this many iterations (0: 128) */
+  int32_t sync;         /* 1: wait for the stream, fill the host outputs, check errors */
+} smpc_solve_opts;
+
+/* Outputs.  Device pointers may be NULL (not copied).  Host outputs are filled
+ * only when opts->sync = 1. */
+typedef struct smpc_result {
+  void* u;              /* device, n_nodes * n_u of the vector type: last z^nu inputs */
+  void* x;              /* device, n_nodes * n_x: last z^nu states */
+  void* y;              /* device, n_nodes * (2 n_x + n_u): final dual y^{nu+1} */
+  double* u0_host;      /* host, n_u: the root input u_0 (the move applied, Alg. 2 step 4) */
+  double* history_host; /* host, max_iters * 3: per iteration (rho, ||Hz||_inf, ||t||_inf) */
+  int32_t iterations;   /* out: iterations run */
+  double rho;           /* out: ||H z - t||_inf of the last iterate (Sec. IV-E) */
+  double rho_rel;       /* out: rho / (1 + max(||H z||_inf, ||t||_inf)) */
+  int32_t launches;     /* out: kernel launches the solve enqueued (set on return) */
+} smpc_result;
+
+typedef struct smpc_tree_info {
+  int32_t n_nodes, horizon, n_leaves, n_chains, n_top, max_chain_len;
+} smpc_tree_info;
+
+/* Validate a scenario tree (Sec. III-C) and upload it.  prob[n] is p_n, the
+ * probability of reaching node n; children's probabilities must add up to the
+ * parent's (relative 1e-12) and the root's must be 1.  prob = NULL means
+ * equiprobable scenarios.  Inputs are copied.
+ * Errors: SMPC_EINVAL (shape, order, probabilities), SMPC_ECUDA, SMPC_ENOMEM. */
+int smpc_tree_create(int32_t n_nodes, const int32_t* parent, const double* prob, smpc_tree** out);
+int smpc_tree_info_get(const smpc_tree* tree, smpc_tree_info* info);
+void smpc_tree_destroy(smpc_tree* tree);
+
+/* Offline factor step (App. A and App. B; Alg. 2 lines 1-2), in float64 on the
+ * host: L = orthonormal basis of null(E), B_bar = B L, R_hat = W_u L,
+ * R_bar = L' R_hat, Cholesky of R_bar, Lambda = -R_bar^{-1}; then per-node packs
+ * [B_bar; L] (n_x + n_u) x n_v and Lambda / (2 p_n) (n_v x n_v, Alg. 1's
+ * node-indexed factor matrices) in the requested precision on the device, the
+ * Jacobi scaling (Sec. IV-D) and the step lambda = 1/L_{H_D} (power iteration
+ * on the device, unless given).  The tree must outlive the factor.
+ * Errors: SMPC_EINVAL (sizes, NaN, E rank deficient, W_u not SPD),
+ *         SMPC_ENOTSUP (A != I), SMPC_ENOMEM, SMPC_ECUDA. */
+int smpc_factor(const smpc_tree* tree, const smpc_network* net, const smpc_cost* cost,
+                const smpc_factor_opts* opts, smpc_factor_t** out);
+void smpc_factor_destroy(smpc_factor_t* fac);
+/* The steps in use: lambda (the scalar of Sec. IV-D; 0 when explicit steps were
+ * given) and, when the pointers are not NULL, the per-entry steps (host float64,
+ * shapes as in smpc_factor_opts). */
+int smpc_factor_steps(const smpc_factor_t* fac, double* lambda, double* step_s, double* step_z,
+                      double* step_p);
+
+/* One SMPC solve (Alg. 2 step 3): the cost update of App. A on the device from
+ * the step data, then APG iterations (eq. apg-iteration) with Algorithm 1 as the
+ * solve step and the prox of App. C, until rho_rel <= tol or max_iters.
+ * Stream-ordered on `stream` (a cudaStream_t; NULL = legacy default stream).
+ * Calls on the same factor must not overlap.
+ * Errors: SMPC_EINVAL, SMPC_ECUDA, SMPC_ETIMEOUT, SMPC_EDIVERGED (sync only). */
+int smpc_solve(smpc_factor_t* fac, const smpc_step_data* data, const smpc_solve_opts* opts,
+               smpc_result* res, void* stream);
+
+/* Completes an asynchronous solve (opts->sync = 0): waits for the stream of the
+ * factor's last solve and fills the host outputs of `res` (iterations, rho,
+ * rho_rel, u0_host, history_host) exactly as a synchronous solve would.
+ * Errors: SMPC_EINVAL (no solve yet), SMPC_ECUDA, SMPC_ETIMEOUT, SMPC_EDIVERGED. */
+int smpc_solve_info(smpc_factor_t* fac, smpc_result* res);
+
+const char* smpc_status_string(int status);
+const char* smpc_last_error(void);
+int smpc_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SMPC_H */

@@ -1,0 +1,228 @@
+"""Python binding of libsmpc.so: the C ABI declared in include/smpc.h, same names.
+
+Argument marshalling only: every step of the solver runs in the library's CUDA
+kernels.  PyTorch tensors serve as device buffers (``data_ptr()``) and their
+stream handles are passed through.  The library must have been built
+(``__graft_entry__.build()``); there is no fallback of any kind.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libsmpc.so")
+
+SMPC_OK, SMPC_EINVAL, SMPC_ENOMEM, SMPC_ECUDA, SMPC_EBUSY, SMPC_ETIMEOUT, SMPC_EDIVERGED, SMPC_ENOTSUP = range(8)
+SMPC_FP64, SMPC_FP32, SMPC_BF16 = 0, 1, 2
+
+_dp = ctypes.POINTER(ctypes.c_double)
+_ip = ctypes.POINTER(ctypes.c_int32)
+
+
+class smpc_network(ctypes.Structure):
+    _fields_ = [("n_x", ctypes.c_int32), ("n_u", ctypes.c_int32), ("n_d", ctypes.c_int32), ("n_e", ctypes.c_int32),
+                ("A", _dp), ("B", _dp), ("Gd", _dp), ("E", _dp), ("Ed", _dp)]
+
+
+class smpc_cost(ctypes.Structure):
+    _fields_ = [("W_alpha", ctypes.c_double), ("alpha1", _dp), ("W_u", _dp), ("W_x", ctypes.c_double),
+                ("gamma_d", ctypes.c_double), ("x_min", _dp), ("x_max", _dp), ("x_s", _dp), ("u_min", _dp),
+                ("u_max", _dp), ("safety_unweighted", ctypes.c_int32)]
+
+
+class smpc_factor_opts(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int32), ("precondition", ctypes.c_int32), ("lambda_", ctypes.c_double),
+                ("power_iters", ctypes.c_int32), ("lambda_margin", ctypes.c_double),
+                ("step_s", _dp), ("step_z", _dp), ("step_p", _dp)]
+
+
+class smpc_step_data(ctypes.Structure):
+    _fields_ = [("p", _dp), ("q", _dp), ("dhat", _dp), ("eps", _dp), ("alpha2", _dp)]
+
+
+class smpc_solve_opts(ctypes.Structure):
+    _fields_ = [("max_iters", ctypes.c_int32), ("tol", ctypes.c_double), ("warm_start", ctypes.c_int32),
+                ("check_every", ctypes.c_int32), ("sync", ctypes.c_int32)]
+
+
+class smpc_result(ctypes.Structure):
+    _fields_ = [("u", ctypes.c_void_p), ("x", ctypes.c_void_p), ("y", ctypes.c_void_p), ("u0_host", _dp),
+                ("history_host", _dp), ("iterations", ctypes.c_int32), ("rho", ctypes.c_double),
+                ("rho_rel", ctypes.c_double), ("launches", ctypes.c_int32)]
+
+
+class smpc_tree_info(ctypes.Structure):
+    _fields_ = [("n_nodes", ctypes.c_int32), ("horizon", ctypes.c_int32), ("n_leaves", ctypes.c_int32),
+                ("n_chains", ctypes.c_int32), ("n_top", ctypes.c_int32), ("max_chain_len", ctypes.c_int32)]
+
+
+# symbol -> (restype, argtypes); every entry point declared in include/smpc.h
+SIGNATURES = {
+    "smpc_tree_create": (ctypes.c_int, [ctypes.c_int32, _ip, _dp, ctypes.POINTER(ctypes.c_void_p)]),
+    "smpc_tree_info_get": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(smpc_tree_info)]),
+    "smpc_tree_destroy": (None, [ctypes.c_void_p]),
+    "smpc_factor": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(smpc_network), ctypes.POINTER(smpc_cost),
+                                   ctypes.POINTER(smpc_factor_opts), ctypes.POINTER(ctypes.c_void_p)]),
+    "smpc_factor_destroy": (None, [ctypes.c_void_p]),
+    "smpc_factor_steps": (ctypes.c_int, [ctypes.c_void_p, _dp, _dp, _dp, _dp]),
+    "smpc_solve": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(smpc_step_data), ctypes.POINTER(smpc_solve_opts),
+                                  ctypes.POINTER(smpc_result), ctypes.c_void_p]),
+    "smpc_solve_info": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(smpc_result)]),
+    "smpc_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+    "smpc_last_error": (ctypes.c_char_p, []),
+    "smpc_version": (ctypes.c_int, []),
+}
+
+_lib = None
+
+
+def lib():
+    """Load libsmpc.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing; build it with __graft_entry__.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+class SmpcError(RuntimeError):
+    def __init__(self, code, where):
+        L = lib()
+        super().__init__(f"{where}: {L.smpc_status_string(code).decode()} ({code}): {L.smpc_last_error().decode()}")
+        self.code = code
+
+
+def _check(code, where):
+    if code != SMPC_OK:
+        raise SmpcError(code, where)
+
+
+def _f64(a):
+    return np.ascontiguousarray(np.asarray(a, dtype=np.float64))
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data_as(_dp)
+
+
+class _Keep:
+    """Holds numpy arrays alive while a call uses their pointers."""
+
+    def __init__(self):
+        self.arrays = []
+
+    def __call__(self, a):
+        if a is None:
+            return None
+        a = _f64(a)
+        self.arrays.append(a)
+        return _ptr(a)
+
+
+# --------------------------------------------------------------------- the calls
+def smpc_tree_create(parent, prob=None):
+    parent = np.ascontiguousarray(np.asarray(parent, dtype=np.int32))
+    prob_a = None if prob is None else _f64(prob)
+    h = ctypes.c_void_p()
+    _check(lib().smpc_tree_create(len(parent), parent.ctypes.data_as(_ip), _ptr(prob_a), ctypes.byref(h)),
+           "smpc_tree_create")
+    return h
+
+
+def smpc_tree_info_get(tree):
+    info = smpc_tree_info()
+    _check(lib().smpc_tree_info_get(tree, ctypes.byref(info)), "smpc_tree_info_get")
+    return {k: getattr(info, k) for k, _ in smpc_tree_info._fields_}
+
+
+def smpc_tree_destroy(tree):
+    lib().smpc_tree_destroy(tree)
+
+
+def smpc_factor(tree, net, cost, precision=SMPC_FP64, precondition=1, lam=0.0, power_iters=0, lambda_margin=0.0,
+                steps=None, safety_unweighted=0):
+    """net / cost: dicts with the fields of smpc_network / smpc_cost (numpy arrays).
+    steps: optional dict {'s': (n,), 'z': (n,), 'p': (n, n_u)} of explicit per-entry steps."""
+    k = _Keep()
+    A = net.get("A")
+    n_x, n_u = net["B"].shape
+    n_d = net["Gd"].shape[1]
+    n_e = net["E"].shape[0] if net.get("E") is not None else 0
+    N = smpc_network(n_x, n_u, n_d, n_e, k(A), k(net["B"]), k(net["Gd"]),
+                     k(net["E"]) if n_e else None, k(net["Ed"]) if n_e else None)
+    C = smpc_cost(float(cost["W_alpha"]), k(cost["alpha1"]), k(cost["W_u"]), float(cost["W_x"]), float(cost["gamma_d"]),
+                  k(cost["x_min"]), k(cost["x_max"]), k(cost["x_s"]), k(cost["u_min"]), k(cost["u_max"]),
+                  int(safety_unweighted))
+    O = smpc_factor_opts(int(precision), int(precondition), float(lam), int(power_iters), float(lambda_margin),
+                         None, None, None)
+    if steps is not None:
+        O.step_s, O.step_z, O.step_p = k(steps["s"]), k(steps["z"]), k(steps["p"])
+    h = ctypes.c_void_p()
+    _check(lib().smpc_factor(tree, ctypes.byref(N), ctypes.byref(C), ctypes.byref(O), ctypes.byref(h)), "smpc_factor")
+    return h
+
+
+def smpc_factor_destroy(fac):
+    lib().smpc_factor_destroy(fac)
+
+
+def smpc_factor_steps(fac, n, n_u):
+    lam = ctypes.c_double()
+    s, z, p = np.zeros(n), np.zeros(n), np.zeros((n, n_u))
+    _check(lib().smpc_factor_steps(fac, ctypes.byref(lam), _ptr(s), _ptr(z), _ptr(p)), "smpc_factor_steps")
+    return lam.value, {"s": s, "z": z, "p": p}
+
+
+def smpc_solve(fac, p, q, dhat, alpha2, eps=None, max_iters=500, tol=0.0, warm_start=0, check_every=0, sync=1,
+               u=None, x=None, y=None, u0_host=None, history_host=None, stream=None):
+    """u, x, y: optional torch device tensors (or raw device pointers) receiving the outputs.
+    u0_host / history_host: optional numpy float64 arrays filled when sync=1."""
+    k = _Keep()
+    D = smpc_step_data(k(p), k(q), k(dhat), k(eps), k(alpha2))
+    O = smpc_solve_opts(int(max_iters), float(tol), int(warm_start), int(check_every), int(sync))
+
+    def dptr(t):
+        if t is None:
+            return None
+        return t if isinstance(t, int) else t.data_ptr()
+
+    R = smpc_result(dptr(u), dptr(x), dptr(y),
+                    None if u0_host is None else u0_host.ctypes.data_as(_dp),
+                    None if history_host is None else history_host.ctypes.data_as(_dp), -1, 0.0, 0.0, 0)
+    if stream is None:
+        s = None
+    elif isinstance(stream, int):
+        s = stream
+    else:
+        s = stream.cuda_stream
+    _check(lib().smpc_solve(fac, ctypes.byref(D), ctypes.byref(O), ctypes.byref(R), s), "smpc_solve")
+    return {"iterations": R.iterations, "rho": R.rho, "rho_rel": R.rho_rel, "launches": R.launches}
+
+
+def smpc_solve_info(fac, u0_host=None, history_host=None):
+    """Completes an asynchronous solve and returns its host-side outputs."""
+    R = smpc_result(None, None, None, None if u0_host is None else u0_host.ctypes.data_as(_dp),
+                    None if history_host is None else history_host.ctypes.data_as(_dp), -1, 0.0, 0.0, 0)
+    _check(lib().smpc_solve_info(fac, ctypes.byref(R)), "smpc_solve_info")
+    return {"iterations": R.iterations, "rho": R.rho, "rho_rel": R.rho_rel, "launches": R.launches}
+
+
+def smpc_status_string(code):
+    return lib().smpc_status_string(code).decode()
+
+
+def smpc_last_error():
+    return lib().smpc_last_error().decode()
+
+
+def smpc_version():
+    return lib().smpc_version()

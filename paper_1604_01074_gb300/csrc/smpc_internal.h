@@ -1,0 +1,162 @@
+// Internal declarations shared by the host code (api.cpp, factor_host.cpp) and
+// the device code (kernels.cu).  Not part of the public ABI.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/smpc.h"
+
+namespace smpc {
+
+void set_error(const char* fmt, ...);
+
+// ---------------------------------------------------------------------------
+// Host FP64 dense linear algebra for the factor step (App. A, App. B).
+struct HostFactor {
+  int n_x = 0, n_u = 0, n_d = 0, n_e = 0, n_v = 0;
+  std::vector<double> L;      // n_u x n_v, orthonormal basis of null(E)
+  std::vector<double> Bbar;   // n_x x n_v
+  std::vector<double> Rhat;   // n_u x n_v
+  std::vector<double> Rbar;   // n_v x n_v
+  std::vector<double> Lam;    // n_v x n_v, -Rbar^{-1}
+  std::vector<double> Pu;     // n_u x n_d, u_hat(d) = Pu d (minimum-norm particular solution)
+  std::vector<double> Pe;     // n_x x n_d, e(d) = B u_hat(d) + Gd d
+  std::vector<double> diagB;  // n_x, diag(Bbar Rbar^{-1} Bbar')
+  std::vector<double> diagL;  // n_u, diag(L Rbar^{-1} L')
+};
+// Returns SMPC_OK or SMPC_EINVAL (rank-deficient E, W_u not positive definite).
+int host_factor(const smpc_network& net, const double* W_u, HostFactor& out);
+
+// ---------------------------------------------------------------------------
+// Tree structure after validation (host copy + device mirrors).
+struct DevTree {
+  int* parent = nullptr;
+  int* stage = nullptr;
+  int* child_begin = nullptr;
+  int* child_count = nullptr;
+  int* chain_off = nullptr;     // n_chains + 1
+  int* chain_node = nullptr;    // chain nodes, top-down
+  int* chain_parent = nullptr;  // top node above each chain head, or -1
+  int* top_nodes = nullptr;     // n_top
+  int* top_expect = nullptr;    // per node: arrivals a top node waits for (children + 1)
+  int* path_off = nullptr;      // per node (n + 1): path of a top node, root .. node
+  int* path_node = nullptr;
+  double* prob = nullptr;
+  double* pbar = nullptr;       // p_n + sum of children's p (App. A)
+};
+
+}  // namespace smpc
+
+struct smpc_tree {
+  int n = 0, N = 0, n_leaves = 0, max_chain_len = 0, device = 0;
+  std::vector<int> parent, stage, child_begin, child_count;
+  std::vector<double> prob, pbar;
+  std::vector<int> chain_off, chain_node, chain_parent;
+  std::vector<int> top_nodes, is_top, top_expect;
+  std::vector<int> path_off, path_node;
+  smpc::DevTree dev;
+};
+
+namespace smpc {
+
+// Device-side parameters of the iteration kernel.  VT: vector type, MT: matrix type.
+struct IterArgs {
+  int n, n_x, n_u, n_v, n_k;     // n_k = n_x + n_u rows of [Bbar; L]
+  int n_chains, n_top;
+  const int* parent;
+  const int* child_begin;
+  const int* child_count;
+  const int* chain_off;
+  const int* chain_node;
+  const int* chain_parent;
+  const int* top_nodes;
+  const int* top_expect;
+  const int* path_off;
+  const int* path_node;
+  const void* packs;             // per node: [Bbar; L] (n_k x n_v) then Lambda/(2 p_n) (n_v x n_v)
+  long long pack_stride;         // entries between consecutive nodes' packs
+  void* ybuf0;                   // y^k for even k: n x (2 n_x + n_u)
+  void* ybuf1;                   // y^k for odd k
+  void* wbuf;                    // w^nu restricted to (xi, psi): n x n_k
+  void* h;                       // [Bbar delta; L delta]: n x n_k
+  const void* uhat;              // n x n_u
+  const void* e;                 // n x n_x
+  const void* beta;              // n x n_v
+  void* spub;                    // n x n_x  (published s of chain heads / top nodes)
+  void* rpub;                    // n x n_v
+  void* uout;                    // n x n_u
+  void* xout;                    // n x n_x
+  const void* step_s;            // n
+  const void* step_z;            // n
+  const void* step_p;            // n x n_u
+  const void* mu_s;              // n
+  const void* x_s;
+  const void* x_min;
+  const void* x_max;
+  const void* u_min;
+  const void* u_max;
+  const void* p0;                // n_x measured state
+  double gamma_d;
+  const double* cvec;            // extrapolation coefficients c_nu, nu = 0..max_iters
+  unsigned long long* res;       // per iteration: rho, ||Hz||, ||t|| as float64 bits
+  int* counters;                 // per node arrival counters (top nodes)
+  int* flags;                    // [0] iterations done (-1 running), [1] error code
+  double tol;
+  double* pw;                    // power iteration: [k] ||y_k||^2, [K + k] <y_k, y_{k+1}>
+  int pw_len;
+};
+
+enum KernelMode : int {
+  MODE_PROX = 1,      // forward of iteration nu-1, prox, dual update (Phase P)
+  MODE_BWD = 2,       // backward sweep of iteration nu
+  MODE_LINEAR = 4,    // power iteration on the (scaled) dual Hessian: no affine data, no prox
+  MODE_CHECK = 8      // honour the stop flag / tolerance
+};
+
+struct LaunchCfg {
+  int grid = 1, block = 256;
+  size_t smem = 0;
+  int stages = 1;
+};
+
+// Kernel launchers (kernels.cu).  prec: smpc_precision.
+LaunchCfg iter_config(int prec, const IterArgs& a, int num_sms);
+int launch_iter(int prec, const IterArgs& a, const LaunchCfg& cfg, int nu, int mode, void* stream);
+int launch_pack(int prec, int n, int n_k, int n_v, const double* K, const double* Lam, const double* prob,
+                void* packs, long long pack_stride, void* stream);
+struct CostArgs {
+  int n, N, n_x, n_u, n_d, n_v;
+  const int* parent;
+  const int* stage;
+  const int* child_begin;
+  const int* child_count;
+  const double* prob;
+  const double* pbar;
+  const double* Pu;       // n_u x n_d
+  const double* Pe;       // n_x x n_d
+  const double* Rhat;     // n_u x n_v
+  const double* L;        // n_u x n_v
+  const double* alpha1;   // n_u
+  double W_alpha;
+  const double* dhat;     // N x n_d
+  const double* eps;      // n x n_d
+  const double* alpha2;   // N x n_u
+  const double* q;        // n_u
+  double* uhat64;         // n x n_u scratch
+  double* abar;           // N x n_v scratch
+  void* uhat;             // outputs in the vector type
+  void* e;
+  void* beta;
+};
+int launch_cost_update(int prec, const CostArgs& a, void* stream);
+int launch_copy_final_y(int prec, const IterArgs& a, int max_iters, void* dst, void* stream);
+long long pack_entries(int n_k, int n_v);
+int launch_init_duals(int prec, const IterArgs& a, int warm, void* stream);
+int launch_convert(int prec, const double* src, void* dst, long long count, void* stream);
+size_t vec_size(int prec);
+size_t mat_size(int prec);
+
+}  // namespace smpc

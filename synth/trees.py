@@ -122,3 +122,10 @@ def random_tree(rng, horizon, max_children=3, branch_stages=None, p_branch=0.5):
     for m in range(1, n):
         prob[m] = prob[parent[m]] * w[m] / child_sum[parent[m]]
     return {"parent": parent, "stage": stages_of(parent), "prob": prob, "horizon": int(horizon)}
+
+
+def tree_from_fanouts_dict(fanouts):
+    """Tree dict (equiprobable scenarios) from explicit per-stage child counts."""
+    parent = tree_from_fanouts(fanouts)
+    return {"parent": parent, "stage": stages_of(parent), "prob": uniform_scenario_probabilities(parent),
+            "horizon": len(fanouts) + 1}

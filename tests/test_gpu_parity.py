@@ -1,0 +1,179 @@
+"""GPU path (through the C ABI) against the FP64 oracle, element by element.
+
+Tolerances:
+* float64 packs and vectors: max over u, x, y of |gpu - oracle| / (1 + |oracle|_inf)
+  <= 1e-9 after 1, 10 and 500 iterations;
+* float32 / bfloat16 packs: |rho_rel,gpu - rho_rel,oracle| <= 1e-4 at equal iteration
+  counts, with the elementwise error of u and the coupling residual stated in the
+  assertion messages.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from tests import harness as H
+
+pytestmark = pytest.mark.gpu
+
+FP64_TOL = 1e-9
+
+
+def compare_fp64(P, steps, iters):
+    R = H.oracle_run(P, steps, iters)
+    g = H.Gpu(P, steps=steps)
+    try:
+        info = g.solve(iters)
+        u, x, y = g.arrays()
+    finally:
+        g.close()
+    assert info["iterations"] == iters
+    eu, ex, ey = H.relerr(u, R.u), H.relerr(x, R.x), H.relerr(y, H.stack_y(R.y))
+    assert max(eu, ex, ey) <= FP64_TOL, (iters, eu, ex, ey)
+    assert abs(info["rho"] - R.rho[-1]) <= FP64_TOL * (1 + abs(R.rho[-1])) * 10
+    np.testing.assert_allclose(info["history"][:, 0], R.rho, rtol=1e-7, atol=1e-9)
+    return info, R
+
+
+@pytest.mark.parametrize("iters", [1, 10, 500])
+def test_tiny_fp64(iters):
+    P = synth.tiny(0)
+    compare_fp64(P, H.tiny_steps(P), iters)
+
+
+@pytest.mark.parametrize("name", list(H.edge_instances()))
+@pytest.mark.parametrize("iters", [1, 10, 200])
+def test_edge_trees_fp64(name, iters):
+    P = H.edge_instances()[name]
+    tree, fac, _ = H.oracle_build(P)
+    steps = oracle.jacobi_steps(fac, tree)
+    compare_fp64(P, steps, iters)
+
+
+@pytest.fixture(scope="module")
+def barcelona_case():
+    P = synth.barcelona(0)
+    tree, fac, _ = H.oracle_build(P)
+    unit = H.closed_form_steps(fac, tree, 1.0)
+    lam = 1.0 / (1.02 * H.oracle_power_lambda(fac, tree, unit, iters=40))
+    return P, H.closed_form_steps(fac, tree, lam)
+
+
+@pytest.mark.parametrize("iters", [1, 10, 60])
+def test_barcelona_fp64_full_size(barcelona_case, iters):
+    P, steps = barcelona_case
+    compare_fp64(P, steps, iters)
+
+
+def test_lambda_and_preconditioner_match_oracle():
+    P = synth.tiny(0)
+    tree, fac, _ = H.oracle_build(P)
+    ref = oracle.jacobi_steps(fac, tree)
+    g = H.Gpu(P, precondition=1, power_iters=400, lambda_margin=1e-12)
+    try:
+        lam, st = g.steps()
+    finally:
+        g.close()
+    assert abs(lam - ref["lambda"]) <= 1e-6 * ref["lambda"]
+    for k in ("s", "z", "p"):
+        assert H.relerr(st[k], ref[k]) <= 1e-6 * (1 + 0 * st[k].max()) or np.abs(st[k] / ref[k] - 1).max() < 1e-6
+
+
+def test_unpreconditioned_lambda_matches_dense_eigenvalue():
+    P = synth.random_instance(3)
+    tree, fac, _ = H.oracle_build(P)
+    L = oracle.lipschitz_dense(oracle.dense_dual_hessian(fac, tree))
+    g = H.Gpu(P, precondition=0, power_iters=600, lambda_margin=1e-12)
+    try:
+        lam, _ = g.steps()
+    finally:
+        g.close()
+    assert abs(1.0 / lam - L) <= 1e-6 * L
+
+
+def test_deterministic_and_warm_start():
+    P = synth.random_instance(21, horizon=6, max_children=3)
+    tree, fac, cu = H.oracle_build(P)
+    steps = oracle.jacobi_steps(fac, tree)
+    g = H.Gpu(P, steps=steps)
+    try:
+        g.solve(50)
+        a = [t.clone() for t in (g.u, g.x, g.y)]
+        g.solve(50)
+        b = [t.clone() for t in (g.u, g.x, g.y)]
+        for s, t in zip(a, b):
+            assert bool((s == t).all())
+        # warm start: y^0 = y^{-1} = the previous final dual
+        y_prev = H.stack_y(oracle.apg(fac, tree, cu, P["cost"], P["p"], steps, 50).y)
+        info = g.solve(30, warm=1)
+        u, x, y = g.arrays()
+    finally:
+        g.close()
+    nx = P["net"]["n_x"]
+    y0 = (y_prev[:, :nx], y_prev[:, nx:2 * nx], y_prev[:, 2 * nx:])
+    R = oracle.apg(fac, tree, cu, P["cost"], P["p"], steps, 30, y0=y0)
+    assert info["iterations"] == 30
+    assert max(H.relerr(u, R.u), H.relerr(x, R.x), H.relerr(y, H.stack_y(R.y))) <= FP64_TOL
+
+
+def test_tolerance_stop_matches_oracle_history():
+    P = synth.tiny(0)
+    steps = H.tiny_steps(P)
+    R = H.oracle_run(P, steps, 3000)
+    tol = 1e-3
+    first = int(np.argmax(R.rho_rel <= tol))
+    assert R.rho_rel[first] <= tol
+    g = H.Gpu(P, steps=steps)
+    try:
+        info = g.solve(3000, tol=tol, check_every=16)
+        u, x, y = g.arrays()
+    finally:
+        g.close()
+    assert info["iterations"] == first + 1
+    R2 = H.oracle_run(P, steps, first + 1)
+    assert max(H.relerr(u, R2.u), H.relerr(x, R2.x), H.relerr(y, H.stack_y(R2.y))) <= FP64_TOL
+    assert info["rho_rel"] <= tol
+
+
+def test_not_supported_and_invalid_on_device():
+    import paper_1604_01074_gb300 as smpc
+    P = synth.tiny(0)
+    t = P["tree"]
+    tree = smpc.smpc_tree_create(t["parent"], t["prob"])
+    try:
+        net = dict(P["net"])
+        net["A"] = 0.9 * np.eye(net["n_x"])
+        with pytest.raises(smpc.SmpcError) as ei:
+            smpc.smpc_factor(tree, net, P["cost"])
+        assert ei.value.code == smpc.SMPC_ENOTSUP
+        net = dict(P["net"])
+        net["E"] = np.vstack([net["E"], net["E"]])
+        net["Ed"] = np.vstack([net["Ed"], net["Ed"]])
+        with pytest.raises(smpc.SmpcError) as ei:
+            smpc.smpc_factor(tree, net, P["cost"])
+        assert ei.value.code == smpc.SMPC_EINVAL
+        cost = dict(P["cost"])
+        cost["W_u"] = -np.eye(P["net"]["n_u"])
+        with pytest.raises(smpc.SmpcError) as ei:
+            smpc.smpc_factor(tree, P["net"], cost)
+        assert ei.value.code == smpc.SMPC_EINVAL
+    finally:
+        smpc.smpc_tree_destroy(tree)
+
+
+@pytest.mark.parametrize("precision", [1, 2])
+def test_reduced_precision_residual(precision):
+    P = synth.tiny(0)
+    steps = H.tiny_steps(P)
+    iters = 500
+    R = H.oracle_run(P, steps, iters)
+    g = H.Gpu(P, steps=steps, precision=precision)
+    try:
+        info = g.solve(iters)
+        u, x, y = g.arrays()
+    finally:
+        g.close()
+    d = H.synth_demands(P) if hasattr(H, "synth_demands") else P["dhat"][P["tree"]["stage"]] + P["eps"]
+    coupling = np.abs(u @ P["net"]["E"].T + d @ P["net"]["Ed"].T).max()
+    eu = H.relerr(u, R.u)
+    assert abs(info["rho_rel"] - R.rho_rel[-1]) <= 1e-4, (info["rho_rel"], R.rho_rel[-1], eu, coupling)
