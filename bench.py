@@ -287,6 +287,7 @@ def run_ours(args, rank, world, local_rank):
     dev_in = [S.device_inputs(i) for i in inputs]
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=device)  # 256 MB > L2
 
+    log("factor ready", S.info)
     # warm-up solves (untimed)
     for k in range(args.warmup):
         S.solve(dev_in[k], args.max_iters, args.tol, stream)
@@ -314,6 +315,7 @@ def run_ours(args, rank, world, local_rank):
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
+    log("timed solves ms", times, "iterations", iters)
     local_s = sum(times) / 1000.0
     units, secs = aggregate(args.steps, local_s, device if world > 1 else None)
     value = units / secs
@@ -322,8 +324,7 @@ def run_ours(args, rank, world, local_rank):
 
     # kernel roofline: one iteration launch, differential timing
     t_iter_ms = time_per_iteration(S, dev_in[0], stream)
-    nbytes, mat_entries, flops = algorithmic_bytes_per_iteration(S.n, S.n_x, S.n_u, S.n_x + S.n_u - S.n_x - 17, prec)
-    # n_v from the network: n_u - rank(E)
+    log("ms per iteration launch", t_iter_ms)
     n_v = S.n_u - np.linalg.matrix_rank(P["net"]["E"])
     nbytes, mat_entries, flops = algorithmic_bytes_per_iteration(S.n, S.n_x, S.n_u, n_v, prec)
     hbm, src = peaks()
@@ -350,6 +351,7 @@ def run_ours(args, rank, world, local_rank):
         S.solve(pin_in[k], args.max_iters, args.tol, stream, sync=1, u0=u0)
         e2e_t.append(time.perf_counter() - t0)
     e2e_units, e2e_secs = aggregate(args.steps, sum(e2e_t), device if world > 1 else None)
+    log("e2e s", e2e_t)
     h2d = sum(int(np.asarray(v).nbytes) for v in inputs[0].values())
     d2h = 8 * S.n_u + 8 + 24
 
@@ -366,6 +368,7 @@ def run_ours(args, rank, world, local_rank):
         "e2e": {"value": e2e_units / e2e_secs, "unit": "solves/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "tree": S.info,
     }
+    log("headline", {k: result[k] for k in ("value", "ms_per_step", "iterations_mean", "p50_ms", "p99_ms")})
     S.close()
     if args.fp64_leg and prec != 0 and rank == 0:
         S64 = Solver(P, 0, device)
@@ -377,6 +380,7 @@ def run_ours(args, rank, world, local_rank):
         e1.record(stream)
         inf64 = S64.finish()
         ms64 = e0.elapsed_time(e1)
+        log("fp64 solve ms", ms64, inf64, "us/iter", 1000 * t64)
         _, _, fl = algorithmic_bytes_per_iteration(S64.n, S64.n_x, S64.n_u, n_v, 0)
         result["fp64"] = {"solves_per_s": 1000.0 / ms64, "ms_per_solve": ms64, "iterations": inf64["iterations"],
                           "us_per_iteration": 1000.0 * t64,
@@ -388,6 +392,7 @@ def run_ours(args, rank, world, local_rank):
         stored, _ = oracle_iters_to_tol(args.config)
         try:
             result["cpu_baseline"] = cpu_baseline(args.config, stored or it_ref)
+            log("cpu baseline", result["cpu_baseline"])
         except Exception as exc:  # noqa: BLE001
             result["cpu_baseline"] = {"error": str(exc)[-300:]}
     if world > 1:
@@ -422,6 +427,18 @@ def run_reference(args, rank, world):
             "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
+def _jsonable(o):
+    if hasattr(o, "item"):
+        return o.item()
+    if isinstance(o, (set, tuple)):
+        return list(o)
+    return str(o)
+
+
+def log(*a):
+    print("[bench]", *a, file=sys.stderr, flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -445,7 +462,7 @@ def main():
     else:
         res = run_ours(args, rank, world, local_rank)
     if rank == 0 and res is not None:
-        print(json.dumps(res))
+        print(json.dumps(res, default=_jsonable))
 
 
 if __name__ == "__main__":

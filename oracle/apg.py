@@ -51,7 +51,9 @@ def _steps(steps, n, n_u):
     return np.full(n, lam), np.full(n, lam), np.full((n, n_u), lam)
 
 
-def apg(fac, tree, cu, cost, p0, steps, iters, mu_s=None, y0=None):
+def apg(fac, tree, cu, cost, p0, steps, iters, mu_s=None, y0=None, tol=None):
+    """Runs `iters` iterations, or stops after the first iterate whose relative
+    residual is <= tol (Sec. IV-E); the returned histories end at that iterate."""
     n, n_x, n_u = tree.n, fac.n_x, fac.n_u
     lam_s, lam_z, lam_p = _steps(steps, n, n_u)
     if mu_s is None:
@@ -92,6 +94,9 @@ def apg(fac, tree, cu, cost, p0, steps, iters, mu_s=None, y0=None):
         else:
             xbar = (1.0 - th) * xbar + th * x
             ubar = (1.0 - th) * ubar + th * u
+        if tol is not None and rho_rel[nu] <= tol:
+            rho, rho_rel = rho[:nu + 1], rho_rel[:nu + 1]
+            break
     return SimpleNamespace(x=x, u=u, t_s=t_s, t_z=t_z, t_p=t_p,
                            y=(y_s, y_z, y_p), y_prev=(yp_s, yp_z, yp_p),
                            rho=rho, rho_rel=rho_rel, xbar=xbar, ubar=ubar, theta=theta)

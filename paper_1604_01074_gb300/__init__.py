@@ -187,7 +187,13 @@ def smpc_solve(fac, p, q, dhat, alpha2, eps=None, max_iters=500, tol=0.0, warm_s
     """u, x, y: optional torch device tensors (or raw device pointers) receiving the outputs.
     u0_host / history_host: optional numpy float64 arrays filled when sync=1."""
     k = _Keep()
-    D = smpc_step_data(k(p), k(q), k(dhat), k(eps), k(alpha2))
+
+    def arg(a):  # host array, or an int device address of float64 data
+        if isinstance(a, int):
+            return ctypes.cast(ctypes.c_void_p(a), _dp)
+        return k(a)
+
+    D = smpc_step_data(arg(p), arg(q), arg(dhat), arg(eps), arg(alpha2))
     O = smpc_solve_opts(int(max_iters), float(tol), int(warm_start), int(check_every), int(sync))
 
     def dptr(t):

@@ -61,6 +61,20 @@ bool finite_array(const double* p, size_t n) {
   return true;
 }
 
+// True when the host may dereference p (pageable, pinned or managed memory).
+bool host_readable(const void* p) {
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return true;
+  }
+  return at.type != cudaMemoryTypeDevice;
+}
+
+// Finiteness of step data that lives in host memory; device-resident data is
+// checked on the device instead (non-finite iterates raise SMPC_EDIVERGED).
+bool finite_if_host(const double* p, size_t n) { return !host_readable(p) || finite_array(p, n); }
+
 void free_tree_dev(smpc::DevTree& d) {
   void* ptrs[] = {d.parent, d.stage, d.child_begin, d.child_count, d.chain_off, d.chain_node, d.chain_parent,
                   d.top_nodes, d.top_expect, d.path_off, d.path_node, d.prob, d.pbar};
@@ -232,6 +246,8 @@ struct smpc_factor_t {
   void *ybuf0 = nullptr, *ybuf1 = nullptr, *wbuf = nullptr, *h = nullptr, *uhat = nullptr, *e = nullptr, *beta = nullptr;
   void *spub = nullptr, *rpub = nullptr, *uout = nullptr, *xout = nullptr;
   void *step_s = nullptr, *step_z = nullptr, *step_p = nullptr, *mu_s = nullptr;
+  void *inv_s = nullptr, *inv_z = nullptr, *thr_s = nullptr, *thr_z = nullptr, *inv_p = nullptr;
+  std::vector<double> mu_host;
   void *x_s = nullptr, *x_min = nullptr, *x_max = nullptr, *u_min = nullptr, *u_max = nullptr, *p0 = nullptr;
   double gamma_d = 0;
   int* counters = nullptr;
@@ -304,6 +320,11 @@ IterArgs make_args(const smpc_factor_t* f) {
   a.step_s = f->step_s;
   a.step_z = f->step_z;
   a.step_p = f->step_p;
+  a.inv_s = f->inv_s;
+  a.inv_z = f->inv_z;
+  a.thr_s = f->thr_s;
+  a.thr_z = f->thr_z;
+  a.inv_p = f->inv_p;
   a.mu_s = f->mu_s;
   a.x_s = f->x_s;
   a.x_min = f->x_min;
@@ -600,7 +621,7 @@ int smpc_factor(const smpc_tree* tree, const smpc_network* net, const smpc_cost*
       (rc = up64(&f->alpha1, cost->alpha1, n_u)))
     return fail(rc);
   // ---- packs
-  f->pack_stride = pack_entries(n_k, n_v);
+  f->pack_stride = pack_entries(f->prec, n_k, n_v);
   if ((rc = f->alloc(&f->packs, (size_t)n * f->pack_stride * f->ms))) return fail(rc);
   if ((rc = launch_pack(f->prec, n, n_k, n_v, f->K64, f->Lam64, tree->dev.prob, f->packs, f->pack_stride, nullptr)))
     return fail(rc);
@@ -608,11 +629,13 @@ int smpc_factor(const smpc_tree* tree, const smpc_network* net, const smpc_cost*
   const size_t vs = f->vs;
   void** vecs[] = {&f->ybuf0, &f->ybuf1, &f->wbuf, &f->h, &f->uhat, &f->e, &f->beta, &f->spub, &f->rpub,
                    &f->uout, &f->xout, &f->step_s, &f->step_z, &f->step_p, &f->mu_s, &f->x_s, &f->x_min,
-                   &f->x_max, &f->u_min, &f->u_max, &f->p0};
+                   &f->x_max, &f->u_min, &f->u_max, &f->p0, &f->inv_s, &f->inv_z, &f->thr_s, &f->thr_z,
+                   &f->inv_p};
   const size_t cnts[] = {(size_t)n * nd, (size_t)n * nd, (size_t)n * n_k, (size_t)n * n_k, (size_t)n * n_u,
                          (size_t)n * n_x, (size_t)n * n_v, (size_t)n * n_x, (size_t)n * n_v, (size_t)n * n_u,
                          (size_t)n * n_x, (size_t)n, (size_t)n, (size_t)n * n_u, (size_t)n, (size_t)n_x,
-                         (size_t)n_x, (size_t)n_x, (size_t)n_u, (size_t)n_u, (size_t)n_x};
+                         (size_t)n_x, (size_t)n_x, (size_t)n_u, (size_t)n_u, (size_t)n_x, (size_t)n,
+                         (size_t)n, (size_t)n, (size_t)n, (size_t)n * n_u};
   for (size_t i = 0; i < sizeof(cnts) / sizeof(cnts[0]); ++i) {
     if ((rc = f->alloc(vecs[i], cnts[i] * vs))) return fail(rc);
     if (cudaMemset(*vecs[i], 0, cnts[i] * vs) != cudaSuccess) {
@@ -643,6 +666,7 @@ int smpc_factor(const smpc_tree* tree, const smpc_network* net, const smpc_cost*
   // bounds and safety weights
   std::vector<double> mu(n);
   for (int m = 0; m < n; ++m) mu[m] = cost->safety_unweighted ? cost->W_x : tree->prob[m] * cost->W_x;
+  f->mu_host = mu;
   if ((rc = put_vec(f, f->mu_s, mu.data(), n)) || (rc = put_vec(f, f->x_s, cost->x_s, n_x)) ||
       (rc = put_vec(f, f->x_min, cost->x_min, n_x)) || (rc = put_vec(f, f->x_max, cost->x_max, n_x)) ||
       (rc = put_vec(f, f->u_min, cost->u_min, n_u)) || (rc = put_vec(f, f->u_max, cost->u_max, n_u)))
@@ -728,6 +752,20 @@ int smpc_factor(const smpc_tree* tree, const smpc_network* net, const smpc_cost*
   if ((rc = put_vec(f, f->step_s, ss.data(), n)) || (rc = put_vec(f, f->step_z, sz.data(), n)) ||
       (rc = put_vec(f, f->step_p, sp.data(), sp.size())))
     return fail(rc);
+  {  // reciprocal steps and prox thresholds mu / step (App. C) used by the prox
+    std::vector<double> is(n), iz(n), ts(n), tz(n), ip(sp.size());
+    for (int m = 0; m < n; ++m) {
+      is[m] = 1.0 / ss[m];
+      iz[m] = 1.0 / sz[m];
+      ts[m] = mu[m] / ss[m];
+      tz[m] = cost->gamma_d / sz[m];
+    }
+    for (size_t i = 0; i < sp.size(); ++i) ip[i] = 1.0 / sp[i];
+    if ((rc = put_vec(f, f->inv_s, is.data(), n)) || (rc = put_vec(f, f->inv_z, iz.data(), n)) ||
+        (rc = put_vec(f, f->thr_s, ts.data(), n)) || (rc = put_vec(f, f->thr_z, tz.data(), n)) ||
+        (rc = put_vec(f, f->inv_p, ip.data(), ip.size())))
+      return fail(rc);
+  }
   if (cudaDeviceSynchronize() != cudaSuccess) {
     set_error("factor: %s", cudaGetErrorString(cudaGetLastError()));
     return fail(SMPC_ECUDA);
@@ -765,8 +803,9 @@ int smpc_solve(smpc_factor_t* f, const smpc_step_data* data, const smpc_solve_op
     return SMPC_EINVAL;
   }
   const int n = f->n, N = f->N, n_x = f->n_x, n_u = f->n_u, n_d = f->n_d;
-  if (!finite_array(data->p, n_x) || !finite_array(data->q, n_u) || !finite_array(data->alpha2, (size_t)N * n_u) ||
-      (n_d && !finite_array(data->dhat, (size_t)N * n_d)) || (data->eps && n_d && !finite_array(data->eps, (size_t)n * n_d))) {
+  if (!finite_if_host(data->p, n_x) || !finite_if_host(data->q, n_u) || !finite_if_host(data->alpha2, (size_t)N * n_u) ||
+      (n_d && !finite_if_host(data->dhat, (size_t)N * n_d)) ||
+      (data->eps && n_d && !finite_if_host(data->eps, (size_t)n * n_d))) {
     set_error("step data contains non-finite values");
     return SMPC_EINVAL;
   }

@@ -35,7 +35,10 @@ namespace {
 
 constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
-constexpr int kChunk = 16384;            // bytes per bulk copy instruction
+// One bulk copy per matrix: on this GPU the copies one SM issues are served one
+// after the other at a roughly fixed cost each, so per-SM bandwidth grows with the
+// copy size (16 KB copies: ~54 GB/s per SM; 64 KB and larger: ~200 GB/s).
+constexpr int kChunk = 1 << 20;          // larger than any matrix of a pack
 constexpr uint64_t kWaitNs = 2000000000ull;  // bounded mbarrier wait: 2 s
 
 __device__ __forceinline__ double to_acc(double v) { return v; }
@@ -123,170 +126,212 @@ __device__ __forceinline__ double warp_max(double v) {
 }
 
 // ------------------------------------------------------------------ CTA mat-vecs
-// out[j] = sum_i A[i*C + j] x[i] for j < C (A' x), A row-major R x C.
+// Matrices sit in shared memory row-major with a row stride `ld` (entries) that is
+// a multiple of 16 bytes, so every access below is a 128-bit shared-memory load:
+// 4 float32, 2 float64 or 8 bfloat16 matrix entries per instruction.
+template <typename MT>
+struct Vec;
+template <>
+struct Vec<float> { static constexpr int V = 4; };
+template <>
+struct Vec<double> { static constexpr int V = 2; };
+template <>
+struct Vec<__nv_bfloat16> { static constexpr int V = 8; };
+
+template <typename MT>
+inline __host__ __device__ int row_stride(int n_v) {
+  const int V = 16 / (int)sizeof(MT);
+  return (n_v + V - 1) / V * V;
+}
+
+__device__ __forceinline__ void ld16(const float* p, float (&o)[4]) {
+  const float4 t = *reinterpret_cast<const float4*>(p);
+  o[0] = t.x; o[1] = t.y; o[2] = t.z; o[3] = t.w;
+}
+__device__ __forceinline__ void ld16(const double* p, double (&o)[2]) {
+  const double2 t = *reinterpret_cast<const double2*>(p);
+  o[0] = t.x; o[1] = t.y;
+}
+// bfloat16 -> float32 is a 16-bit shift of the bit pattern
+__device__ __forceinline__ void ld16(const __nv_bfloat16* p, float (&o)[8]) {
+  const uint4 t = *reinterpret_cast<const uint4*>(p);
+  o[0] = __uint_as_float(t.x << 16); o[1] = __uint_as_float(t.x & 0xffff0000u);
+  o[2] = __uint_as_float(t.y << 16); o[3] = __uint_as_float(t.y & 0xffff0000u);
+  o[4] = __uint_as_float(t.z << 16); o[5] = __uint_as_float(t.z & 0xffff0000u);
+  o[6] = __uint_as_float(t.w << 16); o[7] = __uint_as_float(t.w & 0xffff0000u);
+}
+// V accumulation-type entries of a 16-byte aligned vector
+__device__ __forceinline__ void ldx(const float* p, float (&o)[4]) { ld16(p, o); }
+__device__ __forceinline__ void ldx(const double* p, double (&o)[2]) { ld16(p, o); }
+__device__ __forceinline__ void ldx(const float* p, float (&o)[8]) {
+  const float4 a = *reinterpret_cast<const float4*>(p);
+  const float4 b = *reinterpret_cast<const float4*>(p + 4);
+  o[0] = a.x; o[1] = a.y; o[2] = a.z; o[3] = a.w; o[4] = b.x; o[5] = b.y; o[6] = b.z; o[7] = b.w;
+}
+
+// out[j] = sum_i A[i*ld + j] x[i] for j < C (A' x), A with R rows.  Thread
+// (g, p) accumulates columns g*V .. g*V+V-1 over the p-th slice of the rows; the
+// slices are then added in a fixed order (deterministic).
 template <typename MT, typename AT>
-__device__ void matvec_t(const MT* A, int R, int C, const AT* x, AT* out, AT* part) {
+__device__ void matvec_t(const MT* A, int R, int C, int ld, const AT* x, AT* out, AT* part) {
+  constexpr int V = Vec<MT>::V;
   const int t = threadIdx.x;
-  if (C >= kThreads / 2) {
-    for (int j = t; j < C; j += kThreads) {
-      AT a0 = 0, a1 = 0, a2 = 0, a3 = 0;
-      int i = 0;
-      for (; i + 3 < R; i += 4) {
-        a0 += to_acc(A[(i + 0) * C + j]) * x[i + 0];
-        a1 += to_acc(A[(i + 1) * C + j]) * x[i + 1];
-        a2 += to_acc(A[(i + 2) * C + j]) * x[i + 2];
-        a3 += to_acc(A[(i + 3) * C + j]) * x[i + 3];
-      }
-      for (; i < R; ++i) a0 += to_acc(A[i * C + j]) * x[i];
-      out[j] = (a0 + a1) + (a2 + a3);
-    }
-    __syncthreads();
-    return;
-  }
-  int P = kThreads / C;
-  if (P > 8) P = 8;
+  const int G = ld / V;
+  int P = kThreads / G;
+  if (P > 16) P = 16;
   const int rc = (R + P - 1) / P;
-  if (t < P * C) {
-    const int j = t % C, p = t / C;
+  if (t < P * G) {
+    const int g = t % G, p = t / G;
     const int i0 = p * rc, i1 = min(R, i0 + rc);
-    AT a0 = 0, a1 = 0;
-    int i = i0;
-    for (; i + 1 < i1; i += 2) {
-      a0 += to_acc(A[i * C + j]) * x[i];
-      a1 += to_acc(A[(i + 1) * C + j]) * x[i + 1];
+    AT acc[V];
+#pragma unroll
+    for (int k = 0; k < V; ++k) acc[k] = 0;
+    const MT* col = A + g * V;
+#pragma unroll 4
+    for (int i = i0; i < i1; ++i) {
+      AT av[V];
+      ld16(col + (long long)i * ld, av);
+      const AT xi = x[i];
+#pragma unroll
+      for (int k = 0; k < V; ++k) acc[k] += av[k] * xi;
     }
-    if (i < i1) a0 += to_acc(A[i * C + j]) * x[i];
-    part[p * C + j] = a0 + a1;
+    AT* dst = part + p * ld + g * V;
+#pragma unroll
+    for (int k = 0; k < V; ++k) dst[k] = acc[k];
   }
   __syncthreads();
   for (int j = t; j < C; j += kThreads) {
+    AT v[16];
+#pragma unroll
+    for (int p = 0; p < 16; ++p) v[p] = p < P ? part[p * ld + j] : (AT)0;  // independent loads
     AT s = 0;
-    for (int p = 0; p < P; ++p) s += part[p * C + j];
+#pragma unroll
+    for (int p = 0; p < 16; ++p) s += v[p];  // fixed order: deterministic
     out[j] = s;
   }
   __syncthreads();
 }
 
-// out[i] = sum_j A[i*C + j] x[j] for i < R (A x).
+// out[i] = sum_j A[i*ld + j] x[j] for i < R (A x); x is 16-byte aligned with ld
+// entries, zero beyond the true width.
 template <typename MT, typename AT>
-__device__ void matvec_n(const MT* A, int R, int C, const AT* x, AT* out, AT* part) {
-  const int t = threadIdx.x;
-  if (R >= kThreads / 2) {
-    for (int i = t; i < R; i += kThreads) {
-      const MT* row = A + (long long)i * C;
-      AT a0 = 0, a1 = 0, a2 = 0, a3 = 0;
-      int j = 0;
-      for (; j + 3 < C; j += 4) {
-        a0 += to_acc(row[j + 0]) * x[j + 0];
-        a1 += to_acc(row[j + 1]) * x[j + 1];
-        a2 += to_acc(row[j + 2]) * x[j + 2];
-        a3 += to_acc(row[j + 3]) * x[j + 3];
+__device__ void matvec_n(const MT* A, int R, int ld, const AT* x, AT* out) {
+  constexpr int V = Vec<MT>::V;
+  const int G = ld / V;
+  for (int i = threadIdx.x; i < R; i += kThreads) {
+    const MT* row = A + (long long)i * ld;
+    AT acc0 = 0, acc1 = 0;
+#pragma unroll 4
+    for (int g = 0; g < G; ++g) {
+      AT av[V], xv[V];
+      ld16(row + g * V, av);
+      ldx(x + g * V, xv);
+#pragma unroll
+      for (int k = 0; k < V; k += 2) {
+        acc0 += av[k] * xv[k];
+        acc1 += av[k + 1] * xv[k + 1];
       }
-      for (; j < C; ++j) a0 += to_acc(row[j]) * x[j];
-      out[i] = (a0 + a1) + (a2 + a3);
     }
-    __syncthreads();
-    return;
-  }
-  int P = kThreads / R;
-  if (P > 8) P = 8;
-  const int cc = (C + P - 1) / P;
-  if (t < P * R) {
-    const int i = t % R, p = t / R;
-    const int j0 = p * cc, j1 = min(C, j0 + cc);
-    AT a0 = 0;
-    for (int j = j0; j < j1; ++j) a0 += to_acc(A[(long long)i * C + j]) * x[j];
-    part[p * R + i] = a0;
-  }
-  __syncthreads();
-  for (int i = t; i < R; i += kThreads) {
-    AT s = 0;
-    for (int p = 0; p < P; ++p) s += part[p * R + i];
-    out[i] = s;
+    out[i] = acc0 + acc1;
   }
   __syncthreads();
 }
 
 // ------------------------------------------------------------------ kernel state
-template <typename MT>
-struct Smem {
-  MT* K[4];
-  MT* Lm[4];
-  uint64_t* barK;
-  uint64_t* barL;
-  typename Acc<MT>::T* yv;    // n_k  [s; psi]
-  typename Acc<MT>::T* gv;    // n_v
-  typename Acc<MT>::T* rv;    // n_v
-  typename Acc<MT>::T* dv;    // n_v
-  typename Acc<MT>::T* sv;    // n_x
-  typename Acc<MT>::T* part;  // kThreads
-  double* red;                // 3 * kWarps
-  int* flag;                  // small ints
-};
+constexpr int kSeg = 32;  // chain nodes handled per block of the forward/prox phase
 
 inline __host__ __device__ long long round_up(long long v, long long m) { return (v + m - 1) / m * m; }
 
-// Padded sizes (entries) of the two matrices of a pack; multiples of 32 entries
-// keep every bulk copy 16-byte aligned for all element types.
-inline __host__ __device__ long long kpad(int n_k, int n_v) { return round_up((long long)n_k * n_v, 32); }
-inline __host__ __device__ long long lpad(int n_v) { return round_up((long long)n_v * n_v, 32); }
+// Pack of a node: [Bbar; L] (n_k rows) then Lambda/(2 p_n) (n_v rows), both with
+// the padded row stride row_stride<MT>(n_v); each matrix region is rounded to 32
+// entries so every bulk copy is 16-byte aligned and a multiple of 16 bytes long.
+template <typename MT>
+inline __host__ __device__ long long kpad(int n_k, int n_v) { return round_up((long long)n_k * row_stride<MT>(n_v), 32); }
+template <typename MT>
+inline __host__ __device__ long long lpad(int n_v) { return round_up((long long)n_v * row_stride<MT>(n_v), 32); }
+
+template <typename MT>
+inline __host__ __device__ int part_entries(int n_v) {
+  const int ld = row_stride<MT>(n_v);
+  const int a = 16 * ld, b = 2 * kSeg * kWarps;
+  return a > b ? a : b;
+}
 
 template <typename MT>
 __host__ __device__ size_t vec_smem_bytes(int n_x, int n_u, int n_v) {
   using AT = typename Acc<MT>::T;
-  const int n_k = n_x + n_u;
-  size_t v = (size_t)(n_k + 3 * n_v + n_x + kThreads) * sizeof(AT);
+  const int n_k = n_x + n_u, ld = row_stride<MT>(n_v);
+  size_t v = round_up((size_t)ld * sizeof(AT), 16);
+  v += (size_t)(n_k + 2 * ld + part_entries<MT>(n_v)) * sizeof(AT);
   v = round_up(v, 16);
-  v += 3 * kWarps * sizeof(double) + 16 * sizeof(int);
+  v += 3 * kWarps * sizeof(double) + (kSeg + 8) * sizeof(int);
   return round_up(v, 128);
 }
+
+template <typename MT>
+__host__ __device__ size_t iter_smem_bytes(int S, int n_x, int n_u, int n_v) {
+  size_t m = (size_t)S * (kpad<MT>(n_x + n_u, n_v) + lpad<MT>(n_v)) * sizeof(MT);
+  m = round_up(m, 16) + 8 * sizeof(uint64_t);
+  m = round_up(m, 16);
+  return m + vec_smem_bytes<MT>(n_x, n_u, n_v);
+}
+
+template <typename MT>
+struct Smem {
+  using AT = typename Acc<MT>::T;
+  unsigned char* base;  // S K-slots, then S Lambda-slots
+  size_t kbytes, lbytes;
+  int S;
+  uint64_t* barK;  // [4]
+  uint64_t* barL;  // [4]
+  int ld;          // padded row stride of the matrices
+  AT* dv;          // ld, 16-byte aligned, zero beyond n_v
+  AT* yv;          // n_k
+  AT* gv;          // ld
+  AT* rv;          // ld
+  AT* part;        // part_entries: mat-vec slices
+  AT* red;         // aliases part: per node, per warp, the two block norms
+  double* res3;    // 3 * kWarps
+  int* seg;        // kSeg node ids
+  int* flag;       // 8 ints
+  __device__ MT* K(int s) const { return reinterpret_cast<MT*>(base + (size_t)s * kbytes); }
+  __device__ MT* Lm(int s) const { return reinterpret_cast<MT*>(base + (size_t)S * kbytes + (size_t)s * lbytes); }
+};
 
 template <typename MT>
 __device__ Smem<MT> carve(unsigned char* base, int S, int n_x, int n_u, int n_v) {
   using AT = typename Acc<MT>::T;
   Smem<MT> s;
   const int n_k = n_x + n_u;
-  size_t off = 0;
-  for (int i = 0; i < S; ++i) {
-    s.K[i] = reinterpret_cast<MT*>(base + off);
-    off += kpad(n_k, n_v) * sizeof(MT);
-  }
-  for (int i = 0; i < S; ++i) {
-    s.Lm[i] = reinterpret_cast<MT*>(base + off);
-    off += lpad(n_v) * sizeof(MT);
-  }
-  off = round_up(off, 16);
+  s.base = base;
+  s.S = S;
+  s.ld = row_stride<MT>(n_v);
+  s.kbytes = kpad<MT>(n_k, n_v) * sizeof(MT);
+  s.lbytes = lpad<MT>(n_v) * sizeof(MT);
+  size_t off = round_up((size_t)S * (s.kbytes + s.lbytes), 16);
   s.barK = reinterpret_cast<uint64_t*>(base + off);
   off += 4 * sizeof(uint64_t);
   s.barL = reinterpret_cast<uint64_t*>(base + off);
   off += 4 * sizeof(uint64_t);
   off = round_up(off, 16);
+  s.dv = reinterpret_cast<AT*>(base + off);
+  off += round_up((size_t)s.ld * sizeof(AT), 16);
   AT* v = reinterpret_cast<AT*>(base + off);
   s.yv = v;
   v += n_k;
   s.gv = v;
-  v += n_v;
+  v += s.ld;
   s.rv = v;
-  v += n_v;
-  s.dv = v;
-  v += n_v;
-  s.sv = v;
-  v += n_x;
+  v += s.ld;
   s.part = v;
-  v += kThreads;
+  s.red = v;
+  v += part_entries<MT>(n_v);
   off = round_up(reinterpret_cast<unsigned char*>(v) - base, 16);
-  s.red = reinterpret_cast<double*>(base + off);
+  s.res3 = reinterpret_cast<double*>(base + off);
   off += 3 * kWarps * sizeof(double);
-  s.flag = reinterpret_cast<int*>(base + off);
+  s.seg = reinterpret_cast<int*>(base + off);
+  s.flag = s.seg + kSeg;
   return s;
-}
-
-template <typename MT>
-__host__ __device__ size_t iter_smem_bytes(int S, int n_x, int n_u, int n_v) {
-  size_t m = (size_t)S * (kpad(n_x + n_u, n_v) + lpad(n_v)) * sizeof(MT);
-  m = round_up(m, 16) + 8 * sizeof(uint64_t);
-  m = round_up(m, 16);
-  return m + vec_smem_bytes<MT>(n_x, n_u, n_v);
 }
 
 // Per-CTA cursor over the nodes of its chains, in backward (bottom-up) order.
@@ -295,9 +340,12 @@ struct Cursor {
   int k;      // position inside the chain (top-down index), counting down
 };
 
+// Load pipeline.  Every thread keeps an identical copy; thread 0 issues the copies.
+// A load with sequence number q uses slot q % S and completes phase (q / S) of it.
 struct Pipe {
-  Cursor next_k, next_l;  // next node whose K / Lambda load is to be issued
-  uint32_t issued_k, issued_l, used;
+  Cursor kcur, lcur;                // next chain node whose K / Lambda load is issued
+  int knode, lnode;                 // thread 0: node id at kcur / lcur, loaded one issue ahead
+  uint32_t kiss, kuse, liss, luse;  // issued / consumed sequence numbers
 };
 
 template <typename VT, typename MT>
@@ -307,6 +355,8 @@ struct Kern {
   Smem<MT>& sm;
   int S, nu, mode;
   int nd;  // dual block 2 n_x + n_u
+  bool abort_ = false;
+  double rmax = 0, hzmax = 0, tmax = 0, pnrm = 0, pdot = 0;
 
   __device__ Kern(const IterArgs& args, Smem<MT>& s, int S_, int nu_, int mode_)
       : a(args), sm(s), S(S_), nu(nu_), mode(mode_), nd(2 * args.n_x + args.n_u) {}
@@ -322,304 +372,487 @@ struct Kern {
   __device__ bool linear() const { return (mode & MODE_LINEAR) != 0; }
 
   // ---------------------------------------------------------- cursor helpers
-  __device__ Cursor first_cursor() const {
+  __device__ Cursor chain_cursor(int chain) const {
     Cursor c;
-    c.chain = blockIdx.x;
-    if (c.chain >= a.n_chains) {
-      c.chain = -1;
-      c.k = 0;
-      return c;
-    }
-    c.k = a.chain_off[c.chain + 1] - a.chain_off[c.chain] - 1;
+    c.chain = chain < a.n_chains ? chain : -1;
+    c.k = c.chain >= 0 ? a.chain_off[c.chain + 1] - a.chain_off[c.chain] - 1 : 0;
     return c;
   }
   __device__ void advance(Cursor& c) const {
     if (c.chain < 0) return;
-    if (--c.k < 0) {
-      c.chain += gridDim.x;
-      if (c.chain >= a.n_chains) {
-        c.chain = -1;
-        return;
-      }
-      c.k = a.chain_off[c.chain + 1] - a.chain_off[c.chain] - 1;
-    }
+    if (--c.k < 0) c = chain_cursor(c.chain + gridDim.x);
   }
   __device__ int node_of(const Cursor& c) const { return a.chain_node[a.chain_off[c.chain] + c.k]; }
 
-  // thread 0 only
-  __device__ void issue_k(Pipe& p) {
-    if (p.next_k.chain < 0) return;
-    const int slot = p.issued_k % S;
-    const int n = node_of(p.next_k);
-    const uint32_t bytes = (uint32_t)(kpad(a.n_k, a.n_v) * sizeof(MT));
+  // ---------------------------------------------------------- pipeline (uniform calls)
+  __device__ void copy_k(uint32_t seq, int n) {
+    const int slot = seq % S;
+    const uint32_t bytes = (uint32_t)sm.kbytes;
     mbar_expect_tx(&sm.barK[slot], bytes);
     const unsigned char* src = reinterpret_cast<const unsigned char*>(pack(n));
-    unsigned char* dst = reinterpret_cast<unsigned char*>(sm.K[slot]);
+    unsigned char* dst = reinterpret_cast<unsigned char*>(sm.K(slot));
     for (uint32_t o = 0; o < bytes; o += kChunk) bulk_g2s(dst + o, src + o, min((uint32_t)kChunk, bytes - o), &sm.barK[slot]);
-    ++p.issued_k;
-    advance(p.next_k);
+  }
+  __device__ void copy_l(uint32_t seq, int n) {
+    const int slot = seq % S;
+    const uint32_t bytes = (uint32_t)sm.lbytes;
+    mbar_expect_tx(&sm.barL[slot], bytes);
+    const unsigned char* src = reinterpret_cast<const unsigned char*>(pack(n) + kpad<MT>(a.n_k, a.n_v));
+    unsigned char* dst = reinterpret_cast<unsigned char*>(sm.Lm(slot));
+    for (uint32_t o = 0; o < bytes; o += kChunk) bulk_g2s(dst + o, src + o, min((uint32_t)kChunk, bytes - o), &sm.barL[slot]);
+  }
+  // Thread 0 reads the node id of the next copy right after issuing one, so the
+  // global-memory latency of that read is spent while the node is being processed.
+  __device__ void set_cursors(Pipe& p, Cursor c) {
+    p.kcur = p.lcur = c;
+    if (threadIdx.x == 0) p.knode = p.lnode = c.chain >= 0 ? node_of(c) : -1;
+  }
+  __device__ void issue_k(Pipe& p) {
+    if (p.kcur.chain < 0) return;
+    if (threadIdx.x == 0) {
+      fence_proxy_async();
+      copy_k(p.kiss, p.knode);
+    }
+    ++p.kiss;
+    advance(p.kcur);
+    if (threadIdx.x == 0 && p.kcur.chain >= 0) p.knode = node_of(p.kcur);
   }
   __device__ void issue_l(Pipe& p) {
-    if (p.next_l.chain < 0) return;
-    const int slot = p.issued_l % S;
-    const int n = node_of(p.next_l);
-    const uint32_t bytes = (uint32_t)(lpad(a.n_v) * sizeof(MT));
-    mbar_expect_tx(&sm.barL[slot], bytes);
-    const unsigned char* src = reinterpret_cast<const unsigned char*>(pack(n) + kpad(a.n_k, a.n_v));
-    unsigned char* dst = reinterpret_cast<unsigned char*>(sm.Lm[slot]);
-    for (uint32_t o = 0; o < bytes; o += kChunk) bulk_g2s(dst + o, src + o, min((uint32_t)kChunk, bytes - o), &sm.barL[slot]);
-    ++p.issued_l;
-    advance(p.next_l);
+    if (p.lcur.chain < 0) return;
+    if (threadIdx.x == 0) {
+      fence_proxy_async();
+      copy_l(p.liss, p.lnode);
+    }
+    ++p.liss;
+    advance(p.lcur);
+    if (threadIdx.x == 0 && p.lcur.chain >= 0) p.lnode = node_of(p.lcur);
+  }
+  __device__ void prime(Pipe& p) {
+    for (int s = 0; s < S; ++s) {
+      issue_k(p);
+      issue_l(p);
+    }
+  }
+  // wait for the next K (resp. Lambda) load; returns its slot; sets abort_ on timeout
+  __device__ int wait_k(Pipe& p) {
+    const int slot = p.kuse % S;
+    const bool ok = mbar_wait(&sm.barK[slot], (p.kuse / S) & 1);
+    ++p.kuse;
+    if (__syncthreads_or(!ok)) fail();
+    return slot;
+  }
+  __device__ int wait_l(Pipe& p) {
+    const int slot = p.luse % S;
+    const bool ok = mbar_wait(&sm.barL[slot], (p.luse / S) & 1);
+    ++p.luse;
+    if (__syncthreads_or(!ok)) fail();
+    return slot;
+  }
+  // let every issued copy land (bounded), forget them, and restart issuing at `next`
+  __device__ void flush(Pipe& p, Cursor next) {
+    bool ok = true;
+    for (; p.kuse < p.kiss; ++p.kuse) ok &= mbar_wait(&sm.barK[p.kuse % S], (p.kuse / S) & 1);
+    for (; p.luse < p.liss; ++p.luse) ok &= mbar_wait(&sm.barL[p.luse % S], (p.luse / S) & 1);
+    set_cursors(p, next);
+    if (__syncthreads_or(!ok)) fail();
+  }
+  __device__ void fail() {
+    if (threadIdx.x == 0) a.flags[1] = SMPC_ETIMEOUT;
+    abort_ = true;
   }
 
   // ---------------------------------------------------------- forward + prox
-  // Path sums of the forward sweep for node `top` (inclusive) into thread-owned
-  // accumulators: entry idx < n_x -> (V, X) of the states, else U of the inputs.
-  __device__ void path_init(int node_or_neg, int idx, AT& V, AT& X, AT& U) const {
+  // Path sums down to node `par` (inclusive) for entry e: states (V = Bbar v, X = x)
+  // or inputs (U = L v).
+  __device__ void path_init(int par, int e, AT& V, AT& X, AT& U) const {
     V = 0;
     U = 0;
-    X = (idx < a.n_x && !linear()) ? (AT)cv(a.p0)[idx] : (AT)0;
-    if (node_or_neg < 0) return;
-    const int b = a.path_off[node_or_neg], e = a.path_off[node_or_neg + 1];
-    for (int q = b; q < e; ++q) step_forward(a.path_node[q], idx, V, X, U);
-  }
-  __device__ void step_forward(int m, int idx, AT& V, AT& X, AT& U) const {
-    const VT* hm = hb() + (long long)m * a.n_k;
-    if (idx < a.n_x) {
-      V += (AT)hm[idx];
-      X += V + (linear() ? (AT)0 : (AT)cv(a.e)[(long long)m * a.n_x + idx]);
-    } else {
-      U += (AT)hm[idx];
-    }
-  }
-  __device__ void write_z(int m, int idx, AT X, AT U) const {
-    if (idx < a.n_x)
-      mv(a.xout)[(long long)m * a.n_x + idx] = (VT)X;
-    else {
-      const int i = idx - a.n_x;
-      mv(a.uout)[(long long)m * a.n_u + i] =
-          (VT)(U + (linear() ? (AT)0 : (AT)cv(a.uhat)[(long long)m * a.n_u + i]));
-    }
-  }
-
-  // Prox, dual update and next extrapolation of node m by one warp.
-  // Iteration it = nu - 1: reads y^{it} (buffer it) and y^{it-1} (buffer it+1),
-  // writes y^{it+1} into buffer it+1 and w^{it+1} (xi, psi) into wbuf.
-  __device__ void prox_node(int m, int lane, double& rmax, double& hzmax, double& tmax) {
-    const int it = nu - 1;
-    VT* y1 = y(it) + (long long)m * nd;
-    VT* y2 = y(it + 1) + (long long)m * nd;
-    const VT* xo = cv(a.xout) + (long long)m * a.n_x;
-    const VT* uo = cv(a.uout) + (long long)m * a.n_u;
-    VT* wm = wb() + (long long)m * a.n_k;
-    if (linear()) {
-      // power iteration: y_{k+1} = -D^{1/2} H z ; accumulate norms
-      const AT ss = sqrt((AT)cv(a.step_s)[m]), sz = sqrt((AT)cv(a.step_z)[m]);
-      double nrm = 0, dot = 0;
-      for (int i = lane; i < a.n_x; i += 32) {
-        const AT x = (AT)xo[i];
-        const AT a1 = -ss * x, a2 = -sz * x;
-        dot += (double)a1 * (double)y1[i] + (double)a2 * (double)y1[a.n_x + i];
-        y2[i] = (VT)a1;
-        y2[a.n_x + i] = (VT)a2;
-        nrm += (double)a1 * a1 + (double)a2 * a2;
-      }
-      for (int i = lane; i < a.n_u; i += 32) {
-        const AT u = (AT)uo[i];
-        const AT a3 = -sqrt((AT)cv(a.step_p)[(long long)m * a.n_u + i]) * u;
-        dot += (double)a3 * (double)y1[2 * a.n_x + i];
-        y2[2 * a.n_x + i] = (VT)a3;
-        nrm += (double)a3 * a3;
-      }
-      nrm = warp_sum(nrm);
-      dot = warp_sum(dot);
-      if (lane == 0) {
-        atomicAdd(&a.pw[it + 1], nrm);
-        atomicAdd(&a.pw[a.pw_len + it], dot);
-      }
-      return;
-    }
-    const AT c = (AT)a.cvec[it];
-    const AT cn = (AT)a.cvec[it + 1];
-    const AT ls = (AT)cv(a.step_s)[m], lz = (AT)cv(a.step_z)[m];
-    const AT mu = (AT)cv(a.mu_s)[m];
-    const VT* xs = cv(a.x_s);
-    const VT* xlo = cv(a.x_min);
-    const VT* xhi = cv(a.x_max);
-    AT d2s = 0, d2z = 0;
-    for (int i = lane; i < a.n_x; i += 32) {
-      const AT x = (AT)xo[i];
-      const AT ws = (AT)y1[i] + c * ((AT)y1[i] - (AT)y2[i]);
-      const AT wz = (AT)y1[a.n_x + i] + c * ((AT)y1[a.n_x + i] - (AT)y2[a.n_x + i]);
-      const AT vs = ws / ls + x, vz = wz / lz + x;
-      const AT Ps = fmax(vs, (AT)xs[i]);
-      const AT Pz = fmin(fmax(vz, (AT)xlo[i]), (AT)xhi[i]);
-      d2s += (vs - Ps) * (vs - Ps);
-      d2z += (vz - Pz) * (vz - Pz);
-    }
-    d2s = warp_sum(d2s);
-    d2z = warp_sum(d2z);
-    const AT ds = sqrt(d2s), dz = sqrt(d2z);
-    const AT ths = mu / ls, thz = (AT)a.gamma_d / lz;
-    const bool fs = ds > ths, fz = dz > thz;
-    const AT ks = fs ? ths / ds : (AT)0, kz = fz ? thz / dz : (AT)0;
-    bool bad = false;
-    for (int i = lane; i < a.n_x; i += 32) {
-      const AT x = (AT)xo[i];
-      const AT y1s = (AT)y1[i], y1z = (AT)y1[a.n_x + i];
-      const AT ws = y1s + c * (y1s - (AT)y2[i]);
-      const AT wz = y1z + c * (y1z - (AT)y2[a.n_x + i]);
-      const AT vs = ws / ls + x, vz = wz / lz + x;
-      const AT Ps = fmax(vs, (AT)xs[i]);
-      const AT Pz = fmin(fmax(vz, (AT)xlo[i]), (AT)xhi[i]);
-      const AT ts = fs ? vs + ks * (Ps - vs) : Ps;
-      const AT tz = fz ? vz + kz * (Pz - vz) : Pz;
-      const AT ysn = ws + ls * (x - ts);
-      const AT yzn = wz + lz * (x - tz);
-      y2[i] = (VT)ysn;
-      y2[a.n_x + i] = (VT)yzn;
-      rmax = fmax(rmax, (double)fmax(fabs(x - ts), fabs(x - tz)));
-      hzmax = fmax(hzmax, (double)fabs(x));
-      tmax = fmax(tmax, (double)fmax(fabs(ts), fabs(tz)));
-      const AT wsn = ysn + cn * (ysn - y1s);
-      const AT wzn = yzn + cn * (yzn - y1z);
-      wm[i] = (VT)(wsn + wzn);
-      bad |= !isfinite(ysn) || !isfinite(yzn);
-    }
-    const VT* ulo = cv(a.u_min);
-    const VT* uhi = cv(a.u_max);
-    const VT* lp = cv(a.step_p) + (long long)m * a.n_u;
-    for (int i = lane; i < a.n_u; i += 32) {
-      const AT u = (AT)uo[i];
-      const AT y1p = (AT)y1[2 * a.n_x + i];
-      const AT wp = y1p + c * (y1p - (AT)y2[2 * a.n_x + i]);
-      const AT l = (AT)lp[i];
-      const AT vp = wp / l + u;
-      const AT tp = fmin(fmax(vp, (AT)ulo[i]), (AT)uhi[i]);
-      const AT ypn = wp + l * (u - tp);
-      y2[2 * a.n_x + i] = (VT)ypn;
-      rmax = fmax(rmax, (double)fabs(u - tp));
-      hzmax = fmax(hzmax, (double)fabs(u));
-      tmax = fmax(tmax, (double)fabs(tp));
-      wm[a.n_x + i] = (VT)(ypn + cn * (ypn - y1p));
-      bad |= !isfinite(ypn);
-    }
-    if (bad) a.flags[1] = SMPC_EDIVERGED;
-  }
-
-  // w^nu of node m without a prox (first iteration, or power iteration).
-  __device__ void w_only_node(int m, int idx0, int stride) {
-    VT* wm = wb() + (long long)m * a.n_k;
-    if (linear()) {
-      const double inv = rsqrt(a.pw[nu]);
-      const VT* yk = y(nu) + (long long)m * nd;
-      for (int idx = idx0; idx < a.n_k; idx += stride) {
-        AT w;
-        if (idx < a.n_x) {
-          w = sqrt((AT)cv(a.step_s)[m]) * (AT)yk[idx] + sqrt((AT)cv(a.step_z)[m]) * (AT)yk[a.n_x + idx];
-        } else {
-          const int i = idx - a.n_x;
-          w = sqrt((AT)cv(a.step_p)[(long long)m * a.n_u + i]) * (AT)yk[2 * a.n_x + i];
-        }
-        wm[idx] = (VT)(w * (AT)inv);
-      }
-      return;
-    }
-    const AT c = (AT)a.cvec[nu];
-    const VT* ya = y(nu) + (long long)m * nd;
-    const VT* yb = y(nu + 1) + (long long)m * nd;
-    for (int idx = idx0; idx < a.n_k; idx += stride) {
-      AT w;
-      if (idx < a.n_x) {
-        const AT s1 = (AT)ya[idx], z1 = (AT)ya[a.n_x + idx];
-        w = (s1 + c * (s1 - (AT)yb[idx])) + (z1 + c * (z1 - (AT)yb[a.n_x + idx]));
+    X = (e < a.n_x && !linear()) ? (AT)cv(a.p0)[e] : (AT)0;
+    if (par < 0) return;
+    const int b = a.path_off[par], en = a.path_off[par + 1];
+    for (int q = b; q < en; ++q) {
+      const int m = a.path_node[q];
+      const AT hv = (AT)hb()[(long long)m * a.n_k + e];
+      if (e < a.n_x) {
+        V += hv;
+        X += V + (linear() ? (AT)0 : (AT)cv(a.e)[(long long)m * a.n_x + e]);
       } else {
-        const int i = idx - a.n_x;
-        const AT p1 = (AT)ya[2 * a.n_x + i];
-        w = p1 + c * (p1 - (AT)yb[2 * a.n_x + i]);
+        U += hv;
       }
-      wm[idx] = (VT)w;
     }
   }
 
-  // ---------------------------------------------------------- backward pieces
-  // r := r + [Bbar; L]' yv (K in A), publish, delta = Lam r, h = K delta.
-  __device__ void node_tail(int m, const MT* K, const MT* Lam) {
-    matvec_t<MT, AT>(K, a.n_k, a.n_v, sm.yv, sm.gv, sm.part);
-    for (int j = threadIdx.x; j < a.n_v; j += kThreads) sm.rv[j] += sm.gv[j];
-    __syncthreads();
-    matvec_t<MT, AT>(Lam, a.n_v, a.n_v, sm.rv, sm.dv, sm.part);  // Lambda symmetric
+  // Forward sweep, prox, dual update and next extrapolation for the segment
+  // nodes[0..len) (a chain top-down, or one top node) below node `par`.
+  // Thread e owns entry e of [x (n_x); u (n_u)]: its tank's two distance-block
+  // entries, or its input's box entry.  Loads are batched kB nodes at a time so
+  // that their latencies overlap.
+  //
+  // Prox arithmetic (App. C) in a cancellation-free form.  With a = w / lambda and
+  // v = a + x, each entry of r = v - P_C(v) is max(a + (x - hi), 0) - max((lo - x) - a, 0),
+  // exactly zero where the entry is inside the box.  With kappa = min(1, theta / ||r||)
+  // (theta = mu / lambda) the prox is t = v - kappa r, hence
+  //   y+ = w + lambda (x - t) = lambda kappa r,
+  //   x - t = -a                             inside,
+  //         = (kappa - 1) a + kappa (x - bound)  at the violated bound,
+  // which is the same arithmetic as App. C without forming w / lambda + x and
+  // subtracting it again (w / lambda can exceed x by many orders of magnitude).
+  static constexpr int kB = 8;
+  __device__ static AT box_r(AT a, AT x, AT lo, AT hi) {
+    return fmax(a + (x - hi), (AT)0) - fmax((lo - x) - a, (AT)0);
   }
-
-  // Process top node t with the whole CTA (its children are complete).
-  __device__ void process_top(int t) {
-    const MT* K = pack(t);
-    const MT* Lam = K + kpad(a.n_k, a.n_v);
-    const int cb = a.child_begin[t], cc = a.child_count[t];
-    const VT* wt = wb() + (long long)t * a.n_k;
-    for (int idx = threadIdx.x; idx < a.n_k; idx += kThreads) {
-      AT v = (AT)ldcg(wt + idx);
-      if (idx < a.n_x) {
-        for (int c = cb; c < cb + cc; ++c) v += (AT)ldcg(mv(a.spub) + (long long)c * a.n_x + idx);
-        sm.sv[idx] = v;
-      }
-      sm.yv[idx] = v;
-    }
-    for (int j = threadIdx.x; j < a.n_v; j += kThreads) {
-      AT r = linear() ? (AT)0 : (AT)cv(a.beta)[(long long)t * a.n_v + j];
-      for (int c = cb; c < cb + cc; ++c) r += (AT)ldcg(mv(a.rpub) + (long long)c * a.n_v + j);
-      sm.rv[j] = r;
-    }
-    __syncthreads();
-    node_tail(t, K, Lam);
-    for (int i = threadIdx.x; i < a.n_x; i += kThreads) mv(a.spub)[(long long)t * a.n_x + i] = (VT)sm.sv[i];
-    for (int j = threadIdx.x; j < a.n_v; j += kThreads) mv(a.rpub)[(long long)t * a.n_v + j] = (VT)sm.rv[j];
-    matvec_n<MT, AT>(K, a.n_k, a.n_v, sm.dv, sm.yv, sm.part);
-    for (int i = threadIdx.x; i < a.n_k; i += kThreads) hb()[(long long)t * a.n_k + i] = (VT)sm.yv[i];
-    __syncthreads();
+  __device__ static AT box_res(AT a, AT r, AT kappa, AT x, AT lo, AT hi) {
+    if (r > 0) return (kappa - 1) * a + kappa * (x - hi);
+    if (r < 0) return (kappa - 1) * a + kappa * (x - lo);
+    return -a;
   }
-
-  // Arrive at top node t; while this CTA is the last arrival, process and climb.
-  __device__ void arrive_and_climb(int t) {
-    while (t >= 0) {
+  __device__ void phase_p(int par, const int* nodes, int len) {
+    const int e = threadIdx.x, lane = e & 31, warp = e >> 5;
+    const bool tank = e < a.n_x, input = !tank && e < a.n_k;
+    const int i = e - a.n_x;
+    const bool lin = linear();
+    const int it = nu - 1;  // iteration being finished
+    const AT c = lin ? (AT)0 : (AT)a.cvec[it];
+    const AT cn = lin ? (AT)0 : (AT)a.cvec[it + 1];
+    const AT inf = (AT)INFINITY;
+    const VT* __restrict__ Hb = hb();
+    VT* Y1 = y(it);       // y^{it}
+    VT* Y2 = y(it + 1);   // y^{it-1} in, y^{it+1} out
+    VT* __restrict__ Xo = mv(a.xout);
+    VT* __restrict__ Uo = mv(a.uout);
+    AT V = 0, X = 0, U = 0;
+    if (e < a.n_k) path_init(par, e, V, X, U);
+    const AT xs = tank ? (AT)cv(a.x_s)[e] : (AT)0;
+    const AT xlo = tank ? (AT)cv(a.x_min)[e] : (AT)0;
+    const AT xhi = tank ? (AT)cv(a.x_max)[e] : (AT)0;
+    const AT ulo = input ? (AT)cv(a.u_min)[i] : (AT)0;
+    const AT uhi = input ? (AT)cv(a.u_max)[i] : (AT)0;
+    const int tank_warps = (a.n_x + 31) / 32;
+    AT rm = 0, hm = 0, tm = 0;
+    for (int b0 = 0; b0 < len; b0 += kSeg) {
+      const int bl = min(kSeg, len - b0);
+      if (e < bl) sm.seg[e] = nodes[b0 + e];
       __syncthreads();
-      if (threadIdx.x == 0) {
-        __threadfence();
-        const int old = atomicAdd(&a.counters[t], 1);
-        const int last = (old == a.top_expect[t] - 1);
-        if (last) {
-          a.counters[t] = 0;  // nobody else touches it again in this launch
-          __threadfence();
+      // pass A: forward sweep (prefix sums of h) and the two block distances per node
+      for (int k0 = 0; k0 < bl; k0 += kB) {
+        const int q = min(kB, bl - k0);
+        AT hv[kB], ev[kB], s1[kB], s2[kB], z1[kB], z2[kB], isv[kB], izv[kB];
+#pragma unroll
+        for (int r = 0; r < kB; ++r) {
+          hv[r] = ev[r] = s1[r] = s2[r] = z1[r] = z2[r] = 0;
+          isv[r] = izv[r] = 1;
+          if (r < q && e < a.n_k) {
+            const int m = sm.seg[k0 + r];
+            hv[r] = (AT)Hb[(long long)m * a.n_k + e];
+            if (tank) {
+              if (!lin) {
+                ev[r] = (AT)cv(a.e)[(long long)m * a.n_x + e];
+                const VT* y1 = Y1 + (long long)m * nd;
+                const VT* y2 = Y2 + (long long)m * nd;
+                s1[r] = (AT)y1[e];
+                s2[r] = (AT)y2[e];
+                z1[r] = (AT)y1[a.n_x + e];
+                z2[r] = (AT)y2[a.n_x + e];
+                isv[r] = (AT)cv(a.inv_s)[m];
+                izv[r] = (AT)cv(a.inv_z)[m];
+              }
+            } else if (!lin) {
+              ev[r] = (AT)cv(a.uhat)[(long long)m * a.n_u + i];
+            }
+          }
         }
-        sm.flag[0] = last;
+#pragma unroll
+        for (int r = 0; r < kB; ++r) {
+          if (r < q) {
+            const int m = sm.seg[k0 + r];
+            AT ps = 0, pz = 0;
+            if (tank) {
+              V += hv[r];
+              X += V + ev[r];
+              Xo[(long long)m * a.n_x + e] = (VT)X;
+              if (!lin) {
+                const AT as = (s1[r] + c * (s1[r] - s2[r])) * isv[r];
+                const AT az = (z1[r] + c * (z1[r] - z2[r])) * izv[r];
+                const AT rs = box_r(as, X, xs, inf), rz = box_r(az, X, xlo, xhi);
+                ps = rs * rs;
+                pz = rz * rz;
+              }
+            } else if (input) {
+              U += hv[r];
+              Uo[(long long)m * a.n_u + i] = (VT)(U + ev[r]);
+            }
+            if (!lin && warp < tank_warps) {  // only warps holding tank entries contribute
+              ps = warp_sum(ps);
+              pz = warp_sum(pz);
+              if (lane == 0) {
+                sm.red[((k0 + r) * kWarps + warp) * 2 + 0] = ps;
+                sm.red[((k0 + r) * kWarps + warp) * 2 + 1] = pz;
+              }
+            }
+          }
+        }
       }
       __syncthreads();
-      if (!sm.flag[0]) return;
-      process_top(t);
-      t = a.parent[t];
+      // pass B: prox (App. C), dual update, extrapolation w^{it+1}
+      if (e < a.n_k) {
+        for (int k0 = 0; k0 < bl; k0 += kB) {
+          const int q = min(kB, bl - k0);
+          AT zv[kB], v1[kB], v2[kB], w1[kB], w2[kB], l1[kB], l2[kB], i1[kB], i2[kB], t1[kB], t2[kB];
+#pragma unroll
+          for (int r = 0; r < kB; ++r) {
+            zv[r] = v1[r] = v2[r] = w1[r] = w2[r] = t1[r] = t2[r] = 0;
+            l1[r] = l2[r] = i1[r] = i2[r] = 1;
+            if (r < q) {
+              const int m = sm.seg[k0 + r];
+              const VT* y1 = Y1 + (long long)m * nd;
+              const VT* y2 = Y2 + (long long)m * nd;
+              if (tank) {
+                zv[r] = (AT)Xo[(long long)m * a.n_x + e];
+                v1[r] = (AT)y1[e];
+                v2[r] = (AT)y2[e];
+                w1[r] = (AT)y1[a.n_x + e];
+                w2[r] = (AT)y2[a.n_x + e];
+                l1[r] = (AT)cv(a.step_s)[m];
+                l2[r] = (AT)cv(a.step_z)[m];
+                if (!lin) {
+                  i1[r] = (AT)cv(a.inv_s)[m];
+                  i2[r] = (AT)cv(a.inv_z)[m];
+                  t1[r] = (AT)cv(a.thr_s)[m];
+                  t2[r] = (AT)cv(a.thr_z)[m];
+                }
+              } else {
+                zv[r] = (AT)Uo[(long long)m * a.n_u + i];
+                v1[r] = (AT)y1[2 * a.n_x + i];
+                v2[r] = (AT)y2[2 * a.n_x + i];
+                l1[r] = (AT)cv(a.step_p)[(long long)m * a.n_u + i];
+                if (!lin) i1[r] = (AT)cv(a.inv_p)[(long long)m * a.n_u + i];
+              }
+            }
+          }
+#pragma unroll
+          for (int r = 0; r < kB; ++r) {
+            if (r >= q) continue;
+            const int k = k0 + r;
+            const int m = sm.seg[k];
+            VT* y2 = Y2 + (long long)m * nd;
+            VT* wm = wb() + (long long)m * a.n_k;
+            if (lin) {
+              // power iteration: y_{k+1} = -D^{1/2} H z, with D held in the step arrays
+              if (tank) {
+                const AT a1 = -sqrt(l1[r]) * zv[r], a2 = -sqrt(l2[r]) * zv[r];
+                pdot += (double)a1 * (double)v1[r] + (double)a2 * (double)w1[r];
+                pnrm += (double)a1 * a1 + (double)a2 * a2;
+                y2[e] = (VT)a1;
+                y2[a.n_x + e] = (VT)a2;
+              } else {
+                const AT a3 = -sqrt(l1[r]) * zv[r];
+                pdot += (double)a3 * (double)v1[r];
+                pnrm += (double)a3 * a3;
+                y2[2 * a.n_x + i] = (VT)a3;
+              }
+              continue;
+            }
+            if (tank) {
+              AT ds2 = 0, dz2 = 0;
+              for (int w = 0; w < tank_warps; ++w) {
+                ds2 += sm.red[(k * kWarps + w) * 2 + 0];
+                dz2 += sm.red[(k * kWarps + w) * 2 + 1];
+              }
+              const AT ds = sqrt(ds2), dz = sqrt(dz2);
+              const AT ks = ds > t1[r] ? t1[r] / ds : (AT)1;
+              const AT kz = dz > t2[r] ? t2[r] / dz : (AT)1;
+              const AT x = zv[r];
+              const AT ws = v1[r] + c * (v1[r] - v2[r]);
+              const AT wz = w1[r] + c * (w1[r] - w2[r]);
+              const AT as = ws * i1[r], az = wz * i2[r];
+              const AT rs = box_r(as, x, xs, inf), rz = box_r(az, x, xlo, xhi);
+              const AT es = box_res(as, rs, ks, x, xs, inf), ez = box_res(az, rz, kz, x, xlo, xhi);
+              const AT ysn = l1[r] * ks * rs;
+              const AT yzn = l2[r] * kz * rz;
+              y2[e] = (VT)ysn;
+              y2[a.n_x + e] = (VT)yzn;
+              wm[e] = (VT)((ysn + cn * (ysn - v1[r])) + (yzn + cn * (yzn - w1[r])));
+              rm = fmax(rm, fmax(fabs(es), fabs(ez)));
+              hm = fmax(hm, fabs(x));
+              tm = fmax(tm, fmax(fabs(x - es), fabs(x - ez)));
+              if (!isfinite(ysn) || !isfinite(yzn)) a.flags[1] = SMPC_EDIVERGED;
+            } else {
+              const AT u = zv[r];
+              const AT wp = v1[r] + c * (v1[r] - v2[r]);
+              const AT ap = wp * i1[r];
+              const AT rp = box_r(ap, u, ulo, uhi);
+              const AT ep = box_res(ap, rp, (AT)1, u, ulo, uhi);
+              const AT ypn = l1[r] * rp;
+              y2[2 * a.n_x + i] = (VT)ypn;
+              wm[e] = (VT)(ypn + cn * (ypn - v1[r]));
+              rm = fmax(rm, fabs(ep));
+              hm = fmax(hm, fabs(u));
+              tm = fmax(tm, fabs(u - ep));
+              if (!isfinite(ypn)) a.flags[1] = SMPC_EDIVERGED;
+            }
+          }
+        }
+      }
+      __syncthreads();
+    }
+    rmax = fmax(rmax, (double)rm);
+    hzmax = fmax(hzmax, (double)hm);
+    tmax = fmax(tmax, (double)tm);
+  }
+
+  // w^nu of the segment's nodes without a prox (first iteration, power iteration).
+  __device__ void w_only(const int* nodes, int len) {
+    const int e = threadIdx.x;
+    if (e >= a.n_k) return;
+    for (int k = 0; k < len; ++k) {
+      const int m = nodes[k];
+      VT* wm = wb() + (long long)m * a.n_k;
+      const VT* ya = y(nu) + (long long)m * nd;
+      AT w;
+      if (linear()) {
+        const AT inv = (AT)rsqrt(a.pw[nu]);
+        if (e < a.n_x)
+          w = sqrt((AT)cv(a.step_s)[m]) * (AT)ya[e] + sqrt((AT)cv(a.step_z)[m]) * (AT)ya[a.n_x + e];
+        else
+          w = sqrt((AT)cv(a.step_p)[(long long)m * a.n_u + (e - a.n_x)]) * (AT)ya[2 * a.n_x + (e - a.n_x)];
+        w *= inv;
+      } else {
+        const AT c = (AT)a.cvec[nu];
+        const VT* yb = y(nu + 1) + (long long)m * nd;
+        if (e < a.n_x) {
+          const AT s1 = (AT)ya[e], z1 = (AT)ya[a.n_x + e];
+          w = (s1 + c * (s1 - (AT)yb[e])) + (z1 + c * (z1 - (AT)yb[a.n_x + e]));
+        } else {
+          const int i = e - a.n_x;
+          const AT p1 = (AT)ya[2 * a.n_x + i];
+          w = p1 + c * (p1 - (AT)yb[2 * a.n_x + i]);
+        }
+      }
+      wm[e] = (VT)w;
     }
   }
 
-  // A bounded wait gave up: flag the error, let this CTA's copies in flight land
-  // (again with a bound) so no bulk copy outlives the CTA's shared memory, return.
-  __device__ void drain(const Pipe& p) {
-    if (threadIdx.x == 0) a.flags[1] = SMPC_ETIMEOUT;
-    for (uint32_t q = p.used; q < p.issued_k; ++q) mbar_wait(&sm.barK[q % S], (q / S) & 1);
-    for (uint32_t q = p.used; q < p.issued_l; ++q) mbar_wait(&sm.barL[q % S], (q / S) & 1);
+  // ---------------------------------------------------------- backward sweep
+  // One node's backward step with its pack in slots (K, L):
+  //   r += [Bbar; L]' [s; psi];  delta = Lambda r;  h = [Bbar; L] delta.
+  // On entry yv holds [s; psi] and thread j < n_v holds r_j in rreg.
+  __device__ void node_backward(Pipe& p, int m, AT& rreg, bool refill) {
+    const int e = threadIdx.x;
+    const int ks = wait_k(p);
+    if (abort_) return;
+    matvec_t<MT, AT>(sm.K(ks), a.n_k, a.n_v, sm.ld, sm.yv, sm.gv, sm.part);
+    if (e < a.n_v) {
+      rreg += sm.gv[e];
+      sm.rv[e] = rreg;
+    }
+    const int ls = wait_l(p);
+    if (abort_) return;
+    matvec_t<MT, AT>(sm.Lm(ls), a.n_v, a.n_v, sm.ld, sm.rv, sm.dv, sm.part);  // Lambda is symmetric
+    if (refill) issue_l(p);
+    matvec_n<MT, AT>(sm.K(ks), a.n_k, sm.ld, sm.dv, sm.yv);
+    if (e < a.n_k) hb()[(long long)m * a.n_k + e] = (VT)sm.yv[e];
+    if (refill) issue_k(p);
+    __syncthreads();  // yv is rewritten by the next node
+  }
+
+  __device__ void chain_backward(Pipe& p, const int* nodes, int len) {
+    const int e = threadIdx.x;
+    AT sreg = 0, rreg = 0;
+    const bool lin = linear();
+    int m = nodes[len - 1];
+    AT wcur = e < a.n_k ? (AT)wb()[(long long)m * a.n_k + e] : (AT)0;
+    AT bcur = (e < a.n_v && !lin) ? (AT)cv(a.beta)[(long long)m * a.n_v + e] : (AT)0;
+    for (int k = len - 1; k >= 0; --k) {
+      m = nodes[k];
+      AT wnext = 0, bnext = 0;
+      if (k > 0) {  // prefetch the next node's vectors into registers
+        const int mn = nodes[k - 1];
+        if (e < a.n_k) wnext = (AT)wb()[(long long)mn * a.n_k + e];
+        if (e < a.n_v && !lin) bnext = (AT)cv(a.beta)[(long long)mn * a.n_v + e];
+      }
+      if (e < a.n_x) {
+        sreg += wcur;
+        sm.yv[e] = sreg;
+      } else if (e < a.n_k) {
+        sm.yv[e] = wcur;
+      }
+      rreg += bcur;
+      node_backward(p, m, rreg, true);
+      if (abort_) return;
+      wcur = wnext;
+      bcur = bnext;
+    }
+    const int head = nodes[0];
+    if (e < a.n_x) mv(a.spub)[(long long)head * a.n_x + e] = (VT)sreg;
+    if (e < a.n_v) mv(a.rpub)[(long long)head * a.n_v + e] = (VT)rreg;
+  }
+
+  // Arrival at top node t (children and its own Phase P count); true for the last one.
+  __device__ bool arrive(int t) {
+    __threadfence();  // every thread's writes (spub, rpub, h, wbuf) before the arrival
     __syncthreads();
+    if (threadIdx.x == 0) {
+      const int old = atomicAdd(&a.counters[t], 1);
+      const int last = (old == a.top_expect[t] - 1);
+      if (last) {
+        a.counters[t] = 0;  // nobody else touches it again in this launch
+        __threadfence();
+      }
+      sm.flag[0] = last;
+    }
+    __syncthreads();
+    return sm.flag[0] != 0;
+  }
+
+  // Process top node t (this CTA arrived last) and climb while it stays last.
+  // The chain prefetch in flight is flushed and re-issued from `next` afterwards.
+  __device__ void process_top(Pipe& p, int t, Cursor next) {
+    flush(p, next);
+    if (abort_) return;
+    const int e = threadIdx.x;
+    const bool lin = linear();
+    while (t >= 0) {
+      if (threadIdx.x == 0) {
+        fence_proxy_async();
+        copy_k(p.kiss, t);
+        copy_l(p.liss, t);
+      }
+      ++p.kiss;
+      ++p.liss;
+      const int cb = a.child_begin[t], cc = a.child_count[t];
+      AT sreg = 0, rreg = 0;
+      if (e < a.n_k) {
+        AT v = (AT)ldcg(wb() + (long long)t * a.n_k + e);
+        if (e < a.n_x) {
+          for (int c = cb; c < cb + cc; ++c) v += (AT)ldcg(mv(a.spub) + (long long)c * a.n_x + e);
+          sreg = v;
+        }
+        sm.yv[e] = v;
+      }
+      if (e < a.n_v) {
+        rreg = lin ? (AT)0 : (AT)cv(a.beta)[(long long)t * a.n_v + e];
+        for (int c = cb; c < cb + cc; ++c) rreg += (AT)ldcg(mv(a.rpub) + (long long)c * a.n_v + e);
+      }
+      node_backward(p, t, rreg, false);
+      if (abort_) return;
+      if (e < a.n_x) mv(a.spub)[(long long)t * a.n_x + e] = (VT)sreg;
+      if (e < a.n_v) mv(a.rpub)[(long long)t * a.n_v + e] = (VT)rreg;
+      t = a.parent[t];
+      if (t < 0 || !arrive(t)) break;
+    }
+    prime(p);
   }
 
   // ---------------------------------------------------------- the launch
   __device__ void run() {
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    double rmax = 0, hzmax = 0, tmax = 0;
+    const int tid = threadIdx.x;
     const bool do_prox = (mode & MODE_PROX) != 0 && nu >= 1;
     const bool do_bwd = (mode & MODE_BWD) != 0;
 
-    // pipeline set-up
     Pipe p;
-    p.next_k = p.next_l = first_cursor();
-    p.issued_k = p.issued_l = p.used = 0;
+    set_cursors(p, chain_cursor(blockIdx.x));
+    p.kiss = p.kuse = p.liss = p.luse = 0;
+    for (int j = a.n_v + tid; j < sm.ld; j += kThreads) sm.dv[j] = 0;
     if (tid == 0) {
       for (int s = 0; s < S; ++s) {
         mbar_init(&sm.barK[s], 1);
@@ -629,127 +862,74 @@ struct Kern {
       fence_proxy_async();
     }
     __syncthreads();
-    if (do_bwd && tid == 0) {
-      for (int s = 0; s < S; ++s) {
-        issue_k(p);
-        issue_l(p);
-      }
-    }
+    if (do_bwd) prime(p);
 
-    // top-node tasks: forward + prox (Phase P), then w^nu and the arrival
-    for (int ti = blockIdx.x; ti < a.n_top; ti += gridDim.x) {
+    // top-node tasks: forward + prox (Phase P) or w only, then the arrival
+    for (int ti = blockIdx.x; ti < a.n_top && !abort_; ti += gridDim.x) {
       const int t = a.top_nodes[ti];
-      if (do_prox) {
-        for (int idx = tid; idx < a.n_k; idx += kThreads) {
-          AT V, X, U;
-          path_init(t, idx, V, X, U);
-          write_z(t, idx, X, U);
-        }
-        __syncthreads();
-        if (warp == 0) prox_node(t, lane, rmax, hzmax, tmax);
-        __syncthreads();
-      }
+      if (do_prox) phase_p(a.parent[t], a.top_nodes + ti, 1);
       if (do_bwd) {
-        if (!do_prox || linear()) w_only_node(t, tid, kThreads);
-        arrive_and_climb(t);
+        if (!do_prox || linear()) {
+          w_only(a.top_nodes + ti, 1);
+          __syncthreads();
+        }
+        if (arrive(t)) process_top(p, t, chain_cursor(blockIdx.x));
       }
     }
 
     // chains
-    for (int ch = blockIdx.x; ch < a.n_chains; ch += gridDim.x) {
+    for (int ch = blockIdx.x; ch < a.n_chains && !abort_; ch += gridDim.x) {
       const int cb = a.chain_off[ch], len = a.chain_off[ch + 1] - cb;
       const int* nodes = a.chain_node + cb;
-      if (do_prox) {
-        const int par = a.chain_parent[ch];
-        for (int idx = tid; idx < a.n_k; idx += kThreads) {
-          AT V, X, U;
-          path_init(par, idx, V, X, U);
-          for (int k = 0; k < len; ++k) {
-            step_forward(nodes[k], idx, V, X, U);
-            write_z(nodes[k], idx, X, U);
-          }
-        }
-        __syncthreads();
-        for (int k = warp; k < len; k += kWarps) prox_node(nodes[k], lane, rmax, hzmax, tmax);
-        __syncthreads();
-      }
+      if (do_prox) phase_p(a.chain_parent[ch], nodes, len);
       if (!do_bwd) continue;
       if (!do_prox || linear()) {
-        for (int k = 0; k < len; ++k) w_only_node(nodes[k], tid, kThreads);
+        w_only(nodes, len);
         __syncthreads();
       }
-      // backward along the chain, bottom-up
-      for (int i = tid; i < a.n_x; i += kThreads) sm.sv[i] = 0;
-      for (int j = tid; j < a.n_v; j += kThreads) sm.rv[j] = 0;
-      __syncthreads();
-      for (int k = len - 1; k >= 0; --k) {
-        const int m = nodes[k];
-        const VT* wm = wb() + (long long)m * a.n_k;
-        for (int idx = tid; idx < a.n_k; idx += kThreads) {
-          AT v = (AT)wm[idx];
-          if (idx < a.n_x) {
-            v += sm.sv[idx];
-            sm.sv[idx] = v;
-          }
-          sm.yv[idx] = v;
-        }
-        if (!linear())
-          for (int j = tid; j < a.n_v; j += kThreads) sm.rv[j] += (AT)cv(a.beta)[(long long)m * a.n_v + j];
-        const int slot = p.used % S;
-        const uint32_t par = (p.used / S) & 1;
-        if (__syncthreads_or(!mbar_wait(&sm.barK[slot], par))) {
-          drain(p);
-          return;
-        }
-        matvec_t<MT, AT>(sm.K[slot], a.n_k, a.n_v, sm.yv, sm.gv, sm.part);
-        for (int j = tid; j < a.n_v; j += kThreads) sm.rv[j] += sm.gv[j];
-        if (__syncthreads_or(!mbar_wait(&sm.barL[slot], par))) {
-          drain(p);
-          return;
-        }
-        matvec_t<MT, AT>(sm.Lm[slot], a.n_v, a.n_v, sm.rv, sm.dv, sm.part);
-        if (tid == 0) {  // Lambda slot is free: refill it
-          fence_proxy_async();
-          issue_l(p);
-        }
-        matvec_n<MT, AT>(sm.K[slot], a.n_k, a.n_v, sm.dv, sm.yv, sm.part);
-        VT* hm = hb() + (long long)m * a.n_k;
-        for (int i = tid; i < a.n_k; i += kThreads) hm[i] = (VT)sm.yv[i];
-        if (tid == 0) {  // K slot is free (matvec_n ended with a barrier)
-          fence_proxy_async();
-          issue_k(p);
-        }
-        ++p.used;
-        __syncthreads();  // yv is rewritten by the next node
-      }
-      // publish the chain head's s and r, arrive at its top parent
-      const int head = nodes[0];
-      for (int i = tid; i < a.n_x; i += kThreads) mv(a.spub)[(long long)head * a.n_x + i] = (VT)sm.sv[i];
-      for (int j = tid; j < a.n_v; j += kThreads) mv(a.rpub)[(long long)head * a.n_v + j] = (VT)sm.rv[j];
-      arrive_and_climb(a.chain_parent[ch]);
+      chain_backward(p, nodes, len);
+      if (abort_) break;
+      const int par = a.chain_parent[ch];
+      if (par >= 0 && arrive(par)) process_top(p, par, chain_cursor(ch + gridDim.x));
     }
 
-    if (do_prox && !linear()) {  // residual of iteration nu - 1 (Sec. IV-E)
-      rmax = warp_max(rmax);
-      hzmax = warp_max(hzmax);
-      tmax = warp_max(tmax);
+    // per-CTA reductions: residual maxima (Sec. IV-E) or power-iteration sums
+    const int lane = tid & 31, warp = tid >> 5;
+    if (do_prox && !linear()) {
+      const double r = warp_max(rmax), hz = warp_max(hzmax), tt = warp_max(tmax);
       if (lane == 0) {
-        sm.red[warp] = rmax;
-        sm.red[kWarps + warp] = hzmax;
-        sm.red[2 * kWarps + warp] = tmax;
+        sm.res3[warp] = r;
+        sm.res3[kWarps + warp] = hz;
+        sm.res3[2 * kWarps + warp] = tt;
       }
       __syncthreads();
       if (tid == 0) {
-        double r = 0, hz = 0, tt = 0;
+        double R = 0, HZ = 0, TT = 0;
         for (int w = 0; w < kWarps; ++w) {
-          r = fmax(r, sm.red[w]);
-          hz = fmax(hz, sm.red[kWarps + w]);
-          tt = fmax(tt, sm.red[2 * kWarps + w]);
+          R = fmax(R, sm.res3[w]);
+          HZ = fmax(HZ, sm.res3[kWarps + w]);
+          TT = fmax(TT, sm.res3[2 * kWarps + w]);
         }
         unsigned long long* slot = a.res + 3ll * (nu - 1);
-        atomic_max_nonneg(slot + 0, r);
-        atomic_max_nonneg(slot + 1, hz);
-        atomic_max_nonneg(slot + 2, tt);
+        atomic_max_nonneg(slot + 0, R);
+        atomic_max_nonneg(slot + 1, HZ);
+        atomic_max_nonneg(slot + 2, TT);
+      }
+    } else if (do_prox && linear()) {
+      const double nr = warp_sum(pnrm), dt = warp_sum(pdot);
+      if (lane == 0) {
+        sm.res3[warp] = nr;
+        sm.res3[kWarps + warp] = dt;
+      }
+      __syncthreads();
+      if (tid == 0) {
+        double NR = 0, DT = 0;
+        for (int w = 0; w < kWarps; ++w) {
+          NR += sm.res3[w];
+          DT += sm.res3[kWarps + w];
+        }
+        atomicAdd(&a.pw[nu], NR);
+        atomicAdd(&a.pw[a.pw_len + nu - 1], DT);
       }
     }
   }
@@ -789,14 +969,19 @@ __global__ void __launch_bounds__(kThreads, 1)
 template <typename VT, typename MT>
 __global__ void pack_kernel(int n, int n_k, int n_v, const double* K, const double* Lam, const double* prob,
                             MT* packs, long long stride) {
-  const long long kp = kpad(n_k, n_v), lp = lpad(n_v);
+  const long long kp = kpad<MT>(n_k, n_v), lp = lpad<MT>(n_v);
+  const int ld = row_stride<MT>(n_v);
   for (int m = blockIdx.x; m < n; m += gridDim.x) {
     MT* dst = packs + (long long)m * stride;
     const double inv = 1.0 / (2.0 * prob[m]);
-    for (long long i = threadIdx.x; i < kp; i += blockDim.x)
-      dst[i] = (MT)(i < (long long)n_k * n_v ? K[i] : 0.0);
-    for (long long i = threadIdx.x; i < lp; i += blockDim.x)
-      dst[kp + i] = (MT)(i < (long long)n_v * n_v ? Lam[i] * inv : 0.0);
+    for (long long q = threadIdx.x; q < kp; q += blockDim.x) {
+      const long long i = q / ld, j = q % ld;
+      dst[q] = (MT)(i < n_k && j < n_v ? K[i * n_v + j] : 0.0);
+    }
+    for (long long q = threadIdx.x; q < lp; q += blockDim.x) {
+      const long long i = q / ld, j = q % ld;
+      dst[kp + q] = (MT)(i < n_v && j < n_v ? Lam[i * n_v + j] * inv : 0.0);
+    }
   }
 }
 
@@ -917,7 +1102,8 @@ LaunchCfg config_t(const IterArgs& a, int num_sms, int S_max) {
   while (S > 1 && iter_smem_bytes<MT>(S, a.n_x, a.n_u, a.n_v) > (size_t)optin) --S;
   c.stages = S;
   c.smem = iter_smem_bytes<MT>(S, a.n_x, a.n_u, a.n_v);
-  if (c.smem > (size_t)optin) c.stages = 0;
+  // one thread per entry of [x; u] and of r
+  if (c.smem > (size_t)optin || a.n_k > kThreads || a.n_v > kThreads) c.stages = 0;
   c.block = kThreads;
   c.grid = a.n_chains < num_sms ? a.n_chains : num_sms;
   if (c.grid < 1) c.grid = 1;
@@ -941,7 +1127,13 @@ size_t vec_size(int prec) { return prec == SMPC_FP64 ? sizeof(double) : sizeof(f
 size_t mat_size(int prec) {
   return prec == SMPC_FP64 ? sizeof(double) : prec == SMPC_FP32 ? sizeof(float) : sizeof(__nv_bfloat16);
 }
-long long pack_entries(int n_k, int n_v) { return kpad(n_k, n_v) + lpad(n_v); }
+long long pack_entries(int prec, int n_k, int n_v) {
+  switch (prec) {
+    case SMPC_FP64: return kpad<double>(n_k, n_v) + lpad<double>(n_v);
+    case SMPC_FP32: return kpad<float>(n_k, n_v) + lpad<float>(n_v);
+    default: return kpad<__nv_bfloat16>(n_k, n_v) + lpad<__nv_bfloat16>(n_v);
+  }
+}
 
 LaunchCfg iter_config(int prec, const IterArgs& a, int num_sms) {
   switch (prec) {

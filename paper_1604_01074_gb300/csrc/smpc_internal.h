@@ -92,6 +92,11 @@ struct IterArgs {
   const void* step_s;            // n
   const void* step_z;            // n
   const void* step_p;            // n x n_u
+  const void* inv_s;             // n: 1 / step_s
+  const void* inv_z;             // n: 1 / step_z
+  const void* thr_s;             // n: mu_s / step_s (prox threshold of the safety block)
+  const void* thr_z;             // n: gamma_d / step_z
+  const void* inv_p;             // n x n_u: 1 / step_p
   const void* mu_s;              // n
   const void* x_s;
   const void* x_min;
@@ -153,7 +158,7 @@ struct CostArgs {
 };
 int launch_cost_update(int prec, const CostArgs& a, void* stream);
 int launch_copy_final_y(int prec, const IterArgs& a, int max_iters, void* dst, void* stream);
-long long pack_entries(int n_k, int n_v);
+long long pack_entries(int prec, int n_k, int n_v);
 int launch_init_duals(int prec, const IterArgs& a, int warm, void* stream);
 int launch_convert(int prec, const double* src, void* dst, long long count, void* stream);
 size_t vec_size(int prec);

@@ -177,3 +177,24 @@ def test_reduced_precision_residual(precision):
     coupling = np.abs(u @ P["net"]["E"].T + d @ P["net"]["Ed"].T).max()
     eu = H.relerr(u, R.u)
     assert abs(info["rho_rel"] - R.rho_rel[-1]) <= 1e-4, (info["rho_rel"], R.rho_rel[-1], eu, coupling)
+
+
+def test_device_resident_step_data_matches_host_inputs():
+    import torch
+    P = synth.random_instance(22, n_x=4, n_u=7, n_d=4, n_e=2, horizon=5, max_children=4)
+    tree, fac, _ = H.oracle_build(P)
+    steps = oracle.jacobi_steps(fac, tree)
+    g = H.Gpu(P, steps=steps)
+    try:
+        g.solve(40)
+        ref = [t.clone() for t in (g.u, g.x, g.y)]
+        dev = {k: torch.from_numpy(np.ascontiguousarray(P[k], dtype=np.float64)).cuda()
+               for k in ("p", "q", "dhat", "alpha2", "eps")}
+        info = g.smpc.smpc_solve(g.fac, dev["p"].data_ptr(), dev["q"].data_ptr(), dev["dhat"].data_ptr(),
+                                 dev["alpha2"].data_ptr(), eps=dev["eps"].data_ptr(), max_iters=40, sync=1,
+                                 u=g.u, x=g.x, y=g.y)
+        assert info["iterations"] == 40
+        for a, b in zip(ref, (g.u, g.x, g.y)):
+            assert bool((a == b).all())
+    finally:
+        g.close()
