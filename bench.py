@@ -46,6 +46,20 @@ def peaks():
 FP64_FMA_TFLOPS = 1.157
 
 
+def recorded_traffic(prec_name):
+    """DRAM bytes per launch from the last ncu capture in profiles/, if the kernel
+    source is unchanged since (else None)."""
+    import hashlib
+    try:
+        rec = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))
+        src = open(os.path.join(ROOT, "paper_1604_01074_gb300", "csrc", "kernels.cu"), "rb").read()
+        if hashlib.sha256(src).hexdigest()[:16] != rec.get("kernel_sha256_16"):
+            return None
+        return rec.get(prec_name, {}).get("dram_bytes_per_launch")
+    except Exception:  # noqa: BLE001
+        return None
+
+
 # --------------------------------------------------------------------- workload
 def make_problem(config, seed=0):
     import synth
@@ -323,7 +337,7 @@ def run_ours(args, rank, world, local_rank):
     clocks = clk.summary()
 
     # kernel roofline: one iteration launch, differential timing
-    t_iter_ms = time_per_iteration(S, dev_in[0], stream)
+    t_iter_ms = time_per_iteration(S, dev_in[0], stream, *((20, 60) if prec == 0 else (100, 400)))
     log("ms per iteration launch", t_iter_ms)
     n_v = S.n_u - np.linalg.matrix_rank(P["net"]["E"])
     nbytes, mat_entries, flops = algorithmic_bytes_per_iteration(S.n, S.n_x, S.n_u, n_v, prec)
@@ -331,12 +345,12 @@ def run_ours(args, rank, world, local_rank):
     if prec == 0:
         achieved = flops / (t_iter_ms * 1e-3) / 1e12
         roof = {"bound": "alu", "achieved": achieved, "peak": FP64_FMA_TFLOPS, "unit": "TFLOP/s",
-                "frac": achieved / FP64_FMA_TFLOPS, "traffic": None,
+                "frac": achieved / FP64_FMA_TFLOPS, "traffic": recorded_traffic("fp64"),
                 "peak_source": "measured FP64 FMA microbenchmark on this pool's GB300"}
     else:
         achieved = nbytes / (t_iter_ms * 1e-3) / 1e9
         roof = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
-                "traffic": None, "peak_source": f"{src} hbm_gbs"}
+                "traffic": recorded_traffic(args.precision), "peak_source": f"{src} hbm_gbs"}
     roof.update({"kernel": "apg_iter", "us_per_launch": 1000.0 * t_iter_ms, "bytes_per_launch": nbytes})
 
     # end-to-end: host (pinned) inputs, device->host read of u_0 and the residual, wall clock
@@ -370,25 +384,40 @@ def run_ours(args, rank, world, local_rank):
     }
     log("headline", {k: result[k] for k in ("value", "ms_per_step", "iterations_mean", "p50_ms", "p99_ms")})
     S.close()
-    if args.fp64_leg and prec != 0 and rank == 0:
-        S64 = Solver(P, 0, device)
-        t64 = time_per_iteration(S64, dev_in[0], stream, lo=20, hi=60, reps=2)
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        S64.solve(dev_in[0], args.max_iters, args.tol, stream)
-        e1.record(stream)
-        inf64 = S64.finish()
-        ms64 = e0.elapsed_time(e1)
-        log("fp64 solve ms", ms64, inf64, "us/iter", 1000 * t64)
-        _, _, fl = algorithmic_bytes_per_iteration(S64.n, S64.n_x, S64.n_u, n_v, 0)
-        result["fp64"] = {"solves_per_s": 1000.0 / ms64, "ms_per_solve": ms64, "iterations": inf64["iterations"],
-                          "us_per_iteration": 1000.0 * t64,
-                          "roofline": {"bound": "alu", "achieved": fl / (t64 * 1e-3) / 1e12, "peak": FP64_FMA_TFLOPS,
-                                       "unit": "TFLOP/s", "frac": fl / (t64 * 1e-3) / 1e12 / FP64_FMA_TFLOPS}}
-        S64.close()
+    if args.other_legs and rank == 0:
+        # the other precisions on the same workload: iteration cost, HBM roofline, and the
+        # residual they reach after as many iterations as the headline solve needed
+        legs = {}
+        n_it = int(max(iters)) if iters else 1000
+        for other in (0, 1, 2):
+            if other == prec:
+                continue
+            So = Solver(P, other, device)
+            lo, hi = (20, 60) if other == 0 else (100, 400)
+            t_o = time_per_iteration(So, dev_in[0], stream, lo=lo, hi=hi, reps=2)
+            b_o, _, f_o = algorithmic_bytes_per_iteration(So.n, So.n_x, So.n_u, n_v, other)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            So.solve(dev_in[0], n_it, args.tol, stream)
+            e1.record(stream)
+            inf_o = So.finish()
+            leg = {"us_per_iteration": 1000.0 * t_o, "iterations_run": inf_o["iterations"],
+                   "rho_rel": inf_o["rho_rel"], "reached_tol": inf_o["rho_rel"] <= args.tol,
+                   "ms_for_run": e0.elapsed_time(e1)}
+            if other == 0:
+                leg["roofline"] = {"bound": "alu", "achieved": f_o / (t_o * 1e-3) / 1e12, "peak": FP64_FMA_TFLOPS,
+                                   "unit": "TFLOP/s", "frac": f_o / (t_o * 1e-3) / 1e12 / FP64_FMA_TFLOPS}
+            else:
+                hbm, src = peaks()
+                leg["roofline"] = {"bound": "hbm", "achieved": b_o / (t_o * 1e-3) / 1e9, "peak": hbm, "unit": "GB/s",
+                                   "frac": b_o / (t_o * 1e-3) / 1e9 / hbm}
+            legs[PREC_NAMES[other]] = leg
+            log("leg", PREC_NAMES[other], leg)
+            So.close()
+        result["other_precisions"] = legs
     if rank == 0 and not args.no_cpu_baseline:
-        it_ref = result["fp64"]["iterations"] if "fp64" in result else int(np.mean(iters))
+        it_ref = int(np.mean(iters))
         stored, _ = oracle_iters_to_tol(args.config)
         try:
             result["cpu_baseline"] = cpu_baseline(args.config, stored or it_ref)
@@ -399,6 +428,19 @@ def run_ours(args, rank, world, local_rank):
         dist.barrier()
         dist.destroy_process_group()
     return result
+
+
+def profile_solve(args):
+    import torch
+    device = torch.device("cuda", 0)
+    prec = {"fp64": 0, "fp32": 1, "bf16": 2}[args.precision]
+    P = make_problem(args.config, seed=0)
+    S = Solver(P, prec, device)
+    stream = torch.cuda.current_stream(device)
+    S.solve(S.device_inputs(step_inputs(P, 0)), args.profile_solve, 0.0, stream)
+    info = S.finish()
+    S.close()
+    print(json.dumps({"profile_solve": args.profile_solve, "precision": args.precision, "info": info}))
 
 
 def run_reference(args, rank, world):
@@ -445,16 +487,21 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--precision", choices=["fp64", "fp32", "bf16"], default="fp32")
+    ap.add_argument("--precision", choices=["fp64", "fp32", "bf16"], default="fp64")
     ap.add_argument("--config", choices=["barcelona", "tiny", "large"], default="barcelona")
     ap.add_argument("--tol", type=float, default=1e-3)
     ap.add_argument("--max-iters", type=int, default=100000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-fp64-leg", dest="fp64_leg", action="store_false")
+    ap.add_argument("--no-other-precisions", dest="other_legs", action="store_false")
     ap.add_argument("--oracle-sample", type=int, default=0)
+    ap.add_argument("--profile-solve", type=int, default=0,
+                    help="factor + one solve of this many iterations (tol 0) and exit: the case ncu captures")
     args = ap.parse_args()
     if args.oracle_sample:
         oracle_sample(args.config, args.oracle_sample)
+        return
+    if args.profile_solve:
+        profile_solve(args)
         return
     rank, world, local_rank = dist_env()
     if args.impl == "reference":

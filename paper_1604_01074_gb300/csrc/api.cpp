@@ -428,6 +428,10 @@ int power_iteration(smpc_factor_t* f, int iters, double* out) {
   a.pw = pw;
   a.pw_len = iters + 1;
   LaunchCfg cfg = iter_config(f->prec, a, f->num_sms);
+  if (cfg.stages < 1) {
+    set_error("network too large for the shared-memory pipeline");
+    return SMPC_ENOTSUP;
+  }
   for (int k = 0; k < iters; ++k) {
     TRY(launch_iter(f->prec, a, cfg, k, MODE_BWD | MODE_LINEAR, nullptr));
     TRY(launch_iter(f->prec, a, cfg, k + 1, MODE_PROX | MODE_LINEAR, nullptr));

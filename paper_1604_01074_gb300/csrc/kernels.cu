@@ -250,10 +250,15 @@ inline __host__ __device__ long long kpad(int n_k, int n_v) { return round_up((l
 template <typename MT>
 inline __host__ __device__ long long lpad(int n_v) { return round_up((long long)n_v * row_stride<MT>(n_v), 32); }
 
+// Scratch for the row slices of matvec_t (same slice count as there) and for the
+// per-warp block norms of the prox pass, which reuse it.
 template <typename MT>
 inline __host__ __device__ int part_entries(int n_v) {
   const int ld = row_stride<MT>(n_v);
-  const int a = 16 * ld, b = 2 * kSeg * kWarps;
+  const int G = ld / (16 / (int)sizeof(MT));
+  int P = kThreads / G;
+  if (P > 16) P = 16;
+  const int a = P * ld, b = 2 * kSeg * kWarps;
   return a > b ? a : b;
 }
 
@@ -262,7 +267,7 @@ __host__ __device__ size_t vec_smem_bytes(int n_x, int n_u, int n_v) {
   using AT = typename Acc<MT>::T;
   const int n_k = n_x + n_u, ld = row_stride<MT>(n_v);
   size_t v = round_up((size_t)ld * sizeof(AT), 16);
-  v += (size_t)(n_k + 2 * ld + part_entries<MT>(n_v)) * sizeof(AT);
+  v += (size_t)(n_k + 2 * ld + part_entries<MT>(n_v) + 2 * kSeg) * sizeof(AT);
   v = round_up(v, 16);
   v += 3 * kWarps * sizeof(double) + (kSeg + 8) * sizeof(int);
   return round_up(v, 128);
@@ -291,6 +296,7 @@ struct Smem {
   AT* rv;          // ld
   AT* part;        // part_entries: mat-vec slices
   AT* red;         // aliases part: per node, per warp, the two block norms
+  AT* kap;         // 2 * kSeg: per node, the prox factors kappa of the two distance blocks
   double* res3;    // 3 * kWarps
   int* seg;        // kSeg node ids
   int* flag;       // 8 ints
@@ -326,6 +332,8 @@ __device__ Smem<MT> carve(unsigned char* base, int S, int n_x, int n_u, int n_v)
   s.part = v;
   s.red = v;
   v += part_entries<MT>(n_v);
+  s.kap = v;
+  v += 2 * kSeg;
   off = round_up(reinterpret_cast<unsigned char*>(v) - base, 16);
   s.res3 = reinterpret_cast<double*>(base + off);
   off += 3 * kWarps * sizeof(double);
@@ -593,14 +601,27 @@ struct Kern {
         }
       }
       __syncthreads();
+      if (!lin && e < bl) {  // one thread per node: kappa = min(1, theta / ||r||) of both blocks
+        const int m = sm.seg[e];
+        AT ds2 = 0, dz2 = 0;
+        for (int w = 0; w < tank_warps; ++w) {
+          ds2 += sm.red[(e * kWarps + w) * 2 + 0];
+          dz2 += sm.red[(e * kWarps + w) * 2 + 1];
+        }
+        const AT ds = sqrt(ds2), dz = sqrt(dz2);
+        const AT ths = (AT)cv(a.thr_s)[m], thz = (AT)cv(a.thr_z)[m];
+        sm.kap[2 * e + 0] = ds > ths ? ths / ds : (AT)1;
+        sm.kap[2 * e + 1] = dz > thz ? thz / dz : (AT)1;
+      }
+      __syncthreads();
       // pass B: prox (App. C), dual update, extrapolation w^{it+1}
       if (e < a.n_k) {
         for (int k0 = 0; k0 < bl; k0 += kB) {
           const int q = min(kB, bl - k0);
-          AT zv[kB], v1[kB], v2[kB], w1[kB], w2[kB], l1[kB], l2[kB], i1[kB], i2[kB], t1[kB], t2[kB];
+          AT zv[kB], v1[kB], v2[kB], w1[kB], w2[kB], l1[kB], l2[kB], i1[kB], i2[kB];
 #pragma unroll
           for (int r = 0; r < kB; ++r) {
-            zv[r] = v1[r] = v2[r] = w1[r] = w2[r] = t1[r] = t2[r] = 0;
+            zv[r] = v1[r] = v2[r] = w1[r] = w2[r] = 0;
             l1[r] = l2[r] = i1[r] = i2[r] = 1;
             if (r < q) {
               const int m = sm.seg[k0 + r];
@@ -617,8 +638,6 @@ struct Kern {
                 if (!lin) {
                   i1[r] = (AT)cv(a.inv_s)[m];
                   i2[r] = (AT)cv(a.inv_z)[m];
-                  t1[r] = (AT)cv(a.thr_s)[m];
-                  t2[r] = (AT)cv(a.thr_z)[m];
                 }
               } else {
                 zv[r] = (AT)Uo[(long long)m * a.n_u + i];
@@ -653,14 +672,7 @@ struct Kern {
               continue;
             }
             if (tank) {
-              AT ds2 = 0, dz2 = 0;
-              for (int w = 0; w < tank_warps; ++w) {
-                ds2 += sm.red[(k * kWarps + w) * 2 + 0];
-                dz2 += sm.red[(k * kWarps + w) * 2 + 1];
-              }
-              const AT ds = sqrt(ds2), dz = sqrt(dz2);
-              const AT ks = ds > t1[r] ? t1[r] / ds : (AT)1;
-              const AT kz = dz > t2[r] ? t2[r] / dz : (AT)1;
+              const AT ks = sm.kap[2 * k + 0], kz = sm.kap[2 * k + 1];
               const AT x = zv[r];
               const AT ws = v1[r] + c * (v1[r] - v2[r]);
               const AT wz = w1[r] + c * (w1[r] - w2[r]);
