@@ -174,6 +174,34 @@ int smpc_factor_steps(const smpc_factor_t* fac, double* lambda, double* step_s, 
 int smpc_solve(smpc_factor_t* fac, const smpc_step_data* data, const smpc_solve_opts* opts,
                smpc_result* res, void* stream);
 
+/* smpc_solve without memory allocation.  The paper has no counterpart: it exists for
+ * callers that cannot allocate device memory while they run.  A model-predictive
+ * controller solves once per sampling period and must return its move within the
+ * period (Alg. 2); cudaMalloc and cudaFree may synchronize the whole device and take
+ * unbounded time, and deployments with a fixed device-memory budget forbid allocation
+ * after start-up.  smpc_solve may allocate when a solve asks for more iterations than
+ * any earlier solve on its factor; smpc_solve_static allocates nothing, on the device
+ * or the host.  The factor, created during the caller's set-up, still supplies the
+ * packs, duals and step buffers, and the caller passes inputs and outputs as for
+ * smpc_solve (same arguments, results and errors).
+ *
+ * The iteration kernel's scratch (theta table, residual history, arrival counters, stop
+ * and error flags, w, h and the published s and r of the tree reduction) lives in one
+ * static device array of SMPC_STATIC_SCRATCH_BYTES (16 MiB) that every GPU which loads
+ * the library holds until the process exits.  A solve needing more - about
+ * 32 (max_iters + 3) + 4 n_nodes + vs n_nodes (3 n_x + 2 n_u + n_v) bytes, vs = 8 for
+ * SMPC_FP64 and 4 otherwise - is refused with SMPC_EINVAL before any device work.
+ * The first call on a device resolves the array's device address (cudaGetSymbolAddress)
+ * and should come before any stream capture.  All calls, on any factor and any stream,
+ * share the array and leave their contents in it; each call clears what must start at
+ * zero.  Calls that overlap on the GPU race on the array: the caller must serialize
+ * them.  warm_start continues from the last solve of the same factor by either entry point.
+ * Host outputs (iterations, rho, u0_host, history_host) are filled with opts->sync = 1;
+ * smpc_solve_info completes smpc_solve only. */
+#define SMPC_STATIC_SCRATCH_BYTES (16u << 20)
+int smpc_solve_static(smpc_factor_t* fac, const smpc_step_data* data, const smpc_solve_opts* opts,
+                      smpc_result* res, void* stream);
+
 /* Completes an asynchronous solve (opts->sync = 0): waits for the stream of the
  * factor's last solve and fills the host outputs of `res` (iterations, rho,
  * rho_rel, u0_host, history_host) exactly as a synchronous solve would.

@@ -71,6 +71,8 @@ SIGNATURES = {
     "smpc_solve": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(smpc_step_data), ctypes.POINTER(smpc_solve_opts),
                                   ctypes.POINTER(smpc_result), ctypes.c_void_p]),
     "smpc_solve_info": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(smpc_result)]),
+    "smpc_solve_static": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(smpc_step_data),
+                                         ctypes.POINTER(smpc_solve_opts), ctypes.POINTER(smpc_result), ctypes.c_void_p]),
     "smpc_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "smpc_last_error": (ctypes.c_char_p, []),
     "smpc_version": (ctypes.c_int, []),
@@ -183,7 +185,7 @@ def smpc_factor_steps(fac, n, n_u):
 
 
 def smpc_solve(fac, p, q, dhat, alpha2, eps=None, max_iters=500, tol=0.0, warm_start=0, check_every=0, sync=1,
-               u=None, x=None, y=None, u0_host=None, history_host=None, stream=None):
+               u=None, x=None, y=None, u0_host=None, history_host=None, stream=None, _entry="smpc_solve"):
     """u, x, y: optional torch device tensors (or raw device pointers) receiving the outputs.
     u0_host / history_host: optional numpy float64 arrays filled when sync=1."""
     k = _Keep()
@@ -210,8 +212,17 @@ def smpc_solve(fac, p, q, dhat, alpha2, eps=None, max_iters=500, tol=0.0, warm_s
         s = stream
     else:
         s = stream.cuda_stream
-    _check(lib().smpc_solve(fac, ctypes.byref(D), ctypes.byref(O), ctypes.byref(R), s), "smpc_solve")
+    _check(getattr(lib(), _entry)(fac, ctypes.byref(D), ctypes.byref(O), ctypes.byref(R), s), _entry)
     return {"iterations": R.iterations, "rho": R.rho, "rho_rel": R.rho_rel, "launches": R.launches}
+
+
+def smpc_solve_static(fac, p, q, dhat, alpha2, eps=None, max_iters=500, tol=0.0, warm_start=0, check_every=0,
+                      sync=1, u=None, x=None, y=None, u0_host=None, history_host=None, stream=None):
+    """smpc_solve without memory allocation (scratch in the library's static device
+    array); same arguments and results as smpc_solve."""
+    return smpc_solve(fac, p, q, dhat, alpha2, eps=eps, max_iters=max_iters, tol=tol, warm_start=warm_start,
+                      check_every=check_every, sync=sync, u=u, x=x, y=y, u0_host=u0_host,
+                      history_host=history_host, stream=stream, _entry="smpc_solve_static")
 
 
 def smpc_solve_info(fac, u0_host=None, history_host=None):

@@ -227,59 +227,7 @@ int upload_tree(smpc_tree& t) {
 
 }  // namespace
 
-// ---------------------------------------------------------------------------
-struct smpc_factor_t {
-  const smpc_tree* tree = nullptr;
-  int prec = SMPC_FP64;
-  int n = 0, N = 0, n_x = 0, n_u = 0, n_d = 0, n_e = 0, n_v = 0, n_k = 0, nd = 0;
-  size_t vs = 8, ms = 8;
-  long long pack_stride = 0;
-  double lambda = 0;
-  double W_alpha = 0;
-  smpc::HostFactor hf;
-  std::vector<void*> allocs;
-  // device
-  void* packs = nullptr;
-  double *K64 = nullptr, *Lam64 = nullptr, *Pu = nullptr, *Pe = nullptr, *Rhat = nullptr, *L = nullptr;
-  double *alpha1 = nullptr, *uhat64 = nullptr, *abar = nullptr;
-  double *d_p = nullptr, *d_q = nullptr, *d_dhat = nullptr, *d_eps = nullptr, *d_alpha2 = nullptr;
-  void *ybuf0 = nullptr, *ybuf1 = nullptr, *wbuf = nullptr, *h = nullptr, *uhat = nullptr, *e = nullptr, *beta = nullptr;
-  void *spub = nullptr, *rpub = nullptr, *uout = nullptr, *xout = nullptr;
-  void *step_s = nullptr, *step_z = nullptr, *step_p = nullptr, *mu_s = nullptr;
-  void *inv_s = nullptr, *inv_z = nullptr, *thr_s = nullptr, *thr_z = nullptr, *inv_p = nullptr;
-  std::vector<double> mu_host;
-  void *x_s = nullptr, *x_min = nullptr, *x_max = nullptr, *u_min = nullptr, *u_max = nullptr, *p0 = nullptr;
-  double gamma_d = 0;
-  int* counters = nullptr;
-  int* flags = nullptr;
-  int* flags_host = nullptr;  // pinned, 2 x 2 ints
-  unsigned long long* res = nullptr;
-  double* cvec = nullptr;
-  int cap = 0;                // iterations the res/cvec buffers hold
-  int cvec_for = -1;
-  cudaEvent_t ev[2] = {nullptr, nullptr};
-  cudaStream_t last_stream = nullptr;
-  int last_launches = 0;
-  int num_sms = 0;
-  bool solved_once = false;
-
-  template <typename T>
-  int alloc(T** p, size_t bytes) {
-    *p = nullptr;
-    if (bytes == 0) bytes = 16;
-    void* q = nullptr;
-    CK(cudaMalloc(&q, bytes));
-    allocs.push_back(q);
-    *p = static_cast<T*>(q);
-    return SMPC_OK;
-  }
-  ~smpc_factor_t() {
-    for (void* p : allocs) cudaFree(p);
-    if (flags_host) cudaFreeHost(flags_host);
-    for (auto& v : ev)
-      if (v) cudaEventDestroy(v);
-  }
-};
+// smpc_factor_t is defined in smpc_internal.h
 
 namespace {
 
