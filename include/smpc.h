@@ -17,7 +17,10 @@
  *   y_n = (vsigma_n, zeta_n, psi_n) of length 2 n_x + n_u (Sec. IV-A); this is the
  *   layout that reproduces the variable counts of Table 1.
  * - Device vectors use the "vector type" of a factor: float64 when the factor's
- *   precision is SMPC_FP64, float32 for SMPC_FP32 and SMPC_BF16.
+ *   precision is SMPC_FP64, float32 for SMPC_FP32 and SMPC_BF16.  The dual iterates
+ *   themselves are held internally in float64, or as float32 pairs hi + lo (about
+ *   48 significant bits) for the reduced precisions, so that the small dual moves of
+ *   a late iteration are not rounded away.
  * - Every call returns an smpc_status; none throws.  On failure the message of
  *   the calling thread's last error is available from smpc_last_error().
  * - Objects are owned by the library and released by the matching *_destroy.
@@ -118,6 +121,16 @@ typedef struct smpc_solve_opts {
   int32_t warm_start;   /* 1: start from the duals the previous solve left on the device */
   int32_t check_every;  /* host polls the stop flag every this many iterations (0: 128) */
   int32_t sync;         /* 1: wait for the stream, fill the host outputs, check errors */
+  /* SMPC_BF16 factors only (other precisions ignore both).  The solve step is affine
+   * in w, h(w) = h(w_a) + h_lin(w - w_a): every anchor_every-th iteration (0: 16) is
+   * an anchor that evaluates the whole step at w_a = w^nu with the factor's float32
+   * packs, and the iterations between apply the bfloat16 packs to w - w_a only.  The
+   * iteration's fixed points are those of the float32 packs, while bfloat16 carries
+   * the matrix traffic of all other iterations.  The last polish_iters iterations
+   * (0 <= polish_iters <= max_iters) are all anchors: the final set of iterations
+   * with float32 matrices. */
+  int32_t polish_iters;
+  int32_t anchor_every;
 } smpc_solve_opts;
 
 /* Outputs.  Device pointers may be NULL (not copied).  Host outputs are filled
@@ -153,7 +166,8 @@ void smpc_tree_destroy(smpc_tree* tree);
  * [B_bar; L] (n_x + n_u) x n_v and Lambda / (2 p_n) (n_v x n_v, Alg. 1's
  * node-indexed factor matrices) in the requested precision on the device, the
  * Jacobi scaling (Sec. IV-D) and the step lambda = 1/L_{H_D} (power iteration
- * on the device, unless given).  The tree must outlive the factor.
+ * on the device, unless given).  An SMPC_BF16 factor also keeps float32 packs for
+ * the anchor and polish iterations of smpc_solve_opts.  The tree must outlive the factor.
  * Errors: SMPC_EINVAL (sizes, NaN, E rank deficient, W_u not SPD),
  *         SMPC_ENOTSUP (A != I), SMPC_ENOMEM, SMPC_ECUDA. */
 int smpc_factor(const smpc_tree* tree, const smpc_network* net, const smpc_cost* cost,

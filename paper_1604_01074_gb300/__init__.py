@@ -45,7 +45,8 @@ class smpc_step_data(ctypes.Structure):
 
 class smpc_solve_opts(ctypes.Structure):
     _fields_ = [("max_iters", ctypes.c_int32), ("tol", ctypes.c_double), ("warm_start", ctypes.c_int32),
-                ("check_every", ctypes.c_int32), ("sync", ctypes.c_int32)]
+                ("check_every", ctypes.c_int32), ("sync", ctypes.c_int32), ("polish_iters", ctypes.c_int32),
+                ("anchor_every", ctypes.c_int32)]
 
 
 class smpc_result(ctypes.Structure):
@@ -185,7 +186,8 @@ def smpc_factor_steps(fac, n, n_u):
 
 
 def smpc_solve(fac, p, q, dhat, alpha2, eps=None, max_iters=500, tol=0.0, warm_start=0, check_every=0, sync=1,
-               u=None, x=None, y=None, u0_host=None, history_host=None, stream=None, _entry="smpc_solve"):
+               u=None, x=None, y=None, u0_host=None, history_host=None, stream=None, polish_iters=0,
+               anchor_every=0, _entry="smpc_solve"):
     """u, x, y: optional torch device tensors (or raw device pointers) receiving the outputs.
     u0_host / history_host: optional numpy float64 arrays filled when sync=1."""
     k = _Keep()
@@ -196,7 +198,8 @@ def smpc_solve(fac, p, q, dhat, alpha2, eps=None, max_iters=500, tol=0.0, warm_s
         return k(a)
 
     D = smpc_step_data(arg(p), arg(q), arg(dhat), arg(eps), arg(alpha2))
-    O = smpc_solve_opts(int(max_iters), float(tol), int(warm_start), int(check_every), int(sync))
+    O = smpc_solve_opts(int(max_iters), float(tol), int(warm_start), int(check_every), int(sync), int(polish_iters),
+                        int(anchor_every))
 
     def dptr(t):
         if t is None:
@@ -217,12 +220,14 @@ def smpc_solve(fac, p, q, dhat, alpha2, eps=None, max_iters=500, tol=0.0, warm_s
 
 
 def smpc_solve_static(fac, p, q, dhat, alpha2, eps=None, max_iters=500, tol=0.0, warm_start=0, check_every=0,
-                      sync=1, u=None, x=None, y=None, u0_host=None, history_host=None, stream=None):
+                      sync=1, u=None, x=None, y=None, u0_host=None, history_host=None, stream=None, polish_iters=0,
+                      anchor_every=0):
     """smpc_solve without memory allocation (scratch in the library's static device
     array); same arguments and results as smpc_solve."""
     return smpc_solve(fac, p, q, dhat, alpha2, eps=eps, max_iters=max_iters, tol=tol, warm_start=warm_start,
                       check_every=check_every, sync=sync, u=u, x=x, y=y, u0_host=u0_host,
-                      history_host=history_host, stream=stream, _entry="smpc_solve_static")
+                      history_host=history_host, stream=stream, polish_iters=polish_iters,
+                      anchor_every=anchor_every, _entry="smpc_solve_static")
 
 
 def smpc_solve_info(fac, u0_host=None, history_host=None):

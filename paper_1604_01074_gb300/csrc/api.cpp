@@ -233,7 +233,7 @@ namespace {
 
 IterArgs make_args(const smpc_factor_t* f) {
   const smpc_tree* t = f->tree;
-  IterArgs a;
+  IterArgs a{};
   std::memset(&a, 0, sizeof a);
   a.n = f->n;
   a.n_x = f->n_x;
@@ -270,8 +270,6 @@ IterArgs make_args(const smpc_factor_t* f) {
   a.step_p = f->step_p;
   a.inv_s = f->inv_s;
   a.inv_z = f->inv_z;
-  a.thr_s = f->thr_s;
-  a.thr_z = f->thr_z;
   a.inv_p = f->inv_p;
   a.mu_s = f->mu_s;
   a.x_s = f->x_s;
@@ -298,6 +296,24 @@ int put_vec(smpc_factor_t* f, void* dst, const double* src, size_t count, cudaSt
     for (size_t i = 0; i < count; ++i) tmp[i] = (float)src[i];
     CK(cudaMemcpyAsync(dst, tmp.data(), count * sizeof(float), cudaMemcpyHostToDevice, s));
     CK(cudaStreamSynchronize(s));
+  }
+  return SMPC_OK;
+}
+
+// Upload float64 host values into a dual-state buffer (float64, or float32 pairs
+// hi + lo with lo = 0 for values that are already float32).
+int put_state(smpc_factor_t* f, void* dst, const double* src, size_t count) {
+  if (count == 0) return SMPC_OK;
+  if (f->prec == SMPC_FP64) {
+    CK(cudaMemcpy(dst, src, count * sizeof(double), cudaMemcpyHostToDevice));
+  } else {
+    std::vector<float> tmp(2 * count);
+    for (size_t i = 0; i < count; ++i) {
+      const float hi = (float)src[i];
+      tmp[2 * i] = hi;
+      tmp[2 * i + 1] = (float)(src[i] - (double)hi);
+    }
+    CK(cudaMemcpy(dst, tmp.data(), tmp.size() * sizeof(float), cudaMemcpyHostToDevice));
   }
   return SMPC_OK;
 }
@@ -364,7 +380,7 @@ int power_iteration(smpc_factor_t* f, int iters, double* out) {
     y0[i] = v;
     nrm += v * v;
   }
-  TRY(put_vec(f, f->ybuf0, y0.data(), ny));
+  TRY(put_state(f, f->ybuf0, y0.data(), ny));
   double* pw = nullptr;
   TRY(f->alloc(&pw, sizeof(double) * 2 * (size_t)(iters + 2)));
   CK(cudaMemset(pw, 0, sizeof(double) * 2 * (size_t)(iters + 2)));
@@ -404,6 +420,51 @@ int power_iteration(smpc_factor_t* f, int iters, double* out) {
 }
 
 }  // namespace
+
+namespace smpc {
+
+int plan_iters(const smpc_factor_t* f, const IterArgs& a, const smpc_solve_opts& opts, IterPlan* plan) {
+  const int iters = opts.max_iters;
+  if (opts.polish_iters < 0 || opts.polish_iters > iters || opts.anchor_every < 0) {
+    set_error("polish_iters must be in [0, max_iters] and anchor_every >= 0");
+    return SMPC_EINVAL;
+  }
+  plan->prec = f->prec;
+  plan->args = a;
+  plan->cfg = iter_config(f->prec, a, f->num_sms);
+  if (plan->cfg.stages < 1) {
+    set_error("network too large for the shared-memory pipeline");
+    return SMPC_ENOTSUP;
+  }
+  plan->polish_from = 0x7fffffff;
+  plan->anchor_every = 0;
+  if (f->packs32) {  // SMPC_BF16: anchored solve, float32 packs for anchors and polish
+    plan->args.ha = f->ha;
+    plan->args.wa = f->wa;
+    plan->args32 = plan->args;
+    plan->args32.packs = f->packs32;
+    plan->args32.pack_stride = f->pack_stride32;
+    plan->cfg32 = iter_config(SMPC_FP32, plan->args32, f->num_sms);
+    if (plan->cfg32.stages < 1) {
+      set_error("network too large for the float32 pipeline");
+      return SMPC_ENOTSUP;
+    }
+    plan->anchor_every = opts.anchor_every > 0 ? opts.anchor_every : 16;
+    if (opts.polish_iters > 0) plan->polish_from = iters - opts.polish_iters;
+  }
+  return SMPC_OK;
+}
+
+int launch_planned(const IterPlan& plan, int nu, int mode, void* stream) {
+  if (plan.anchor_every > 0) {
+    if (nu >= plan.polish_from || nu % plan.anchor_every == 0)
+      return launch_iter(SMPC_FP32, plan.args32, plan.cfg32, nu, mode | MODE_ANCHOR, stream);
+    return launch_iter(plan.prec, plan.args, plan.cfg, nu, mode | MODE_DELTA, stream);
+  }
+  return launch_iter(plan.prec, plan.args, plan.cfg, nu, mode, stream);
+}
+
+}  // namespace smpc
 
 extern "C" {
 
@@ -577,20 +638,31 @@ int smpc_factor(const smpc_tree* tree, const smpc_network* net, const smpc_cost*
   if ((rc = f->alloc(&f->packs, (size_t)n * f->pack_stride * f->ms))) return fail(rc);
   if ((rc = launch_pack(f->prec, n, n_k, n_v, f->K64, f->Lam64, tree->dev.prob, f->packs, f->pack_stride, nullptr)))
     return fail(rc);
+  if (f->prec == SMPC_BF16) {  // float32 packs for the polish iterations
+    f->pack_stride32 = pack_entries(SMPC_FP32, n_k, n_v);
+    if ((rc = f->alloc(&f->packs32, (size_t)n * f->pack_stride32 * sizeof(float)))) return fail(rc);
+    if ((rc = launch_pack(SMPC_FP32, n, n_k, n_v, f->K64, f->Lam64, tree->dev.prob, f->packs32, f->pack_stride32,
+                          nullptr)))
+      return fail(rc);
+    const size_t hb = sizeof(float) * (size_t)n * n_k;
+    if ((rc = f->alloc(&f->ha, hb)) || (rc = f->alloc(&f->wa, hb))) return fail(rc);
+    if (cudaMemset(f->ha, 0, hb) != cudaSuccess || cudaMemset(f->wa, 0, hb) != cudaSuccess) return fail(SMPC_ECUDA);
+  }
   // ---- vectors
   const size_t vs = f->vs;
   void** vecs[] = {&f->ybuf0, &f->ybuf1, &f->wbuf, &f->h, &f->uhat, &f->e, &f->beta, &f->spub, &f->rpub,
                    &f->uout, &f->xout, &f->step_s, &f->step_z, &f->step_p, &f->mu_s, &f->x_s, &f->x_min,
-                   &f->x_max, &f->u_min, &f->u_max, &f->p0, &f->inv_s, &f->inv_z, &f->thr_s, &f->thr_z,
-                   &f->inv_p};
+                   &f->x_max, &f->u_min, &f->u_max, &f->p0, &f->inv_s, &f->inv_z, &f->inv_p};
   const size_t cnts[] = {(size_t)n * nd, (size_t)n * nd, (size_t)n * n_k, (size_t)n * n_k, (size_t)n * n_u,
                          (size_t)n * n_x, (size_t)n * n_v, (size_t)n * n_x, (size_t)n * n_v, (size_t)n * n_u,
                          (size_t)n * n_x, (size_t)n, (size_t)n, (size_t)n * n_u, (size_t)n, (size_t)n_x,
                          (size_t)n_x, (size_t)n_x, (size_t)n_u, (size_t)n_u, (size_t)n_x, (size_t)n,
-                         (size_t)n, (size_t)n, (size_t)n, (size_t)n * n_u};
+                         (size_t)n, (size_t)n * n_u};
+  static_assert(sizeof(vecs) / sizeof(vecs[0]) == sizeof(cnts) / sizeof(cnts[0]), "one count per vector");
   for (size_t i = 0; i < sizeof(cnts) / sizeof(cnts[0]); ++i) {
-    if ((rc = f->alloc(vecs[i], cnts[i] * vs))) return fail(rc);
-    if (cudaMemset(*vecs[i], 0, cnts[i] * vs) != cudaSuccess) {
+    const size_t bytes = cnts[i] * (i < 2 ? kStateSize : vs);  // the two dual buffers hold the state type
+    if ((rc = f->alloc(vecs[i], bytes))) return fail(rc);
+    if (cudaMemset(*vecs[i], 0, bytes) != cudaSuccess) {
       set_error("cudaMemset failed");
       return fail(SMPC_ECUDA);
     }
@@ -692,7 +764,7 @@ int smpc_factor(const smpc_tree* tree, const smpc_network* net, const smpc_cost*
       lam = 1.0 / (L * (1.0 + margin));
       // reset the buffers the power iteration used
       const size_t ny = (size_t)n * nd;
-      if (cudaMemset(f->ybuf0, 0, ny * vs) != cudaSuccess || cudaMemset(f->ybuf1, 0, ny * vs) != cudaSuccess ||
+      if (cudaMemset(f->ybuf0, 0, ny * kStateSize) != cudaSuccess || cudaMemset(f->ybuf1, 0, ny * kStateSize) != cudaSuccess ||
           cudaMemset(f->counters, 0, sizeof(int) * n) != cudaSuccess)
         return fail(SMPC_ECUDA);
     }
@@ -704,17 +776,14 @@ int smpc_factor(const smpc_tree* tree, const smpc_network* net, const smpc_cost*
   if ((rc = put_vec(f, f->step_s, ss.data(), n)) || (rc = put_vec(f, f->step_z, sz.data(), n)) ||
       (rc = put_vec(f, f->step_p, sp.data(), sp.size())))
     return fail(rc);
-  {  // reciprocal steps and prox thresholds mu / step (App. C) used by the prox
-    std::vector<double> is(n), iz(n), ts(n), tz(n), ip(sp.size());
+  {  // reciprocal steps: the prox turns y+ - w = lambda (x - t) into the residual x - t
+    std::vector<double> is(n), iz(n), ip(sp.size());
     for (int m = 0; m < n; ++m) {
       is[m] = 1.0 / ss[m];
       iz[m] = 1.0 / sz[m];
-      ts[m] = mu[m] / ss[m];
-      tz[m] = cost->gamma_d / sz[m];
     }
     for (size_t i = 0; i < sp.size(); ++i) ip[i] = 1.0 / sp[i];
     if ((rc = put_vec(f, f->inv_s, is.data(), n)) || (rc = put_vec(f, f->inv_z, iz.data(), n)) ||
-        (rc = put_vec(f, f->thr_s, ts.data(), n)) || (rc = put_vec(f, f->thr_z, tz.data(), n)) ||
         (rc = put_vec(f, f->inv_p, ip.data(), ip.size())))
       return fail(rc);
   }
@@ -811,11 +880,8 @@ int smpc_solve(smpc_factor_t* f, const smpc_step_data* data, const smpc_solve_op
   CK(cudaMemsetAsync(f->flags, 0xff, sizeof(int), s));
   CK(cudaMemsetAsync(f->flags + 1, 0, sizeof(int), s));
   CK(cudaMemsetAsync(f->res, 0, sizeof(unsigned long long) * 3 * (size_t)(iters + 2), s));
-  LaunchCfg cfg = iter_config(f->prec, a, f->num_sms);
-  if (cfg.stages < 1) {
-    set_error("network too large for the shared-memory pipeline");
-    return SMPC_ENOTSUP;
-  }
+  IterPlan plan;
+  TRY(plan_iters(f, a, *opts, &plan));
   const int chunk = opts->check_every > 0 ? opts->check_every : 128;
   int launched = 0, chunks = 0;
   bool stop = false;
@@ -823,7 +889,7 @@ int smpc_solve(smpc_factor_t* f, const smpc_step_data* data, const smpc_solve_op
     const int upto = std::min(iters, launched + chunk);
     for (int nu = launched; nu < upto; ++nu) {
       int mode = MODE_BWD | MODE_CHECK | (nu > 0 ? MODE_PROX : 0);
-      TRY(launch_iter(f->prec, a, cfg, nu, mode, s));
+      TRY(launch_planned(plan, nu, mode, s));
     }
     launched = upto;
     const int slot = chunks & 1;
@@ -835,7 +901,7 @@ int smpc_solve(smpc_factor_t* f, const smpc_step_data* data, const smpc_solve_op
     CK(cudaEventRecord(f->ev[slot], s));
     ++chunks;
   }
-  TRY(launch_iter(f->prec, a, cfg, launched, MODE_PROX | MODE_CHECK, s));
+  TRY(launch_planned(plan, launched, MODE_PROX | MODE_CHECK, s));
   TRY(launch_copy_final_y(f->prec, a, launched, res->y, s));
   if (res->u) CK(cudaMemcpyAsync(res->u, f->uout, (size_t)n * n_u * f->vs, cudaMemcpyDefault, s));
   if (res->x) CK(cudaMemcpyAsync(res->x, f->xout, (size_t)n * n_x * f->vs, cudaMemcpyDefault, s));

@@ -41,10 +41,6 @@ constexpr int kWarps = kThreads / 32;
 constexpr int kChunk = 1 << 20;          // larger than any matrix of a pack
 constexpr uint64_t kWaitNs = 2000000000ull;  // bounded mbarrier wait: 2 s
 
-__device__ __forceinline__ double to_acc(double v) { return v; }
-__device__ __forceinline__ float to_acc(float v) { return v; }
-__device__ __forceinline__ float to_acc(__nv_bfloat16 v) { return __bfloat162float(v); }
-
 template <typename MT>
 struct Acc;
 template <>
@@ -123,6 +119,86 @@ __device__ __forceinline__ double warp_max(double v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
   return v;
+}
+
+// ------------------------------------------------------------------ dual state
+// Late in a solve the dual iterates move by lambda (H z - t) per iteration, far
+// below the rounding unit of |y| in float32: a float32 dual state rounds those
+// moves away and the iteration stalls well above a useful residual.  Factors with
+// float32 or bfloat16 packs therefore hold y^nu and y^{nu-1} as unevaluated sums
+// hi + lo of two float32 (about 48 significant bits) and update them with
+// error-free transformations built from float32 operations: TwoSum (Knuth, TAOCP
+// vol. 2, Sec. 4.2.2), FastTwoSum and the product error through a fused
+// multiply-add (Dekker, 1971).  float64 factors hold the state in float64.  Both
+// take 8 bytes per entry.  The solve step itself reads w rounded to its vector type.
+struct DS {
+  float hi, lo;
+};
+template <typename VT>
+struct St;
+template <>
+struct St<double> { using T = double; };
+template <>
+struct St<float> { using T = DS; };
+
+// exact sum a + b = s + e, valid when |a| >= |b| or a = 0
+__device__ __forceinline__ DS fast_two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+// exact sum a + b = s + e for any a, b
+__device__ __forceinline__ DS two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  return {s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb))};
+}
+__device__ __forceinline__ DS st_add(DS x, DS y) {
+  const DS t = two_sum(x.hi, y.hi);
+  return fast_two_sum(t.hi, __fadd_rn(t.lo, __fadd_rn(x.lo, y.lo)));
+}
+__device__ __forceinline__ DS st_sub(DS x, DS y) { return st_add(x, DS{-y.hi, -y.lo}); }
+// k x
+__device__ __forceinline__ DS st_scale(DS x, float k) {
+  const float p = __fmul_rn(x.hi, k);
+  const float e = __fmaf_rn(x.lo, k, __fmaf_rn(x.hi, k, -p));
+  return fast_two_sum(p, e);
+}
+// w + l d with the product l d taken exactly
+__device__ __forceinline__ DS st_axpy(DS w, float l, float d) {
+  const float p = __fmul_rn(l, d);
+  const float pe = __fmaf_rn(l, d, -p);
+  const DS t = two_sum(w.hi, p);
+  return fast_two_sum(t.hi, __fadd_rn(t.lo, __fadd_rn(w.lo, pe)));
+}
+__device__ __forceinline__ float st_val(DS x) { return __fadd_rn(x.hi, x.lo); }
+__device__ __forceinline__ bool st_pos(DS x) { return x.hi > 0.f; }
+__device__ __forceinline__ bool st_neg(DS x) { return x.hi < 0.f; }
+template <typename ST>
+__device__ __forceinline__ ST st_from(double v);
+template <>
+__device__ __forceinline__ DS st_from<DS>(double v) { return DS{(float)v, 0.f}; }
+
+__device__ __forceinline__ double st_add(double x, double y) { return x + y; }
+__device__ __forceinline__ double st_sub(double x, double y) { return x - y; }
+__device__ __forceinline__ double st_scale(double x, double k) { return x * k; }
+__device__ __forceinline__ double st_axpy(double w, double l, double d) { return fma(l, d, w); }
+__device__ __forceinline__ double st_val(double x) { return x; }
+__device__ __forceinline__ bool st_pos(double x) { return x > 0.0; }
+__device__ __forceinline__ bool st_neg(double x) { return x < 0.0; }
+template <>
+__device__ __forceinline__ double st_from<double>(double v) { return v; }
+
+// extrapolation y1 + c (y1 - y2) of eq. optim:acceleration
+template <typename ST, typename AT>
+__device__ __forceinline__ ST st_extrap(ST y1, ST y2, AT c) {
+  return st_add(y1, st_scale(st_sub(y1, y2), c));
+}
+// lambda r of a box block (App. C): with q_hi = w + lambda (x - hi) and
+// q_lo = w + lambda (x - lo) (q_hi <= q_lo), lambda r = q_hi where q_hi > 0,
+// q_lo where q_lo < 0, and 0 inside the box.
+template <typename ST>
+__device__ __forceinline__ ST box_lr(ST qh, ST ql) {
+  return st_pos(qh) ? qh : (st_neg(ql) ? ql : st_from<ST>(0.0));
 }
 
 // ------------------------------------------------------------------ CTA mat-vecs
@@ -359,6 +435,7 @@ struct Pipe {
 template <typename VT, typename MT>
 struct Kern {
   using AT = typename Acc<MT>::T;
+  using ST = typename St<VT>::T;  // dual state
   const IterArgs& a;
   Smem<MT>& sm;
   int S, nu, mode;
@@ -369,7 +446,7 @@ struct Kern {
   __device__ Kern(const IterArgs& args, Smem<MT>& s, int S_, int nu_, int mode_)
       : a(args), sm(s), S(S_), nu(nu_), mode(mode_), nd(2 * args.n_x + args.n_u) {}
 
-  __device__ VT* y(int k) const { return reinterpret_cast<VT*>((k & 1) ? a.ybuf1 : a.ybuf0); }
+  __device__ ST* ys(int k) const { return reinterpret_cast<ST*>((k & 1) ? a.ybuf1 : a.ybuf0); }
   __device__ VT* wb() const { return reinterpret_cast<VT*>(a.wbuf); }
   __device__ VT* hb() const { return reinterpret_cast<VT*>(a.h); }
   __device__ const VT* cv(const void* p) const { return reinterpret_cast<const VT*>(p); }
@@ -378,6 +455,31 @@ struct Kern {
     return reinterpret_cast<const MT*>(a.packs) + (long long)n * a.pack_stride;
   }
   __device__ bool linear() const { return (mode & MODE_LINEAR) != 0; }
+  // Anchored solves (bfloat16 packs): an anchor launch evaluates the solve step at
+  // w_a = w^nu with the float32 packs (h_a, stored apart); the launches between run
+  // the bfloat16 packs on w - w_a only, without the affine data, since the solve
+  // step is affine in w: h(w) = h_a + h_lin(w - w_a).
+  __device__ bool anchor() const { return (mode & MODE_ANCHOR) != 0; }
+  __device__ bool delta() const { return (mode & MODE_DELTA) != 0; }
+  __device__ bool no_affine() const { return (mode & (MODE_LINEAR | MODE_DELTA)) != 0; }
+  // h of node m, entry e, as the forward sweep sees it
+  __device__ AT h_at(long long m, int e) const {
+    const long long q = m * a.n_k + e;
+    AT v = (AT)hb()[q];
+    if (a.ha) v += (AT)cv(a.ha)[q];
+    return v;
+  }
+  // stores w^nu (entry e of node m) for the backward sweep of this launch
+  __device__ void put_w(long long m, int e, ST w) const {
+    const long long q = m * a.n_k + e;
+    if (delta()) {
+      wb()[q] = (VT)st_val(st_sub(w, st_from<ST>((double)cv(a.wa)[q])));
+    } else {
+      const VT v = (VT)st_val(w);
+      wb()[q] = v;
+      if (anchor()) mv(a.wa)[q] = v;
+    }
+  }
 
   // ---------------------------------------------------------- cursor helpers
   __device__ Cursor chain_cursor(int chain) const {
@@ -480,7 +582,7 @@ struct Kern {
     const int b = a.path_off[par], en = a.path_off[par + 1];
     for (int q = b; q < en; ++q) {
       const int m = a.path_node[q];
-      const AT hv = (AT)hb()[(long long)m * a.n_k + e];
+      const AT hv = h_at(m, e);
       if (e < a.n_x) {
         V += hv;
         X += V + (linear() ? (AT)0 : (AT)cv(a.e)[(long long)m * a.n_x + e]);
@@ -496,24 +598,15 @@ struct Kern {
   // entries, or its input's box entry.  Loads are batched kB nodes at a time so
   // that their latencies overlap.
   //
-  // Prox arithmetic (App. C) in a cancellation-free form.  With a = w / lambda and
-  // v = a + x, each entry of r = v - P_C(v) is max(a + (x - hi), 0) - max((lo - x) - a, 0),
-  // exactly zero where the entry is inside the box.  With kappa = min(1, theta / ||r||)
-  // (theta = mu / lambda) the prox is t = v - kappa r, hence
-  //   y+ = w + lambda (x - t) = lambda kappa r,
-  //   x - t = -a                             inside,
-  //         = (kappa - 1) a + kappa (x - bound)  at the violated bound,
-  // which is the same arithmetic as App. C without forming w / lambda + x and
-  // subtracting it again (w / lambda can exceed x by many orders of magnitude).
+  // Prox and dual update (App. C; eq. optim:dual:update1-2) without forming
+  // w / lambda + x.  For a block with step lambda, set C and weight mu (mu = 0 for
+  // an indicator), r = v - P_C(v) with v = w / lambda + x, and lambda r follows
+  // from q = w + lambda (x - bound) (box_lr).  The distance prox moves v towards
+  // P_C(v) by min(||r||, mu / lambda), so with kappa = min(1, mu / ||lambda r||)
+  //   y+ = w + lambda (x - t) = kappa lambda r,   x - t = (y+ - w) / lambda.
+  // Every sum that carries w runs in the state type, so y+ keeps the small move
+  // lambda (x - t) however large |w| is.
   static constexpr int kB = 8;
-  __device__ static AT box_r(AT a, AT x, AT lo, AT hi) {
-    return fmax(a + (x - hi), (AT)0) - fmax((lo - x) - a, (AT)0);
-  }
-  __device__ static AT box_res(AT a, AT r, AT kappa, AT x, AT lo, AT hi) {
-    if (r > 0) return (kappa - 1) * a + kappa * (x - hi);
-    if (r < 0) return (kappa - 1) * a + kappa * (x - lo);
-    return -a;
-  }
   __device__ void phase_p(int par, const int* nodes, int len) {
     const int e = threadIdx.x, lane = e & 31, warp = e >> 5;
     const bool tank = e < a.n_x, input = !tank && e < a.n_k;
@@ -522,10 +615,8 @@ struct Kern {
     const int it = nu - 1;  // iteration being finished
     const AT c = lin ? (AT)0 : (AT)a.cvec[it];
     const AT cn = lin ? (AT)0 : (AT)a.cvec[it + 1];
-    const AT inf = (AT)INFINITY;
-    const VT* __restrict__ Hb = hb();
-    VT* Y1 = y(it);       // y^{it}
-    VT* Y2 = y(it + 1);   // y^{it-1} in, y^{it+1} out
+    ST* Y1 = ys(it);       // y^{it}
+    ST* Y2 = ys(it + 1);   // y^{it-1} in, y^{it+1} out
     VT* __restrict__ Xo = mv(a.xout);
     VT* __restrict__ Uo = mv(a.uout);
     AT V = 0, X = 0, U = 0;
@@ -535,34 +626,36 @@ struct Kern {
     const AT xhi = tank ? (AT)cv(a.x_max)[e] : (AT)0;
     const AT ulo = input ? (AT)cv(a.u_min)[i] : (AT)0;
     const AT uhi = input ? (AT)cv(a.u_max)[i] : (AT)0;
+    const ST zero = st_from<ST>(0.0);
     const int tank_warps = (a.n_x + 31) / 32;
     AT rm = 0, hm = 0, tm = 0;
     for (int b0 = 0; b0 < len; b0 += kSeg) {
       const int bl = min(kSeg, len - b0);
       if (e < bl) sm.seg[e] = nodes[b0 + e];
       __syncthreads();
-      // pass A: forward sweep (prefix sums of h) and the two block distances per node
+      // pass A: forward sweep (prefix sums of h) and the two block norms ||lambda r|| per node
       for (int k0 = 0; k0 < bl; k0 += kB) {
         const int q = min(kB, bl - k0);
-        AT hv[kB], ev[kB], s1[kB], s2[kB], z1[kB], z2[kB], isv[kB], izv[kB];
+        AT hv[kB], ev[kB], lsv[kB], lzv[kB];
+        ST s1[kB], s2[kB], z1[kB], z2[kB];
 #pragma unroll
         for (int r = 0; r < kB; ++r) {
-          hv[r] = ev[r] = s1[r] = s2[r] = z1[r] = z2[r] = 0;
-          isv[r] = izv[r] = 1;
+          hv[r] = ev[r] = lsv[r] = lzv[r] = 0;
+          s1[r] = s2[r] = z1[r] = z2[r] = zero;
           if (r < q && e < a.n_k) {
             const int m = sm.seg[k0 + r];
-            hv[r] = (AT)Hb[(long long)m * a.n_k + e];
+            hv[r] = h_at(m, e);
             if (tank) {
               if (!lin) {
                 ev[r] = (AT)cv(a.e)[(long long)m * a.n_x + e];
-                const VT* y1 = Y1 + (long long)m * nd;
-                const VT* y2 = Y2 + (long long)m * nd;
-                s1[r] = (AT)y1[e];
-                s2[r] = (AT)y2[e];
-                z1[r] = (AT)y1[a.n_x + e];
-                z2[r] = (AT)y2[a.n_x + e];
-                isv[r] = (AT)cv(a.inv_s)[m];
-                izv[r] = (AT)cv(a.inv_z)[m];
+                const ST* y1 = Y1 + (long long)m * nd;
+                const ST* y2 = Y2 + (long long)m * nd;
+                s1[r] = y1[e];
+                s2[r] = y2[e];
+                z1[r] = y1[a.n_x + e];
+                z2[r] = y2[a.n_x + e];
+                lsv[r] = (AT)cv(a.step_s)[m];
+                lzv[r] = (AT)cv(a.step_z)[m];
               }
             } else if (!lin) {
               ev[r] = (AT)cv(a.uhat)[(long long)m * a.n_u + i];
@@ -579,9 +672,10 @@ struct Kern {
               X += V + ev[r];
               Xo[(long long)m * a.n_x + e] = (VT)X;
               if (!lin) {
-                const AT as = (s1[r] + c * (s1[r] - s2[r])) * isv[r];
-                const AT az = (z1[r] + c * (z1[r] - z2[r])) * izv[r];
-                const AT rs = box_r(as, X, xs, inf), rz = box_r(az, X, xlo, xhi);
+                const ST ws = st_extrap(s1[r], s2[r], c), wz = st_extrap(z1[r], z2[r], c);
+                const ST qs = st_axpy(ws, lsv[r], X - xs);
+                const AT rs = st_neg(qs) ? (AT)st_val(qs) : (AT)0;  // C = {x >= x_s}
+                const AT rz = (AT)st_val(box_lr(st_axpy(wz, lzv[r], X - xhi), st_axpy(wz, lzv[r], X - xlo)));
                 ps = rs * rs;
                 pz = rz * rz;
               }
@@ -601,7 +695,7 @@ struct Kern {
         }
       }
       __syncthreads();
-      if (!lin && e < bl) {  // one thread per node: kappa = min(1, theta / ||r||) of both blocks
+      if (!lin && e < bl) {  // one thread per node: kappa = min(1, mu / ||lambda r||) of both blocks
         const int m = sm.seg[e];
         AT ds2 = 0, dz2 = 0;
         for (int w = 0; w < tank_warps; ++w) {
@@ -609,30 +703,32 @@ struct Kern {
           dz2 += sm.red[(e * kWarps + w) * 2 + 1];
         }
         const AT ds = sqrt(ds2), dz = sqrt(dz2);
-        const AT ths = (AT)cv(a.thr_s)[m], thz = (AT)cv(a.thr_z)[m];
-        sm.kap[2 * e + 0] = ds > ths ? ths / ds : (AT)1;
-        sm.kap[2 * e + 1] = dz > thz ? thz / dz : (AT)1;
+        const AT mus = (AT)cv(a.mu_s)[m], muz = (AT)a.gamma_d;
+        sm.kap[2 * e + 0] = ds > mus ? mus / ds : (AT)1;
+        sm.kap[2 * e + 1] = dz > muz ? muz / dz : (AT)1;
       }
       __syncthreads();
       // pass B: prox (App. C), dual update, extrapolation w^{it+1}
       if (e < a.n_k) {
         for (int k0 = 0; k0 < bl; k0 += kB) {
           const int q = min(kB, bl - k0);
-          AT zv[kB], v1[kB], v2[kB], w1[kB], w2[kB], l1[kB], l2[kB], i1[kB], i2[kB];
+          AT zv[kB], l1[kB], l2[kB], i1[kB], i2[kB];
+          ST v1[kB], v2[kB], w1[kB], w2[kB];
 #pragma unroll
           for (int r = 0; r < kB; ++r) {
-            zv[r] = v1[r] = v2[r] = w1[r] = w2[r] = 0;
+            zv[r] = 0;
+            v1[r] = v2[r] = w1[r] = w2[r] = zero;
             l1[r] = l2[r] = i1[r] = i2[r] = 1;
             if (r < q) {
               const int m = sm.seg[k0 + r];
-              const VT* y1 = Y1 + (long long)m * nd;
-              const VT* y2 = Y2 + (long long)m * nd;
+              const ST* y1 = Y1 + (long long)m * nd;
+              const ST* y2 = Y2 + (long long)m * nd;
               if (tank) {
                 zv[r] = (AT)Xo[(long long)m * a.n_x + e];
-                v1[r] = (AT)y1[e];
-                v2[r] = (AT)y2[e];
-                w1[r] = (AT)y1[a.n_x + e];
-                w2[r] = (AT)y2[a.n_x + e];
+                v1[r] = y1[e];
+                v2[r] = y2[e];
+                w1[r] = y1[a.n_x + e];
+                w2[r] = y2[a.n_x + e];
                 l1[r] = (AT)cv(a.step_s)[m];
                 l2[r] = (AT)cv(a.step_z)[m];
                 if (!lin) {
@@ -641,8 +737,8 @@ struct Kern {
                 }
               } else {
                 zv[r] = (AT)Uo[(long long)m * a.n_u + i];
-                v1[r] = (AT)y1[2 * a.n_x + i];
-                v2[r] = (AT)y2[2 * a.n_x + i];
+                v1[r] = y1[2 * a.n_x + i];
+                v2[r] = y2[2 * a.n_x + i];
                 l1[r] = (AT)cv(a.step_p)[(long long)m * a.n_u + i];
                 if (!lin) i1[r] = (AT)cv(a.inv_p)[(long long)m * a.n_u + i];
               }
@@ -653,54 +749,49 @@ struct Kern {
             if (r >= q) continue;
             const int k = k0 + r;
             const int m = sm.seg[k];
-            VT* y2 = Y2 + (long long)m * nd;
-            VT* wm = wb() + (long long)m * a.n_k;
+            ST* y2 = Y2 + (long long)m * nd;
             if (lin) {
               // power iteration: y_{k+1} = -D^{1/2} H z, with D held in the step arrays
               if (tank) {
                 const AT a1 = -sqrt(l1[r]) * zv[r], a2 = -sqrt(l2[r]) * zv[r];
-                pdot += (double)a1 * (double)v1[r] + (double)a2 * (double)w1[r];
+                pdot += (double)a1 * (double)st_val(v1[r]) + (double)a2 * (double)st_val(w1[r]);
                 pnrm += (double)a1 * a1 + (double)a2 * a2;
-                y2[e] = (VT)a1;
-                y2[a.n_x + e] = (VT)a2;
+                y2[e] = st_from<ST>(a1);
+                y2[a.n_x + e] = st_from<ST>(a2);
               } else {
                 const AT a3 = -sqrt(l1[r]) * zv[r];
-                pdot += (double)a3 * (double)v1[r];
+                pdot += (double)a3 * (double)st_val(v1[r]);
                 pnrm += (double)a3 * a3;
-                y2[2 * a.n_x + i] = (VT)a3;
+                y2[2 * a.n_x + i] = st_from<ST>(a3);
               }
               continue;
             }
+            const AT x = zv[r];
             if (tank) {
               const AT ks = sm.kap[2 * k + 0], kz = sm.kap[2 * k + 1];
-              const AT x = zv[r];
-              const AT ws = v1[r] + c * (v1[r] - v2[r]);
-              const AT wz = w1[r] + c * (w1[r] - w2[r]);
-              const AT as = ws * i1[r], az = wz * i2[r];
-              const AT rs = box_r(as, x, xs, inf), rz = box_r(az, x, xlo, xhi);
-              const AT es = box_res(as, rs, ks, x, xs, inf), ez = box_res(az, rz, kz, x, xlo, xhi);
-              const AT ysn = l1[r] * ks * rs;
-              const AT yzn = l2[r] * kz * rz;
-              y2[e] = (VT)ysn;
-              y2[a.n_x + e] = (VT)yzn;
-              wm[e] = (VT)((ysn + cn * (ysn - v1[r])) + (yzn + cn * (yzn - w1[r])));
+              const ST ws = st_extrap(v1[r], v2[r], c), wz = st_extrap(w1[r], w2[r], c);
+              const ST qs = st_axpy(ws, l1[r], x - xs);
+              const ST ysn = st_scale(st_neg(qs) ? qs : zero, ks);
+              const ST yzn = st_scale(box_lr(st_axpy(wz, l2[r], x - xhi), st_axpy(wz, l2[r], x - xlo)), kz);
+              const AT es = (AT)st_val(st_sub(ysn, ws)) * i1[r];
+              const AT ez = (AT)st_val(st_sub(yzn, wz)) * i2[r];
+              y2[e] = ysn;
+              y2[a.n_x + e] = yzn;
+              put_w(m, e, st_add(st_extrap(ysn, v1[r], cn), st_extrap(yzn, w1[r], cn)));
               rm = fmax(rm, fmax(fabs(es), fabs(ez)));
               hm = fmax(hm, fabs(x));
               tm = fmax(tm, fmax(fabs(x - es), fabs(x - ez)));
-              if (!isfinite(ysn) || !isfinite(yzn)) a.flags[1] = SMPC_EDIVERGED;
+              if (!isfinite(st_val(ysn)) || !isfinite(st_val(yzn))) a.flags[1] = SMPC_EDIVERGED;
             } else {
-              const AT u = zv[r];
-              const AT wp = v1[r] + c * (v1[r] - v2[r]);
-              const AT ap = wp * i1[r];
-              const AT rp = box_r(ap, u, ulo, uhi);
-              const AT ep = box_res(ap, rp, (AT)1, u, ulo, uhi);
-              const AT ypn = l1[r] * rp;
-              y2[2 * a.n_x + i] = (VT)ypn;
-              wm[e] = (VT)(ypn + cn * (ypn - v1[r]));
+              const ST wp = st_extrap(v1[r], v2[r], c);
+              const ST ypn = box_lr(st_axpy(wp, l1[r], x - uhi), st_axpy(wp, l1[r], x - ulo));
+              const AT ep = (AT)st_val(st_sub(ypn, wp)) * i1[r];
+              y2[2 * a.n_x + i] = ypn;
+              put_w(m, e, st_extrap(ypn, v1[r], cn));
               rm = fmax(rm, fabs(ep));
-              hm = fmax(hm, fabs(u));
-              tm = fmax(tm, fabs(u - ep));
-              if (!isfinite(ypn)) a.flags[1] = SMPC_EDIVERGED;
+              hm = fmax(hm, fabs(x));
+              tm = fmax(tm, fabs(x - ep));
+              if (!isfinite(st_val(ypn))) a.flags[1] = SMPC_EDIVERGED;
             }
           }
         }
@@ -718,29 +809,23 @@ struct Kern {
     if (e >= a.n_k) return;
     for (int k = 0; k < len; ++k) {
       const int m = nodes[k];
-      VT* wm = wb() + (long long)m * a.n_k;
-      const VT* ya = y(nu) + (long long)m * nd;
-      AT w;
+      const ST* ya = ys(nu) + (long long)m * nd;
       if (linear()) {
         const AT inv = (AT)rsqrt(a.pw[nu]);
+        AT w;
         if (e < a.n_x)
-          w = sqrt((AT)cv(a.step_s)[m]) * (AT)ya[e] + sqrt((AT)cv(a.step_z)[m]) * (AT)ya[a.n_x + e];
+          w = sqrt((AT)cv(a.step_s)[m]) * (AT)st_val(ya[e]) + sqrt((AT)cv(a.step_z)[m]) * (AT)st_val(ya[a.n_x + e]);
         else
-          w = sqrt((AT)cv(a.step_p)[(long long)m * a.n_u + (e - a.n_x)]) * (AT)ya[2 * a.n_x + (e - a.n_x)];
-        w *= inv;
+          w = sqrt((AT)cv(a.step_p)[(long long)m * a.n_u + (e - a.n_x)]) * (AT)st_val(ya[2 * a.n_x + (e - a.n_x)]);
+        wb()[(long long)m * a.n_k + e] = (VT)(w * inv);
       } else {
         const AT c = (AT)a.cvec[nu];
-        const VT* yb = y(nu + 1) + (long long)m * nd;
-        if (e < a.n_x) {
-          const AT s1 = (AT)ya[e], z1 = (AT)ya[a.n_x + e];
-          w = (s1 + c * (s1 - (AT)yb[e])) + (z1 + c * (z1 - (AT)yb[a.n_x + e]));
-        } else {
-          const int i = e - a.n_x;
-          const AT p1 = (AT)ya[2 * a.n_x + i];
-          w = p1 + c * (p1 - (AT)yb[2 * a.n_x + i]);
-        }
+        const ST* yb = ys(nu + 1) + (long long)m * nd;
+        if (e < a.n_x)
+          put_w(m, e, st_add(st_extrap(ya[e], yb[e], c), st_extrap(ya[a.n_x + e], yb[a.n_x + e], c)));
+        else
+          put_w(m, e, st_extrap(ya[2 * a.n_x + (e - a.n_x)], yb[2 * a.n_x + (e - a.n_x)], c));
       }
-      wm[e] = (VT)w;
     }
   }
 
@@ -762,7 +847,14 @@ struct Kern {
     matvec_t<MT, AT>(sm.Lm(ls), a.n_v, a.n_v, sm.ld, sm.rv, sm.dv, sm.part);  // Lambda is symmetric
     if (refill) issue_l(p);
     matvec_n<MT, AT>(sm.K(ks), a.n_k, sm.ld, sm.dv, sm.yv);
-    if (e < a.n_k) hb()[(long long)m * a.n_k + e] = (VT)sm.yv[e];
+    if (e < a.n_k) {
+      if (anchor()) {  // h_a = h(w_a); the part on w - w_a starts at zero
+        mv(a.ha)[(long long)m * a.n_k + e] = (VT)sm.yv[e];
+        hb()[(long long)m * a.n_k + e] = (VT)0;
+      } else {
+        hb()[(long long)m * a.n_k + e] = (VT)sm.yv[e];
+      }
+    }
     if (refill) issue_k(p);
     __syncthreads();  // yv is rewritten by the next node
   }
@@ -770,7 +862,7 @@ struct Kern {
   __device__ void chain_backward(Pipe& p, const int* nodes, int len) {
     const int e = threadIdx.x;
     AT sreg = 0, rreg = 0;
-    const bool lin = linear();
+    const bool lin = no_affine();
     int m = nodes[len - 1];
     AT wcur = e < a.n_k ? (AT)wb()[(long long)m * a.n_k + e] : (AT)0;
     AT bcur = (e < a.n_v && !lin) ? (AT)cv(a.beta)[(long long)m * a.n_v + e] : (AT)0;
@@ -822,7 +914,7 @@ struct Kern {
     flush(p, next);
     if (abort_) return;
     const int e = threadIdx.x;
-    const bool lin = linear();
+    const bool lin = no_affine();
     while (t >= 0) {
       if (threadIdx.x == 0) {
         fence_proxy_async();
@@ -1059,6 +1151,7 @@ __global__ void cost_beta_kernel(CostArgs a) {
 
 template <typename VT>
 __global__ void final_y_kernel(IterArgs a, int max_iters, VT* dst) {
+  using ST = typename St<VT>::T;
   __shared__ int it;
   if (threadIdx.x == 0) {
     it = a.flags[0];
@@ -1067,22 +1160,23 @@ __global__ void final_y_kernel(IterArgs a, int max_iters, VT* dst) {
   __syncthreads();
   if (blockIdx.x == 0 && threadIdx.x == 0) a.flags[0] = it;
   if (!dst) return;
-  const VT* src = reinterpret_cast<const VT*>((it & 1) ? a.ybuf1 : a.ybuf0);
+  const ST* src = reinterpret_cast<const ST*>((it & 1) ? a.ybuf1 : a.ybuf0);
   const long long total = (long long)a.n * (2 * a.n_x + a.n_u);
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x)
-    dst[i] = src[i];
+    dst[i] = (VT)st_val(src[i]);
 }
 
 template <typename VT>
 __global__ void init_duals_kernel(IterArgs a, int warm) {
   // cold: y^0 = y^{-1} = 0 ; warm: both = the final dual of the previous solve
+  using ST = typename St<VT>::T;
   const long long total = (long long)a.n * (2 * a.n_x + a.n_u);
   int it = a.flags[0];
-  const VT* src = reinterpret_cast<const VT*>((it & 1) ? a.ybuf1 : a.ybuf0);
-  VT* y0 = reinterpret_cast<VT*>(a.ybuf0);
-  VT* y1 = reinterpret_cast<VT*>(a.ybuf1);
+  const ST* src = reinterpret_cast<const ST*>((it & 1) ? a.ybuf1 : a.ybuf0);
+  ST* y0 = reinterpret_cast<ST*>(a.ybuf0);
+  ST* y1 = reinterpret_cast<ST*>(a.ybuf1);
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x) {
-    const VT v = warm ? src[i] : (VT)0;
+    const ST v = warm ? src[i] : st_from<ST>(0.0);
     y0[i] = v;
     y1[i] = v;
   }

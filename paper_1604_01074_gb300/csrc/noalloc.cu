@@ -219,7 +219,7 @@ extern "C" int smpc_solve_static(smpc_factor_t* f, const smpc_step_data* data, c
 
   // iteration-kernel arguments: the factor's state, the scratch from the static array
   const smpc_tree* t = f->tree;
-  IterArgs a;
+  IterArgs a{};
   std::memset(&a, 0, sizeof a);
   a.n = n;
   a.n_x = n_x;
@@ -252,8 +252,6 @@ extern "C" int smpc_solve_static(smpc_factor_t* f, const smpc_step_data* data, c
   a.step_p = f->step_p;
   a.inv_s = f->inv_s;
   a.inv_z = f->inv_z;
-  a.thr_s = f->thr_s;
-  a.thr_z = f->thr_z;
   a.inv_p = f->inv_p;
   a.mu_s = f->mu_s;
   a.x_s = f->x_s;
@@ -280,18 +278,15 @@ extern "C" int smpc_solve_static(smpc_factor_t* f, const smpc_step_data* data, c
   SCK(cudaMemsetAsync(flags, 0xff, sizeof(int), s));
   SCK(cudaMemsetAsync(flags + 1, 0, sizeof(int), s));
   SCK(cudaMemsetAsync(resv, 0, sizeof(unsigned long long) * 3 * ((size_t)iters + 2), s));
-  LaunchCfg cfg = iter_config(f->prec, a, f->num_sms);
-  if (cfg.stages < 1) {
-    set_error("network too large for the shared-memory pipeline");
-    return SMPC_ENOTSUP;
-  }
+  IterPlan plan;
+  STRY(plan_iters(f, a, *opts, &plan));
   const int chunk = opts->check_every > 0 ? opts->check_every : 128;
   int launched = 0, chunks = 0;
   bool stop = false;
   while (launched < iters && !stop) {
     const int upto = iters < launched + chunk ? iters : launched + chunk;
     for (int nu = launched; nu < upto; ++nu)
-      STRY(launch_iter(f->prec, a, cfg, nu, MODE_BWD | MODE_CHECK | (nu > 0 ? MODE_PROX : 0), s));
+      STRY(launch_planned(plan, nu, MODE_BWD | MODE_CHECK | (nu > 0 ? MODE_PROX : 0), s));
     launched = upto;
     const int slot = chunks & 1;
     if (chunks >= 2) {
@@ -302,7 +297,7 @@ extern "C" int smpc_solve_static(smpc_factor_t* f, const smpc_step_data* data, c
     SCK(cudaEventRecord(f->ev[slot], s));
     ++chunks;
   }
-  STRY(launch_iter(f->prec, a, cfg, launched, MODE_PROX | MODE_CHECK, s));
+  STRY(launch_planned(plan, launched, MODE_PROX | MODE_CHECK, s));
   STRY(launch_copy_final_y(f->prec, a, launched, res->y, s));
   // keep the factor's record of its final iterate current (warm starts of either entry point)
   SCK(cudaMemcpyAsync(f->flags, flags, 2 * sizeof(int), cudaMemcpyDeviceToDevice, s));

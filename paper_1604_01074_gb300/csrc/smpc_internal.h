@@ -80,10 +80,12 @@ struct IterArgs {
   const int* path_node;
   const void* packs;             // per node: [Bbar; L] (n_k x n_v) then Lambda/(2 p_n) (n_v x n_v)
   long long pack_stride;         // entries between consecutive nodes' packs
-  void* ybuf0;                   // y^k for even k: n x (2 n_x + n_u)
-  void* ybuf1;                   // y^k for odd k
+  void* ybuf0;                   // y^k for even k: n x (2 n_x + n_u) of the state type
+  void* ybuf1;                   // y^k for odd k (float64, or float32 pairs hi + lo)
   void* wbuf;                    // w^nu restricted to (xi, psi): n x n_k
-  void* h;                       // [Bbar delta; L delta]: n x n_k
+  void* h;                       // [Bbar delta; L delta]: n x n_k (anchored: the part on w - w_a)
+  void* ha;                      // anchored solves: h at the anchor w_a (n x n_k), else NULL
+  void* wa;                      // anchored solves: the anchor w_a (n x n_k)
   const void* uhat;              // n x n_u
   const void* e;                 // n x n_x
   const void* beta;              // n x n_v
@@ -96,10 +98,8 @@ struct IterArgs {
   const void* step_p;            // n x n_u
   const void* inv_s;             // n: 1 / step_s
   const void* inv_z;             // n: 1 / step_z
-  const void* thr_s;             // n: mu_s / step_s (prox threshold of the safety block)
-  const void* thr_z;             // n: gamma_d / step_z
   const void* inv_p;             // n x n_u: 1 / step_p
-  const void* mu_s;              // n
+  const void* mu_s;              // n: weight mu_S,n of the safety distance block
   const void* x_s;
   const void* x_min;
   const void* x_max;
@@ -120,7 +120,9 @@ enum KernelMode : int {
   MODE_PROX = 1,      // forward of iteration nu-1, prox, dual update (Phase P)
   MODE_BWD = 2,       // backward sweep of iteration nu
   MODE_LINEAR = 4,    // power iteration on the (scaled) dual Hessian: no affine data, no prox
-  MODE_CHECK = 8      // honour the stop flag / tolerance
+  MODE_CHECK = 8,     // honour the stop flag / tolerance
+  MODE_ANCHOR = 16,   // anchored solve: evaluate the whole solve step at w_a = w^nu into ha
+  MODE_DELTA = 32     // anchored solve: solve step on w^nu - w_a, without the affine data
 };
 
 struct LaunchCfg {
@@ -164,8 +166,26 @@ long long pack_entries(int prec, int n_k, int n_v);
 int launch_init_duals(int prec, const IterArgs& a, int warm, void* stream);
 int launch_convert(int prec, const double* src, void* dst, long long count, void* stream);
 size_t vec_size(int prec);
+
+// The launch plan of one solve (api.cpp): iteration launches nu >= polish_from of a
+// SMPC_BF16 factor run the float32-pack kernel on the same vectors (args32, cfg32).
+struct IterPlan {
+  int prec = SMPC_FP64;
+  IterArgs args{}, args32{};
+  LaunchCfg cfg, cfg32;
+  int polish_from = 0x7fffffff;
+  int anchor_every = 0;  // > 0: anchored solve (SMPC_BF16)
+};
+constexpr size_t kStateSize = 8;  // bytes per dual-state entry (float64, or two float32)
 size_t mat_size(int prec);
 
+}  // namespace smpc
+
+namespace smpc {
+// Validates polish_iters and the kernel configuration; SMPC_ENOTSUP when the network
+// does not fit the shared-memory pipeline.
+int plan_iters(const smpc_factor_t* f, const IterArgs& a, const smpc_solve_opts& opts, IterPlan* plan);
+int launch_planned(const IterPlan& plan, int nu, int mode, void* stream);
 }  // namespace smpc
 
 // Factor state shared by the solve entry points (api.cpp, noalloc.cu).
@@ -181,13 +201,16 @@ struct smpc_factor_t {
   std::vector<void*> allocs;
   // device
   void* packs = nullptr;
+  void* packs32 = nullptr;    // SMPC_BF16 only: float32 packs (anchor and polish launches)
+  long long pack_stride32 = 0;
+  void *ha = nullptr, *wa = nullptr;  // SMPC_BF16 only: anchor h and w, n x n_k each
   double *K64 = nullptr, *Lam64 = nullptr, *Pu = nullptr, *Pe = nullptr, *Rhat = nullptr, *L = nullptr;
   double *alpha1 = nullptr, *uhat64 = nullptr, *abar = nullptr;
   double *d_p = nullptr, *d_q = nullptr, *d_dhat = nullptr, *d_eps = nullptr, *d_alpha2 = nullptr;
   void *ybuf0 = nullptr, *ybuf1 = nullptr, *wbuf = nullptr, *h = nullptr, *uhat = nullptr, *e = nullptr, *beta = nullptr;
   void *spub = nullptr, *rpub = nullptr, *uout = nullptr, *xout = nullptr;
   void *step_s = nullptr, *step_z = nullptr, *step_p = nullptr, *mu_s = nullptr;
-  void *inv_s = nullptr, *inv_z = nullptr, *thr_s = nullptr, *thr_z = nullptr, *inv_p = nullptr;
+  void *inv_s = nullptr, *inv_z = nullptr, *inv_p = nullptr;
   std::vector<double> mu_host;
   void *x_s = nullptr, *x_min = nullptr, *x_max = nullptr, *u_min = nullptr, *u_max = nullptr, *p0 = nullptr;
   double gamma_d = 0;
