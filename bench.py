@@ -85,18 +85,31 @@ def step_inputs(P, k):
     return {"p": p, "q": P["q"], "dhat": dhat, "alpha2": alpha2}
 
 
+ANCHOR_EVERY = 16  # the library's default anchor interval of bfloat16 solves
+
+
 def algorithmic_bytes_per_iteration(n, n_x, n_u, n_v, prec):
-    """Bytes one APG iteration must move: every pack entry once, plus the node vectors."""
-    ms = {0: 8, 1: 4, 2: 2}[prec]
+    """Bytes one APG iteration must move: every pack entry once ([Bbar; L] is read
+    once and used for both of its mat-vecs), the node vectors in the vector type and
+    the dual state (8 bytes per entry).  bfloat16 solves average one float32-pack
+    anchor iteration per ANCHOR_EVERY and read the anchor h and w besides."""
     vs = 8 if prec == 0 else 4
     n_k = n_x + n_u
     nd = 2 * n_x + n_u
     mat = n_k * n_v + n_v * n_v
-    # forward+prox reads h, e, u_hat, y^nu-1, y^nu-2, steps (n_u + 2), mu; writes u, x, y^nu, w
-    # backward reads w, beta; writes h
-    vec_r = n_k + n_x + n_u + 2 * nd + n_u + 3 + n_k + n_v
-    vec_w = n_k + nd + n_k + n_k
-    return n * (mat * ms + (vec_r + vec_w) * vs), n * mat, n * 2 * (n_k * n_v + n_v * n_v + n_k * n_v)
+    if prec == 2:
+        ms = (2 * (ANCHOR_EVERY - 1) + 4) / ANCHOR_EVERY
+    else:
+        ms = {0: 8, 1: 4}[prec]
+    # forward+prox reads h, e, u_hat, steps (n_u + 2) and reciprocals (n_u + 2), mu;
+    # writes u, x, w.  The dual state: reads y^nu, y^{nu-1}; writes y^{nu+1}.
+    # backward reads w, beta; writes h.
+    vec_r = n_k + n_x + n_u + 2 * (n_u + 2) + 1 + n_k + n_v
+    vec_w = n_k + n_k + n_k
+    if prec == 2:
+        vec_r += 2 * n_k  # anchor h and w
+    state = 3 * nd * 8
+    return n * (mat * ms + (vec_r + vec_w) * vs + state), n * mat, n * 2 * (n_k * n_v + n_v * n_v + n_k * n_v)
 
 
 # --------------------------------------------------------------------- CPU oracle leg
@@ -385,23 +398,28 @@ def run_ours(args, rank, world, local_rank):
     log("headline", {k: result[k] for k in ("value", "ms_per_step", "iterations_mean", "p50_ms", "p99_ms")})
     S.close()
     if args.other_legs and rank == 0:
-        # the other precisions on the same workload: iteration cost, HBM roofline, and the
-        # residual they reach after as many iterations as the headline solve needed
+        # the other precisions on the same workload: iteration cost, roofline, and one
+        # solve of the first step's input to the same tolerance
         legs = {}
-        n_it = int(max(iters)) if iters else 1000
+        sols = {}
         for other in (0, 1, 2):
-            if other == prec:
-                continue
             So = Solver(P, other, device)
+            if other == prec:  # the headline precision on the legs' input, for the error statement
+                So.solve(dev_in[0], args.max_iters, args.tol, stream)
+                So.finish()
+                sols[other] = (So.u.double().cpu().numpy(), So.x.double().cpu().numpy())
+                So.close()
+                continue
             lo, hi = (20, 60) if other == 0 else (100, 400)
             t_o = time_per_iteration(So, dev_in[0], stream, lo=lo, hi=hi, reps=2)
             b_o, _, f_o = algorithmic_bytes_per_iteration(So.n, So.n_x, So.n_u, n_v, other)
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            So.solve(dev_in[0], n_it, args.tol, stream)
+            So.solve(dev_in[0], args.max_iters, args.tol, stream)
             e1.record(stream)
             inf_o = So.finish()
+            sols[other] = (So.u.double().cpu().numpy(), So.x.double().cpu().numpy())
             leg = {"us_per_iteration": 1000.0 * t_o, "iterations_run": inf_o["iterations"],
                    "rho_rel": inf_o["rho_rel"], "reached_tol": inf_o["rho_rel"] <= args.tol,
                    "ms_for_run": e0.elapsed_time(e1)}
@@ -415,7 +433,19 @@ def run_ours(args, rank, world, local_rank):
             legs[PREC_NAMES[other]] = leg
             log("leg", PREC_NAMES[other], leg)
             So.close()
+        # every precision's result against the float64 solve of the same input (which
+        # the parity tests tie to the oracle), relative to 1 + max |.|, and the residual
+        # of the demand coupling E u + E_d d = 0
+        d = P["dhat"][P["tree"]["stage"]] + P["eps"]
+        u64, x64 = sols[0]
+        errs = {}
+        for k, (u, x) in sols.items():
+            errs[PREC_NAMES[k]] = {
+                "u": float(np.abs(u - u64).max() / (1 + np.abs(u64).max())),
+                "x": float(np.abs(x - x64).max() / (1 + np.abs(x64).max())),
+                "coupling": float(np.abs(u @ P["net"]["E"].T + d @ P["net"]["Ed"].T).max())}
         result["other_precisions"] = legs
+        result["error_vs_fp64_solve"] = errs
     if rank == 0 and not args.no_cpu_baseline:
         it_ref = int(np.mean(iters))
         stored, _ = oracle_iters_to_tol(args.config)
@@ -487,7 +517,7 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--precision", choices=["fp64", "fp32", "bf16"], default="fp64")
+    ap.add_argument("--precision", choices=["fp64", "fp32", "bf16"], default="fp32")
     ap.add_argument("--config", choices=["barcelona", "tiny", "large"], default="barcelona")
     ap.add_argument("--tol", type=float, default=1e-3)
     ap.add_argument("--max-iters", type=int, default=100000)
