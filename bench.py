@@ -228,7 +228,7 @@ def aggregate(local_units, local_seconds, backend_device=None):
 
 # --------------------------------------------------------------------- our arm
 class Solver:
-    def __init__(self, P, precision, device):
+    def __init__(self, P, precision, device, schedule=0):
         import torch
 
         import paper_1604_01074_gb300 as smpc
@@ -237,7 +237,8 @@ class Solver:
         self.n, self.n_x, self.n_u = len(t["parent"]), net["n_x"], net["n_u"]
         self.tree = smpc.smpc_tree_create(t["parent"], t["prob"])
         self.info = smpc.smpc_tree_info_get(self.tree)
-        self.fac = smpc.smpc_factor(self.tree, net, P["cost"], precision=precision, precondition=1)
+        self.fac = smpc.smpc_factor(self.tree, net, P["cost"], precision=precision, precondition=1, schedule=schedule)
+        self.schedule, self.tuned_ms = smpc.smpc_factor_schedule(self.fac)
         dt = torch.float64 if precision == 0 else torch.float32
         self.u = torch.empty((self.n, self.n_u), dtype=dt, device=device)
         self.x = torch.empty((self.n, self.n_x), dtype=dt, device=device)
@@ -307,7 +308,7 @@ def run_ours(args, rank, world, local_rank):
         dist.init_process_group("nccl", device_id=device)
     prec = {"fp64": 0, "fp32": 1, "bf16": 2}[args.precision]
     P = make_problem(args.config, seed=0)
-    S = Solver(P, prec, device)
+    S = Solver(P, prec, device, args.schedule)
     stream = torch.cuda.current_stream(device)
     n_steps = args.steps + args.warmup
     inputs = [step_inputs(P, k) for k in range(n_steps)]
@@ -465,7 +466,7 @@ def profile_solve(args):
     device = torch.device("cuda", 0)
     prec = {"fp64": 0, "fp32": 1, "bf16": 2}[args.precision]
     P = make_problem(args.config, seed=0)
-    S = Solver(P, prec, device)
+    S = Solver(P, prec, device, args.schedule)
     stream = torch.cuda.current_stream(device)
     S.solve(S.device_inputs(step_inputs(P, 0)), args.profile_solve, 0.0, stream)
     info = S.finish()
@@ -520,6 +521,8 @@ def main():
     ap.add_argument("--precision", choices=["fp64", "fp32", "bf16"], default="fp32")
     ap.add_argument("--config", choices=["barcelona", "tiny", "large"], default="barcelona")
     ap.add_argument("--tol", type=float, default=1e-3)
+    ap.add_argument("--schedule", type=int, choices=[0, 1, 2], default=0,
+                    help="iteration schedule: 0 = the factor times both and keeps the faster")
     ap.add_argument("--max-iters", type=int, default=100000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-other-precisions", dest="other_legs", action="store_false")

@@ -36,7 +36,7 @@ class smpc_cost(ctypes.Structure):
 class smpc_factor_opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int32), ("precondition", ctypes.c_int32), ("lambda_", ctypes.c_double),
                 ("power_iters", ctypes.c_int32), ("lambda_margin", ctypes.c_double),
-                ("step_s", _dp), ("step_z", _dp), ("step_p", _dp)]
+                ("step_s", _dp), ("step_z", _dp), ("step_p", _dp), ("schedule", ctypes.c_int32)]
 
 
 class smpc_step_data(ctypes.Structure):
@@ -69,6 +69,9 @@ SIGNATURES = {
                                    ctypes.POINTER(smpc_factor_opts), ctypes.POINTER(ctypes.c_void_p)]),
     "smpc_factor_destroy": (None, [ctypes.c_void_p]),
     "smpc_factor_steps": (ctypes.c_int, [ctypes.c_void_p, _dp, _dp, _dp, _dp]),
+    "smpc_factor_schedule": (ctypes.c_int, [ctypes.c_void_p, _dp]),
+    "smpc_profile_solve": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(smpc_step_data), ctypes.c_int32, _dp,
+                                          ctypes.c_int32]),
     "smpc_solve": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(smpc_step_data), ctypes.POINTER(smpc_solve_opts),
                                   ctypes.POINTER(smpc_result), ctypes.c_void_p]),
     "smpc_solve_info": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(smpc_result)]),
@@ -152,9 +155,10 @@ def smpc_tree_destroy(tree):
 
 
 def smpc_factor(tree, net, cost, precision=SMPC_FP64, precondition=1, lam=0.0, power_iters=0, lambda_margin=0.0,
-                steps=None, safety_unweighted=0):
+                steps=None, safety_unweighted=0, schedule=0):
     """net / cost: dicts with the fields of smpc_network / smpc_cost (numpy arrays).
-    steps: optional dict {'s': (n,), 'z': (n,), 'p': (n, n_u)} of explicit per-entry steps."""
+    steps: optional dict {'s': (n,), 'z': (n,), 'p': (n, n_u)} of explicit per-entry steps.
+    schedule: 0 = time both iteration schedules and keep the faster, 1 = chain, 2 = node."""
     k = _Keep()
     A = net.get("A")
     n_x, n_u = net["B"].shape
@@ -166,7 +170,7 @@ def smpc_factor(tree, net, cost, precision=SMPC_FP64, precondition=1, lam=0.0, p
                   k(cost["x_min"]), k(cost["x_max"]), k(cost["x_s"]), k(cost["u_min"]), k(cost["u_max"]),
                   int(safety_unweighted))
     O = smpc_factor_opts(int(precision), int(precondition), float(lam), int(power_iters), float(lambda_margin),
-                         None, None, None)
+                         None, None, None, int(schedule))
     if steps is not None:
         O.step_s, O.step_z, O.step_p = k(steps["s"]), k(steps["z"]), k(steps["p"])
     h = ctypes.c_void_p()
@@ -176,6 +180,15 @@ def smpc_factor(tree, net, cost, precision=SMPC_FP64, precondition=1, lam=0.0, p
 
 def smpc_factor_destroy(fac):
     lib().smpc_factor_destroy(fac)
+
+
+def smpc_factor_schedule(fac):
+    """(schedule in use, {1: ms per iteration, 2: ms per iteration} as timed by the factor)."""
+    ms = (ctypes.c_double * 2)()
+    s = lib().smpc_factor_schedule(fac, ms)
+    if s < 0:
+        raise SmpcError(-s, smpc_last_error())
+    return s, {1: ms[0], 2: ms[1]}
 
 
 def smpc_factor_steps(fac, n, n_u):
@@ -228,6 +241,24 @@ def smpc_solve_static(fac, p, q, dhat, alpha2, eps=None, max_iters=500, tol=0.0,
                       check_every=check_every, sync=sync, u=u, x=x, y=y, u0_host=u0_host,
                       history_host=history_host, stream=stream, polish_iters=polish_iters,
                       anchor_every=anchor_every, _entry="smpc_solve_static")
+
+
+def smpc_profile_solve(fac, p, q, dhat, alpha2, eps=None, iters=50):
+    """Mean device ms of each kernel of an iteration over a cold-start solve of `iters`
+    iterations (list: 1 entry for schedule 1, 5 for schedule 2)."""
+    k = _Keep()
+
+    def arg(a):
+        if isinstance(a, int):
+            return ctypes.cast(ctypes.c_void_p(a), _dp)
+        return k(a)
+
+    D = smpc_step_data(arg(p), arg(q), arg(dhat), arg(eps), arg(alpha2))
+    out = (ctypes.c_double * 8)()
+    n = lib().smpc_profile_solve(fac, ctypes.byref(D), int(iters), out, 8)
+    if n < 0:
+        raise SmpcError(-n, smpc_last_error())
+    return [out[i] for i in range(n)]
 
 
 def smpc_solve_info(fac, u0_host=None, history_host=None):

@@ -391,7 +391,9 @@ int power_iteration(smpc_factor_t* f, int iters, double* out) {
   IterArgs a = make_args(f);
   a.pw = pw;
   a.pw_len = iters + 1;
-  LaunchCfg cfg = iter_config(f->prec, a, f->num_sms);
+  // one fixed schedule, so that the estimate does not depend on the autotuner's timing
+  LaunchCfg cfg = iter_config(f->prec, a, f->num_sms, SCHED_CHAIN);
+  if (cfg.stages < 1) cfg = iter_config(f->prec, a, f->num_sms, SCHED_NODE);
   if (cfg.stages < 1) {
     set_error("network too large for the shared-memory pipeline");
     return SMPC_ENOTSUP;
@@ -423,6 +425,80 @@ int power_iteration(smpc_factor_t* f, int iters, double* out) {
 
 namespace smpc {
 
+// Iteration schedule of a factor: the requested one, or (0) the faster of the two on
+// this GPU, timed with CUDA events over a few solve-mode iterations of the factor's
+// own tree and packs from a zero state; the state is cleared again afterwards.
+int choose_schedule(smpc_factor_t* f, int requested) {
+  if (requested < 0 || requested > SCHED_NODE) {
+    set_error("schedule must be 0 (auto), 1 (chain) or 2 (node)");
+    return SMPC_EINVAL;
+  }
+  IterArgs a = make_args(f);
+  const bool anchored = f->packs32 != nullptr;
+  if (anchored) {
+    a.ha = f->ha;
+    a.wa = f->wa;
+  }
+  const int mode_extra = anchored ? MODE_DELTA : 0;
+  bool fits[3] = {false, false, false};
+  for (int s = SCHED_CHAIN; s <= SCHED_NODE; ++s) fits[s] = iter_config(f->prec, a, f->num_sms, s).stages > 0;
+  if (requested != 0) {
+    if (!fits[requested]) {
+      set_error("the requested schedule does not fit this network");
+      return SMPC_ENOTSUP;
+    }
+    f->schedule = requested;
+    return SMPC_OK;
+  }
+  if (!fits[SCHED_CHAIN] || !fits[SCHED_NODE]) {
+    f->schedule = fits[SCHED_NODE] ? SCHED_NODE : SCHED_CHAIN;
+    return SMPC_OK;
+  }
+  TRY(upload_cvec(f, 16));
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  float best = 0;
+  constexpr int kWarm = 2, kTimed = 6;
+  for (int s = SCHED_CHAIN; s <= SCHED_NODE; ++s) {
+    const LaunchCfg cfg = iter_config(f->prec, a, f->num_sms, s);
+    int rc = SMPC_OK;
+    for (int nu = 1; nu <= kWarm && !rc; ++nu) rc = launch_iter(f->prec, a, cfg, nu, MODE_BWD | MODE_PROX | mode_extra, nullptr);
+    cudaEventRecord(e0);
+    for (int nu = kWarm + 1; nu <= kWarm + kTimed && !rc; ++nu)
+      rc = launch_iter(f->prec, a, cfg, nu, MODE_BWD | MODE_PROX | mode_extra, nullptr);
+    cudaEventRecord(e1);
+    float ms = 0;
+    if (rc || cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+      cudaEventDestroy(e0);
+      cudaEventDestroy(e1);
+      if (!rc) set_error("schedule timing failed: %s", cudaGetErrorString(cudaGetLastError()));
+      return rc ? rc : SMPC_ECUDA;
+    }
+    if (s == SCHED_CHAIN || ms < best) {
+      best = ms;
+      f->schedule = s;
+    }
+    f->tuned_ms[s] = ms / kTimed;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  // back to the state a fresh factor has
+  const size_t ny = (size_t)f->n * f->nd;
+  const size_t nk = (size_t)f->n * f->n_k;
+  if (cudaMemset(f->ybuf0, 0, ny * kStateSize) != cudaSuccess || cudaMemset(f->ybuf1, 0, ny * kStateSize) != cudaSuccess ||
+      cudaMemset(f->wbuf, 0, nk * f->vs) != cudaSuccess || cudaMemset(f->h, 0, nk * f->vs) != cudaSuccess ||
+      cudaMemset(f->counters, 0, sizeof(int) * f->n) != cudaSuccess ||
+      cudaMemset(f->res, 0, sizeof(unsigned long long) * 3 * (size_t)(f->cap + 2)) != cudaSuccess ||
+      (anchored && (cudaMemset(f->ha, 0, nk * sizeof(float)) != cudaSuccess ||
+                    cudaMemset(f->wa, 0, nk * sizeof(float)) != cudaSuccess)) ||
+      cudaDeviceSynchronize() != cudaSuccess) {
+    set_error("schedule timing: %s", cudaGetErrorString(cudaGetLastError()));
+    return SMPC_ECUDA;
+  }
+  return SMPC_OK;
+}
+
 int plan_iters(const smpc_factor_t* f, const IterArgs& a, const smpc_solve_opts& opts, IterPlan* plan) {
   const int iters = opts.max_iters;
   if (opts.polish_iters < 0 || opts.polish_iters > iters || opts.anchor_every < 0) {
@@ -431,20 +507,21 @@ int plan_iters(const smpc_factor_t* f, const IterArgs& a, const smpc_solve_opts&
   }
   plan->prec = f->prec;
   plan->args = a;
-  plan->cfg = iter_config(f->prec, a, f->num_sms);
+  plan->cfg = iter_config(f->prec, a, f->num_sms, f->schedule);
   if (plan->cfg.stages < 1) {
     set_error("network too large for the shared-memory pipeline");
     return SMPC_ENOTSUP;
   }
   plan->polish_from = 0x7fffffff;
   plan->anchor_every = 0;
+  plan->profile = f->profile;
   if (f->packs32) {  // SMPC_BF16: anchored solve, float32 packs for anchors and polish
     plan->args.ha = f->ha;
     plan->args.wa = f->wa;
     plan->args32 = plan->args;
     plan->args32.packs = f->packs32;
     plan->args32.pack_stride = f->pack_stride32;
-    plan->cfg32 = iter_config(SMPC_FP32, plan->args32, f->num_sms);
+    plan->cfg32 = iter_config(SMPC_FP32, plan->args32, f->num_sms, f->schedule);
     if (plan->cfg32.stages < 1) {
       set_error("network too large for the float32 pipeline");
       return SMPC_ENOTSUP;
@@ -456,12 +533,30 @@ int plan_iters(const smpc_factor_t* f, const IterArgs& a, const smpc_solve_opts&
 }
 
 int launch_planned(const IterPlan& plan, int nu, int mode, void* stream) {
+  int prec = plan.prec;
+  const IterArgs* a = &plan.args;
+  LaunchCfg cfg = plan.cfg;
+  bool anchor = false;
   if (plan.anchor_every > 0) {
-    if (nu >= plan.polish_from || nu % plan.anchor_every == 0)
-      return launch_iter(SMPC_FP32, plan.args32, plan.cfg32, nu, mode | MODE_ANCHOR, stream);
-    return launch_iter(plan.prec, plan.args, plan.cfg, nu, mode | MODE_DELTA, stream);
+    if (nu >= plan.polish_from || nu % plan.anchor_every == 0) {
+      prec = SMPC_FP32;
+      a = &plan.args32;
+      cfg = plan.cfg32;
+      mode |= MODE_ANCHOR;
+      anchor = true;
+    } else {
+      mode |= MODE_DELTA;
+    }
   }
-  return launch_iter(plan.prec, plan.args, plan.cfg, nu, mode, stream);
+  Profile* pf = plan.profile;
+  const bool prof = pf && !anchor && (mode & MODE_BWD) && (mode & MODE_PROX) && nu >= 1 && pf->count < pf->capacity;
+  if (prof) cfg.events = pf->ev.data() + (size_t)pf->count * Profile::kStageEvents;
+  TRY(launch_iter(prec, *a, cfg, nu, mode, stream));
+  if (prof) {
+    pf->stages = kernels_per_call(cfg, mode);
+    ++pf->count;
+  }
+  return SMPC_OK;
 }
 
 }  // namespace smpc
@@ -791,11 +886,24 @@ int smpc_factor(const smpc_tree* tree, const smpc_network* net, const smpc_cost*
     set_error("factor: %s", cudaGetErrorString(cudaGetLastError()));
     return fail(SMPC_ECUDA);
   }
+  if ((rc = choose_schedule(f, o.schedule))) return fail(rc);
   *out = f;
   return SMPC_OK;
 }
 
 void smpc_factor_destroy(smpc_factor_t* f) { delete f; }
+
+int smpc_factor_schedule(const smpc_factor_t* f, double* ms_per_iter) {
+  if (!f) {
+    set_error("NULL factor");
+    return -SMPC_EINVAL;
+  }
+  if (ms_per_iter) {
+    ms_per_iter[0] = f->tuned_ms[SCHED_CHAIN];
+    ms_per_iter[1] = f->tuned_ms[SCHED_NODE];
+  }
+  return f->schedule;
+}
 
 int smpc_factor_steps(const smpc_factor_t* f, double* lambda, double* step_s, double* step_z, double* step_p) {
   if (!f) {
@@ -912,6 +1020,55 @@ int smpc_solve(smpc_factor_t* f, const smpc_step_data* data, const smpc_solve_op
   res->iterations = -1;
   if (!opts->sync) return SMPC_OK;
   return smpc_solve_info(f, res);
+}
+
+int smpc_profile_solve(smpc_factor_t* f, const smpc_step_data* data, int32_t iters, double* stage_ms,
+                       int32_t max_stages) {
+  if (!f || !data || !stage_ms || max_stages < 1 || iters < 2) {
+    set_error("smpc_profile_solve needs a factor, step data, iters >= 2 and room for the stage times");
+    return -SMPC_EINVAL;
+  }
+  Profile P;
+  P.capacity = iters;
+  P.ev.assign((size_t)iters * Profile::kStageEvents, nullptr);
+  auto release = [&]() {
+    for (auto& e : P.ev)
+      if (e) cudaEventDestroy(e);
+  };
+  for (auto& e : P.ev)
+    if (cudaEventCreate(&e) != cudaSuccess) {
+      set_error("cudaEventCreate failed");
+      release();
+      return -SMPC_ECUDA;
+    }
+  smpc_solve_opts o{};
+  o.max_iters = iters;
+  o.sync = 1;
+  smpc_result r{};
+  f->profile = &P;
+  const int rc = smpc_solve(f, data, &o, &r, nullptr);
+  f->profile = nullptr;
+  if (rc != SMPC_OK || P.count == 0) {
+    if (rc == SMPC_OK) set_error("no full iteration was profiled");
+    release();
+    return rc != SMPC_OK ? -rc : -SMPC_EINVAL;
+  }
+  std::vector<double> ms(P.stages, 0.0);
+  for (int q = 0; q < P.count; ++q)
+    for (int j = 0; j < P.stages; ++j) {
+      float t = 0;
+      cudaEvent_t* e = P.ev.data() + (size_t)q * Profile::kStageEvents;
+      if (cudaEventElapsedTime(&t, e[j], e[j + 1]) != cudaSuccess) {
+        set_error("cudaEventElapsedTime failed");
+        release();
+        return -SMPC_ECUDA;
+      }
+      ms[j] += t;
+    }
+  release();
+  const int n = std::min(P.stages, (int)max_stages);
+  for (int j = 0; j < n; ++j) stage_ms[j] = ms[j] / P.count;
+  return P.stages;
 }
 
 int smpc_solve_info(smpc_factor_t* f, smpc_result* res) {

@@ -40,6 +40,7 @@ constexpr int kWarps = kThreads / 32;
 // copy size (16 KB copies: ~54 GB/s per SM; 64 KB and larger: ~200 GB/s).
 constexpr int kChunk = 1 << 20;          // larger than any matrix of a pack
 constexpr uint64_t kWaitNs = 2000000000ull;  // bounded mbarrier wait: 2 s
+constexpr int kMaxSlots = 4;                 // pack slots per CTA: one mbarrier each (barK, barL)
 
 template <typename MT>
 struct Acc;
@@ -350,8 +351,8 @@ __host__ __device__ size_t vec_smem_bytes(int n_x, int n_u, int n_v) {
 }
 
 template <typename MT>
-__host__ __device__ size_t iter_smem_bytes(int S, int n_x, int n_u, int n_v) {
-  size_t m = (size_t)S * (kpad<MT>(n_x + n_u, n_v) + lpad<MT>(n_v)) * sizeof(MT);
+__host__ __device__ size_t iter_smem_bytes(int S, int n_x, int n_u, int n_v, bool with_l = true) {
+  size_t m = (size_t)S * (kpad<MT>(n_x + n_u, n_v) + (with_l ? lpad<MT>(n_v) : 0)) * sizeof(MT);
   m = round_up(m, 16) + 8 * sizeof(uint64_t);
   m = round_up(m, 16);
   return m + vec_smem_bytes<MT>(n_x, n_u, n_v);
@@ -381,7 +382,7 @@ struct Smem {
 };
 
 template <typename MT>
-__device__ Smem<MT> carve(unsigned char* base, int S, int n_x, int n_u, int n_v) {
+__device__ Smem<MT> carve(unsigned char* base, int S, int n_x, int n_u, int n_v, bool with_l = true) {
   using AT = typename Acc<MT>::T;
   Smem<MT> s;
   const int n_k = n_x + n_u;
@@ -389,7 +390,7 @@ __device__ Smem<MT> carve(unsigned char* base, int S, int n_x, int n_u, int n_v)
   s.S = S;
   s.ld = row_stride<MT>(n_v);
   s.kbytes = kpad<MT>(n_k, n_v) * sizeof(MT);
-  s.lbytes = lpad<MT>(n_v) * sizeof(MT);
+  s.lbytes = with_l ? lpad<MT>(n_v) * sizeof(MT) : 0;
   size_t off = round_up((size_t)S * (s.kbytes + s.lbytes), 16);
   s.barK = reinterpret_cast<uint64_t*>(base + off);
   off += 4 * sizeof(uint64_t);
@@ -574,22 +575,42 @@ struct Kern {
   // ---------------------------------------------------------- forward + prox
   // Path sums down to node `par` (inclusive) for entry e: states (V = Bbar v, X = x)
   // or inputs (U = L v).
+  // Adds the nodes list[0..cnt) (top-down) to the path sums; the node ids, then their
+  // vectors, are loaded 8 at a time so that the loads of a batch overlap.
+  __device__ void path_add(const int* list, int cnt, int e, AT& V, AT& X, AT& U) const {
+    constexpr int P = 8;
+    const bool tank = e < a.n_x, lin = linear();
+    for (int q0 = 0; q0 < cnt; q0 += P) {
+      int id[P];
+      AT hv[P], ev[P];
+#pragma unroll
+      for (int j = 0; j < P; ++j) id[j] = q0 + j < cnt ? list[q0 + j] : -1;
+#pragma unroll
+      for (int j = 0; j < P; ++j) {
+        hv[j] = ev[j] = 0;
+        if (id[j] >= 0) {
+          hv[j] = h_at(id[j], e);
+          if (tank && !lin) ev[j] = (AT)cv(a.e)[(long long)id[j] * a.n_x + e];
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < P; ++j) {
+        if (id[j] < 0) continue;
+        if (tank) {
+          V += hv[j];
+          X += V + ev[j];
+        } else {
+          U += hv[j];
+        }
+      }
+    }
+  }
   __device__ void path_init(int par, int e, AT& V, AT& X, AT& U) const {
     V = 0;
     U = 0;
     X = (e < a.n_x && !linear()) ? (AT)cv(a.p0)[e] : (AT)0;
     if (par < 0) return;
-    const int b = a.path_off[par], en = a.path_off[par + 1];
-    for (int q = b; q < en; ++q) {
-      const int m = a.path_node[q];
-      const AT hv = h_at(m, e);
-      if (e < a.n_x) {
-        V += hv;
-        X += V + (linear() ? (AT)0 : (AT)cv(a.e)[(long long)m * a.n_x + e]);
-      } else {
-        U += hv;
-      }
-    }
+    path_add(a.path_node + a.path_off[par], a.path_off[par + 1] - a.path_off[par], e, V, X, U);
   }
 
   // Forward sweep, prox, dual update and next extrapolation for the segment
@@ -829,6 +850,195 @@ struct Kern {
     }
   }
 
+  // ---------------------------------------------------------- forward sweep alone
+  // Segment b of the node-parallel schedule: top node b (b < n_top), else chain
+  // b - n_top.  Thread e sums entry e of [x; u] down the segment's path and writes the
+  // forward-sweep result of every node of the segment to xout / uout.
+  __device__ void store_xu(long long m, int e, AT X, AT U) const {
+    if (e < a.n_x) {
+      mv(a.xout)[m * a.n_x + e] = (VT)X;
+    } else {
+      const int i = e - a.n_x;
+      mv(a.uout)[m * a.n_u + i] = (VT)(U + (linear() ? (AT)0 : (AT)cv(a.uhat)[m * a.n_u + i]));
+    }
+  }
+  __device__ void fwd_segment(int b) const {
+    const int e = threadIdx.x;
+    if (e >= a.n_k) return;
+    AT V = 0, X = 0, U = 0;
+    if (b < a.n_top) {
+      const int t = a.top_nodes[b];
+      path_init(t, e, V, X, U);
+      store_xu(t, e, X, U);
+      return;
+    }
+    const int c = b - a.n_top;
+    path_init(a.chain_parent[c], e, V, X, U);
+    const int cb = a.chain_off[c], len = a.chain_off[c + 1] - cb;
+    const bool tank = e < a.n_x, lin = linear();
+    constexpr int B = 16;
+    for (int k0 = 0; k0 < len; k0 += B) {
+      AT hv[B], ev[B];
+#pragma unroll
+      for (int j = 0; j < B; ++j) {
+        hv[j] = ev[j] = 0;
+        if (k0 + j < len) {
+          const int m = a.chain_node[cb + k0 + j];
+          hv[j] = h_at(m, e);
+          if (tank && !lin) ev[j] = (AT)cv(a.e)[(long long)m * a.n_x + e];
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < B; ++j) {
+        if (k0 + j >= len) break;
+        if (tank) {
+          V += hv[j];
+          X += V + ev[j];
+        } else {
+          U += hv[j];
+        }
+        store_xu(a.chain_node[cb + k0 + j], e, X, U);
+      }
+    }
+  }
+
+  // ---------------------------------------------------------- warp-level Phase P
+  // Node m alone on one warp (node-parallel schedule): lane l owns the entries
+  // e = l + 32 k of [x; u].  The arithmetic of phase_p, with warp reductions only,
+  // so the warps of a CTA run independent nodes without block barriers.
+  static constexpr int kEPL = kThreads / 32;  // entries per lane (n_k <= kThreads)
+  // x and u of node m come from the forward sweep (fwd_segment, previous launch).
+  __device__ void warp_prox(int m, bool do_prox, bool do_w) {
+    const int lane = threadIdx.x & 31;
+    const bool lin = linear();
+    AT X[kEPL], U[kEPL];  // x entries, or u (with u_hat) entries
+#pragma unroll
+    for (int k = 0; k < kEPL; ++k) {
+      const int e = lane + 32 * k;
+      X[k] = U[k] = 0;
+      if (!do_prox || e >= a.n_k) continue;
+      if (e < a.n_x)
+        X[k] = (AT)cv(a.xout)[(long long)m * a.n_x + e];
+      else
+        U[k] = (AT)cv(a.uout)[(long long)m * a.n_u + (e - a.n_x)];
+    }
+    const ST zero = st_from<ST>(0.0);
+    const long long mk = (long long)m * a.n_k;
+    if (do_prox) {
+      const int it = nu - 1;
+      const AT c = lin ? (AT)0 : (AT)a.cvec[it];
+      const AT cn = lin ? (AT)0 : (AT)a.cvec[it + 1];
+      const ST* y1 = ys(it) + (long long)m * nd;
+      ST* y2 = ys(it + 1) + (long long)m * nd;
+      const AT ls = (AT)cv(a.step_s)[m], lz = (AT)cv(a.step_z)[m];
+      if (lin) {  // power iteration: y_{k+1} = -D^{1/2} H z
+#pragma unroll
+        for (int k = 0; k < kEPL; ++k) {
+          const int e = lane + 32 * k;
+          if (e < a.n_x) {
+            const AT a1 = -sqrt(ls) * X[k], a2 = -sqrt(lz) * X[k];
+            pdot += (double)a1 * (double)st_val(y1[e]) + (double)a2 * (double)st_val(y1[a.n_x + e]);
+            pnrm += (double)a1 * a1 + (double)a2 * a2;
+            y2[e] = st_from<ST>(a1);
+            y2[a.n_x + e] = st_from<ST>(a2);
+          } else if (e < a.n_k) {
+            const int i = e - a.n_x;
+            const AT a3 = -sqrt((AT)cv(a.step_p)[(long long)m * a.n_u + i]) * U[k];
+            pdot += (double)a3 * (double)st_val(y1[2 * a.n_x + i]);
+            pnrm += (double)a3 * a3;
+            y2[2 * a.n_x + i] = st_from<ST>(a3);
+          }
+        }
+      } else {
+        // block norms ||lambda r|| of the two distance blocks
+        AT ps = 0, pz = 0;
+#pragma unroll
+        for (int k = 0; k < kEPL; ++k) {
+          const int e = lane + 32 * k;
+          if (e < a.n_x) {
+            const ST ws = st_extrap(y1[e], y2[e], c), wz = st_extrap(y1[a.n_x + e], y2[a.n_x + e], c);
+            const ST qs = st_axpy(ws, ls, X[k] - (AT)cv(a.x_s)[e]);
+            const AT rs = st_neg(qs) ? (AT)st_val(qs) : (AT)0;
+            const AT rz = (AT)st_val(box_lr(st_axpy(wz, lz, X[k] - (AT)cv(a.x_max)[e]),
+                                            st_axpy(wz, lz, X[k] - (AT)cv(a.x_min)[e])));
+            ps += rs * rs;
+            pz += rz * rz;
+          }
+        }
+        ps = warp_sum(ps);
+        pz = warp_sum(pz);
+        const AT ds = sqrt(ps), dz = sqrt(pz);
+        const AT mus = (AT)cv(a.mu_s)[m], muz = (AT)a.gamma_d;
+        const AT ks = ds > mus ? mus / ds : (AT)1, kz = dz > muz ? muz / dz : (AT)1;
+        const AT is = (AT)cv(a.inv_s)[m], iz = (AT)cv(a.inv_z)[m];
+        AT rm = 0, hm = 0, tm = 0;
+#pragma unroll
+        for (int k = 0; k < kEPL; ++k) {
+          const int e = lane + 32 * k;
+          if (e < a.n_x) {
+            const AT x = X[k];
+            const ST v1 = y1[e], w1 = y1[a.n_x + e];
+            const ST ws = st_extrap(v1, y2[e], c), wz = st_extrap(w1, y2[a.n_x + e], c);
+            const ST qs = st_axpy(ws, ls, x - (AT)cv(a.x_s)[e]);
+            const ST ysn = st_scale(st_neg(qs) ? qs : zero, ks);
+            const ST yzn = st_scale(box_lr(st_axpy(wz, lz, x - (AT)cv(a.x_max)[e]),
+                                           st_axpy(wz, lz, x - (AT)cv(a.x_min)[e])), kz);
+            const AT es = (AT)st_val(st_sub(ysn, ws)) * is;
+            const AT ez = (AT)st_val(st_sub(yzn, wz)) * iz;
+            y2[e] = ysn;
+            y2[a.n_x + e] = yzn;
+            put_w(m, e, st_add(st_extrap(ysn, v1, cn), st_extrap(yzn, w1, cn)));
+            rm = fmax(rm, fmax(fabs(es), fabs(ez)));
+            hm = fmax(hm, fabs(x));
+            tm = fmax(tm, fmax(fabs(x - es), fabs(x - ez)));
+            if (!isfinite(st_val(ysn)) || !isfinite(st_val(yzn))) a.flags[1] = SMPC_EDIVERGED;
+          } else if (e < a.n_k) {
+            const int i = e - a.n_x;
+            const AT u = U[k];
+            const AT lp = (AT)cv(a.step_p)[(long long)m * a.n_u + i];
+            const ST p1 = y1[2 * a.n_x + i];
+            const ST wp = st_extrap(p1, y2[2 * a.n_x + i], c);
+            const ST ypn = box_lr(st_axpy(wp, lp, u - (AT)cv(a.u_max)[i]), st_axpy(wp, lp, u - (AT)cv(a.u_min)[i]));
+            const AT ep = (AT)st_val(st_sub(ypn, wp)) * (AT)cv(a.inv_p)[(long long)m * a.n_u + i];
+            y2[2 * a.n_x + i] = ypn;
+            put_w(m, e, st_extrap(ypn, p1, cn));
+            rm = fmax(rm, fabs(ep));
+            hm = fmax(hm, fabs(u));
+            tm = fmax(tm, fabs(u - ep));
+            if (!isfinite(st_val(ypn))) a.flags[1] = SMPC_EDIVERGED;
+          }
+        }
+        rmax = fmax(rmax, (double)rm);
+        hzmax = fmax(hzmax, (double)hm);
+        tmax = fmax(tmax, (double)tm);
+      }
+    }
+    if (do_w) {  // w^nu without a prox (first iteration, power iteration)
+      const ST* ya = ys(nu) + (long long)m * nd;
+      const ST* yb = ys(nu + 1) + (long long)m * nd;
+#pragma unroll
+      for (int k = 0; k < kEPL; ++k) {
+        const int e = lane + 32 * k;
+        if (e >= a.n_k) continue;
+        if (lin) {
+          const AT inv = (AT)rsqrt(a.pw[nu]);
+          AT w;
+          if (e < a.n_x)
+            w = sqrt((AT)cv(a.step_s)[m]) * (AT)st_val(ya[e]) + sqrt((AT)cv(a.step_z)[m]) * (AT)st_val(ya[a.n_x + e]);
+          else
+            w = sqrt((AT)cv(a.step_p)[(long long)m * a.n_u + (e - a.n_x)]) * (AT)st_val(ya[2 * a.n_x + (e - a.n_x)]);
+          wb()[mk + e] = (VT)(w * inv);
+        } else {
+          const AT c = (AT)a.cvec[nu];
+          if (e < a.n_x)
+            put_w(m, e, st_add(st_extrap(ya[e], yb[e], c), st_extrap(ya[a.n_x + e], yb[a.n_x + e], c)));
+          else
+            put_w(m, e, st_extrap(ya[2 * a.n_x + (e - a.n_x)], yb[2 * a.n_x + (e - a.n_x)], c));
+        }
+      }
+    }
+  }
+
   // ---------------------------------------------------------- backward sweep
   // One node's backward step with its pack in slots (K, L):
   //   r += [Bbar; L]' [s; psi];  delta = Lambda r;  h = [Bbar; L] delta.
@@ -997,7 +1207,12 @@ struct Kern {
       if (par >= 0 && arrive(par)) process_top(p, par, chain_cursor(ch + gridDim.x));
     }
 
-    // per-CTA reductions: residual maxima (Sec. IV-E) or power-iteration sums
+    reduce_out(do_prox);
+  }
+
+  // per-CTA reductions: residual maxima (Sec. IV-E) or power-iteration sums
+  __device__ void reduce_out(bool do_prox) {
+    const int tid = threadIdx.x;
     const int lane = tid & 31, warp = tid >> 5;
     if (do_prox && !linear()) {
       const double r = warp_max(rmax), hz = warp_max(hzmax), tt = warp_max(tmax);
@@ -1039,18 +1254,16 @@ struct Kern {
   }
 };
 
-template <typename VT, typename MT>
-__global__ void __launch_bounds__(kThreads, 1)
-    apg_iter(const __grid_constant__ IterArgs a, int S, int nu, int mode) {
-  extern __shared__ __align__(128) unsigned char smem_raw[];
-  Smem<MT> sm = carve<MT>(smem_raw, S, a.n_x, a.n_u, a.n_v);
-  // uniform early exit: stopped, failed, or converged two iterations ago
+// Uniform early exit of a launch of iteration nu: the solve stopped or failed, or (with
+// `decide`) the residual of iteration nu - 2 met the tolerance, which ends the solve
+// after nu - 1 iterations.
+__device__ bool early_exit(const IterArgs& a, int nu, int mode, int* flag, bool decide) {
   if (threadIdx.x == 0) {
     int stop = 0;
     if (mode & MODE_CHECK) {
       const int done = ldcg(a.flags + 0), err = ldcg(a.flags + 1);
       if (done >= 0 || err != 0) stop = 1;
-      if (!stop && a.tol > 0 && nu >= 2) {
+      if (decide && !stop && a.tol > 0 && nu >= 2) {
         const unsigned long long* r = a.res + 3ll * (nu - 2);
         const double rho = __longlong_as_double((long long)ldcg(r + 0));
         const double hz = __longlong_as_double((long long)ldcg(r + 1));
@@ -1061,12 +1274,201 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
       }
     }
-    sm.flag[1] = stop;
+    *flag = stop;
   }
   __syncthreads();
-  if (sm.flag[1]) return;
+  return *flag != 0;
+}
+
+template <typename VT, typename MT>
+__global__ void __launch_bounds__(kThreads, 1)
+    apg_iter(const __grid_constant__ IterArgs a, int S, int nu, int mode) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  Smem<MT> sm = carve<MT>(smem_raw, S, a.n_x, a.n_u, a.n_v);
+  if (early_exit(a, nu, mode, sm.flag + 1, true)) return;
   Kern<VT, MT> k(a, sm, S, nu, mode);
   k.run();
+}
+
+// ------------------------------------------------------------------ node-parallel schedule
+// The backward sweep is linear in (w, beta).  With s = subtree sums of xi,
+// g_n = [Bbar; L]_n' [s_n; psi_n] and r = subtree sums of beta + g, the mat-vecs of
+// different nodes are independent, so one iteration becomes five launches:
+//   prox_node  forward sweep (each node sums its own path), prox, dual update, w^nu
+//   scan (s)   s_n = xi_n + sum_c s_c             (chains bottom-up, top nodes on arrival)
+//   node_gt    g_n = [Bbar; L]_n' [s_n; psi_n]
+//   scan (r)   r_n = beta_n + g_n + sum_c r_c      (in place over g)
+//   node_dh    h_n = [Bbar; L]_n (Lambda_n / (2 p_n)) r_n
+// [Bbar; L] is read twice per iteration instead of once, but each launch has one
+// independent task per node instead of one sequential task per chain.
+
+// forward sweep of iteration nu - 1: one CTA per top node and per chain
+template <typename VT, typename MT>
+__global__ void __launch_bounds__(kThreads) fwd_scan(const __grid_constant__ IterArgs a, int nu, int mode) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  Smem<MT> sm = carve<MT>(smem_raw, 0, a.n_x, a.n_u, a.n_v);
+  if (early_exit(a, nu, mode, sm.flag + 1, true)) return;
+  Kern<VT, MT> k(a, sm, 0, nu, mode);
+  for (int b = blockIdx.x; b < a.n_top + a.n_chains; b += gridDim.x) k.fwd_segment(b);
+}
+
+template <typename VT, typename MT>
+__global__ void __launch_bounds__(kThreads) prox_node(const __grid_constant__ IterArgs a, int nu, int mode) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  Smem<MT> sm = carve<MT>(smem_raw, 0, a.n_x, a.n_u, a.n_v);
+  // the forward sweep (when there is one) already took the stop decision
+  const bool decide = !((mode & MODE_PROX) && nu >= 1);
+  if (early_exit(a, nu, mode, sm.flag + 1, decide)) return;
+  Kern<VT, MT> k(a, sm, 0, nu, mode);
+  const bool do_prox = (mode & MODE_PROX) != 0 && nu >= 1;
+  const bool do_bwd = (mode & MODE_BWD) != 0;
+  const int warp = threadIdx.x >> 5;
+  for (int m = blockIdx.x * kWarps + warp; m < a.n; m += gridDim.x * kWarps)
+    k.warp_prox(m, do_prox, do_bwd && (!do_prox || k.linear()));
+  k.reduce_out(do_prox);
+}
+
+// Subtree sums out_n = in_n (+ beta_n) + sum over children c of out_c.  One CTA per chain
+// (bottom-up in registers), then each top node is summed by the CTA whose arrival
+// completes its children.  which = 0: s from xi = w[:, :n_x]; which = 1: r from g, in place.
+template <typename VT>
+__global__ void __launch_bounds__(kThreads) scan_kernel(const __grid_constant__ IterArgs a, int which, int nu,
+                                                        int mode) {
+  __shared__ int flag[2];
+  if (early_exit(a, nu, mode, flag, false)) return;
+  const int e = threadIdx.x;
+  const int W = which == 0 ? a.n_x : a.n_v;
+  const bool with_beta = which == 1 && (mode & (MODE_LINEAR | MODE_DELTA)) == 0;
+  const VT* in = reinterpret_cast<const VT*>(which == 0 ? a.wbuf : a.rpub);
+  VT* out = reinterpret_cast<VT*>(which == 0 ? a.spub : a.rpub);
+  const VT* beta = reinterpret_cast<const VT*>(a.beta);
+  const long long is = which == 0 ? a.n_k : a.n_v, os = W;
+  constexpr int B = 32;  // chain nodes whose loads are in flight together
+  for (int ch = blockIdx.x; ch < a.n_chains; ch += gridDim.x) {
+    const int cb = a.chain_off[ch], len = a.chain_off[ch + 1] - cb;
+    if (e < W) {
+      VT acc = 0;
+      for (int k1 = len; k1 > 0; k1 -= B) {  // nodes k1-1 .. k1-B, bottom-up, loads batched
+        VT v[B];
+#pragma unroll
+        for (int j = 0; j < B; ++j) {
+          v[j] = 0;
+          const int k = k1 - 1 - j;
+          if (k >= 0) {
+            const long long m = a.chain_node[cb + k];
+            v[j] = in[m * is + e];
+            if (with_beta) v[j] += beta[m * a.n_v + e];
+          }
+        }
+#pragma unroll
+        for (int j = 0; j < B; ++j) {
+          const int k = k1 - 1 - j;
+          if (k >= 0) {
+            acc += v[j];
+            out[(long long)a.chain_node[cb + k] * os + e] = acc;
+          }
+        }
+      }
+    }
+    for (int t = a.chain_parent[ch]; t >= 0; t = a.parent[t]) {
+      __threadfence();  // this CTA's outputs before its arrival
+      __syncthreads();
+      if (e == 0) {
+        const int last = atomicAdd(&a.counters[t], 1) == a.child_count[t] - 1;
+        if (last) a.counters[t] = 0;
+        flag[1] = last;
+      }
+      __syncthreads();
+      if (!flag[1]) break;
+      __threadfence();
+      if (e < W) {
+        VT v = in[(long long)t * is + e];
+        if (with_beta) v += beta[(long long)t * a.n_v + e];
+        const int c0 = a.child_begin[t], c1 = c0 + a.child_count[t];
+        for (int c = c0; c < c1; ++c) v += ldcg(out + (long long)c * os + e);
+        out[(long long)t * os + e] = v;
+      }
+    }
+  }
+}
+
+// Per-node mat-vec launches: CTA b handles nodes b, b + G, ... and streams their packs
+// through S shared-memory slots with cp.async.bulk, so that the copies of the next
+// nodes overlap the current node's mat-vecs.  gt: g_n = [Bbar; L]_n' [s_n; psi_n];
+// dh: delta = Lambda_n r_n / (2 p_n), h_n = [Bbar; L]_n delta.
+template <typename VT, typename MT, bool DH>
+__global__ void __launch_bounds__(kThreads, 1) node_mv(const __grid_constant__ IterArgs a, int S, int nu, int mode) {
+  using AT = typename Acc<MT>::T;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  Smem<MT> sm = carve<MT>(smem_raw, S, a.n_x, a.n_u, a.n_v, DH);
+  if (early_exit(a, nu, mode, sm.flag + 1, false)) return;
+  const int tid = threadIdx.x;
+  const MT* packs = reinterpret_cast<const MT*>(a.packs);
+  const long long kp = kpad<MT>(a.n_k, a.n_v);
+  const uint32_t kb = (uint32_t)sm.kbytes, lb = (uint32_t)sm.lbytes;
+  const int G = gridDim.x;
+  const int count = a.n > (int)blockIdx.x ? (a.n - 1 - (int)blockIdx.x) / G + 1 : 0;
+  if (tid == 0) {
+    for (int q = 0; q < S; ++q) mbar_init(&sm.barK[q], 1);
+    fence_barrier_init();
+  }
+  for (int j = a.n_v + tid; j < sm.ld; j += kThreads) sm.dv[j] = 0;
+  __syncthreads();
+  auto issue = [&](int q) {  // thread 0: copies of the q-th node into slot q % S
+    const int m = blockIdx.x + q * G;
+    const int slot = q % S;
+    fence_proxy_async();
+    mbar_expect_tx(&sm.barK[slot], kb + (DH ? lb : 0u));
+    const unsigned char* src = reinterpret_cast<const unsigned char*>(packs + (long long)m * a.pack_stride);
+    bulk_g2s(sm.K(slot), src, kb, &sm.barK[slot]);
+    if (DH) bulk_g2s(sm.Lm(slot), src + kp * sizeof(MT), lb, &sm.barK[slot]);
+  };
+  if (tid == 0)
+    for (int q = 0; q < S && q < count; ++q) issue(q);
+  const VT* wb = reinterpret_cast<const VT*>(a.wbuf);
+  const VT* sp = reinterpret_cast<const VT*>(a.spub);
+  VT* rp = reinterpret_cast<VT*>(a.rpub);
+  int failed_at = -1;
+  for (int q = 0; q < count; ++q) {
+    const long long m = blockIdx.x + (long long)q * G;
+    const int slot = q % S;
+    // node vectors into shared memory while the copy lands
+    if (DH) {
+      if (tid < a.n_v) sm.rv[tid] = (AT)rp[m * a.n_v + tid];
+    } else if (tid < a.n_k) {
+      sm.yv[tid] = tid < a.n_x ? (AT)sp[m * a.n_x + tid] : (AT)wb[m * a.n_k + tid];
+    }
+    const bool ok = mbar_wait(&sm.barK[slot], (q / S) & 1);
+    if (__syncthreads_or(!ok)) {
+      failed_at = q;
+      break;
+    }
+    if (DH) {
+      matvec_t<MT, AT>(sm.Lm(slot), a.n_v, a.n_v, sm.ld, sm.rv, sm.dv, sm.part);  // Lambda is symmetric
+      matvec_n<MT, AT>(sm.K(slot), a.n_k, sm.ld, sm.dv, sm.yv);
+      if (tid < a.n_k) {
+        VT* h = reinterpret_cast<VT*>(a.h);
+        if (mode & MODE_ANCHOR) {
+          reinterpret_cast<VT*>(a.ha)[m * a.n_k + tid] = (VT)sm.yv[tid];
+          h[m * a.n_k + tid] = (VT)0;
+        } else {
+          h[m * a.n_k + tid] = (VT)sm.yv[tid];
+        }
+      }
+    } else {
+      matvec_t<MT, AT>(sm.K(slot), a.n_k, a.n_v, sm.ld, sm.yv, sm.gv, sm.part);
+      if (tid < a.n_v) rp[m * a.n_v + tid] = (VT)sm.gv[tid];
+    }
+    __syncthreads();  // the slot and the vectors are free again
+    if (tid == 0 && q + S < count) issue(q + S);
+  }
+  if (failed_at >= 0 && tid == 0) {
+    // let this CTA's copies still in flight (nodes failed_at .. failed_at + S - 1) land,
+    // each wait bounded, before leaving
+    a.flags[1] = SMPC_ETIMEOUT;
+    const int end = min(count, failed_at + S);
+    for (int q = failed_at; q < end; ++q) mbar_wait(&sm.barK[q % S], (q / S) & 1);
+  }
 }
 
 // ------------------------------------------------------------------ helpers
@@ -1197,22 +1599,47 @@ int check_launch(const char* what) {
   return SMPC_OK;
 }
 
-template <typename VT, typename MT>
-LaunchCfg config_t(const IterArgs& a, int num_sms, int S_max) {
-  LaunchCfg c;
+int optin_smem() {
   int dev = 0, optin = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-  if (optin <= 0) optin = 232448;
-  int S = S_max;
-  while (S > 1 && iter_smem_bytes<MT>(S, a.n_x, a.n_u, a.n_v) > (size_t)optin) --S;
-  c.stages = S;
-  c.smem = iter_smem_bytes<MT>(S, a.n_x, a.n_u, a.n_v);
-  // one thread per entry of [x; u] and of r
-  if (c.smem > (size_t)optin || a.n_k > kThreads || a.n_v > kThreads) c.stages = 0;
+  return optin > 0 ? optin : 232448;
+}
+
+template <typename VT, typename MT>
+LaunchCfg config_t(const IterArgs& a, int num_sms, int S_max, int schedule) {
+  LaunchCfg c;
+  const int optin = optin_smem();
+  c.schedule = schedule;
   c.block = kThreads;
-  c.grid = a.n_chains < num_sms ? a.n_chains : num_sms;
-  if (c.grid < 1) c.grid = 1;
+  const bool fits_threads = a.n_k <= kThreads && a.n_v <= kThreads;  // one thread per entry
+  if (schedule == SCHED_CHAIN) {
+    int S = S_max;
+    while (S > 1 && iter_smem_bytes<MT>(S, a.n_x, a.n_u, a.n_v) > (size_t)optin) --S;
+    c.stages = S;
+    c.smem = iter_smem_bytes<MT>(S, a.n_x, a.n_u, a.n_v);
+    if (c.smem > (size_t)optin || !fits_threads) c.stages = 0;
+    c.grid = a.n_chains < num_sms ? a.n_chains : num_sms;
+    if (c.grid < 1) c.grid = 1;
+    return c;
+  }
+  c.stages = fits_threads ? 1 : 0;
+  c.smem_prox = iter_smem_bytes<MT>(0, a.n_x, a.n_u, a.n_v);  // barriers + vectors, no pack slot
+  c.grid_prox = (a.n + kWarps - 1) / kWarps;  // one warp per node
+  if (c.grid_prox > 8 * num_sms) c.grid_prox = 8 * num_sms;
+  c.grid_scan = a.n_chains < 4 * num_sms ? a.n_chains : 4 * num_sms;
+  c.grid_fwd = a.n_top + a.n_chains < 8 * num_sms ? a.n_top + a.n_chains : 8 * num_sms;
+  c.grid_mv = a.n < num_sms ? a.n : num_sms;
+  if (c.grid_scan < 1) c.grid_scan = 1;
+  int S = kMaxSlots;
+  while (S > 0 && iter_smem_bytes<MT>(S, a.n_x, a.n_u, a.n_v, false) > (size_t)optin) --S;
+  c.s_gt = S;
+  c.smem_gt = iter_smem_bytes<MT>(S > 0 ? S : 1, a.n_x, a.n_u, a.n_v, false);
+  S = kMaxSlots;
+  while (S > 0 && iter_smem_bytes<MT>(S, a.n_x, a.n_u, a.n_v, true) > (size_t)optin) --S;
+  c.s_dh = S;
+  c.smem_dh = iter_smem_bytes<MT>(S > 0 ? S : 1, a.n_x, a.n_u, a.n_v, true);
+  if (c.s_gt < 1 || c.s_dh < 1) c.stages = 0;
   return c;
 }
 
@@ -1221,10 +1648,39 @@ int launch_t(const IterArgs& a, const LaunchCfg& c, int nu, int mode, cudaStream
   static bool attr_set = false;
   if (!attr_set) {
     cudaFuncSetAttribute(apg_iter<VT, MT>, cudaFuncAttributeMaxDynamicSharedMemorySize, 232448);
+    cudaFuncSetAttribute(node_mv<VT, MT, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 232448);
+    cudaFuncSetAttribute(node_mv<VT, MT, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 232448);
+    cudaFuncSetAttribute(prox_node<VT, MT>, cudaFuncAttributeMaxDynamicSharedMemorySize, 232448);
+    cudaFuncSetAttribute(fwd_scan<VT, MT>, cudaFuncAttributeMaxDynamicSharedMemorySize, 232448);
     attr_set = true;
   }
-  apg_iter<VT, MT><<<c.grid, c.block, c.smem, s>>>(a, c.stages, nu, mode);
-  return check_launch("apg_iter");
+  int ev = 0;
+  auto mark = [&]() {
+    if (c.events) cudaEventRecord(c.events[ev++], s);
+  };
+  mark();
+  if (c.schedule == SCHED_CHAIN) {
+    apg_iter<VT, MT><<<c.grid, c.block, c.smem, s>>>(a, c.stages, nu, mode);
+    mark();
+    return check_launch("apg_iter");
+  }
+  if ((mode & MODE_PROX) && nu >= 1) {
+    fwd_scan<VT, MT><<<c.grid_fwd, c.block, c.smem_prox, s>>>(a, nu, mode);
+    mark();
+  }
+  prox_node<VT, MT><<<c.grid_prox, c.block, c.smem_prox, s>>>(a, nu, mode);
+  mark();
+  if (mode & MODE_BWD) {
+    scan_kernel<VT><<<c.grid_scan, c.block, 0, s>>>(a, 0, nu, mode);
+    mark();
+    node_mv<VT, MT, false><<<c.grid_mv, c.block, c.smem_gt, s>>>(a, c.s_gt, nu, mode);
+    mark();
+    scan_kernel<VT><<<c.grid_scan, c.block, 0, s>>>(a, 1, nu, mode);
+    mark();
+    node_mv<VT, MT, true><<<c.grid_mv, c.block, c.smem_dh, s>>>(a, c.s_dh, nu, mode);
+    mark();
+  }
+  return check_launch("node-parallel iteration");
 }
 
 }  // namespace
@@ -1241,11 +1697,11 @@ long long pack_entries(int prec, int n_k, int n_v) {
   }
 }
 
-LaunchCfg iter_config(int prec, const IterArgs& a, int num_sms) {
+LaunchCfg iter_config(int prec, const IterArgs& a, int num_sms, int schedule) {
   switch (prec) {
-    case SMPC_FP64: return config_t<double, double>(a, num_sms, 1);
-    case SMPC_FP32: return config_t<float, float>(a, num_sms, 2);
-    default: return config_t<float, __nv_bfloat16>(a, num_sms, 4);
+    case SMPC_FP64: return config_t<double, double>(a, num_sms, 1, schedule);
+    case SMPC_FP32: return config_t<float, float>(a, num_sms, 2, schedule);
+    default: return config_t<float, __nv_bfloat16>(a, num_sms, 4, schedule);
   }
 }
 

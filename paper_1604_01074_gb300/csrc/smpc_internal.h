@@ -125,14 +125,32 @@ enum KernelMode : int {
   MODE_DELTA = 32     // anchored solve: solve step on w^nu - w_a, without the affine data
 };
 
-struct LaunchCfg {
-  int grid = 1, block = 256;
-  size_t smem = 0;
-  int stages = 1;
+enum Schedule : int {
+  SCHED_CHAIN = 1,  // one apg_iter launch per iteration, one CTA per chain
+  SCHED_NODE = 2    // five launches per iteration, one task per node in each
 };
 
+struct LaunchCfg {
+  int schedule = SCHED_CHAIN;
+  int grid = 1, block = 256;
+  size_t smem = 0;
+  int stages = 1;           // chain schedule: pack slots per CTA (0: does not fit)
+  // node schedule
+  int grid_prox = 1, grid_scan = 1, grid_mv = 1, grid_fwd = 1;
+  size_t smem_prox = 0, smem_gt = 0, smem_dh = 0;
+  int s_gt = 0, s_dh = 0;   // pack slots of the two mat-vec launches (0: does not fit)
+  // profiling: when set, an event is recorded before the first and after every kernel
+  // of a launch_iter call (kernels_per_call + 1 events)
+  cudaEvent_t* events = nullptr;
+};
+// kernels one launch_iter call enqueues
+inline int kernels_per_call(const LaunchCfg& c, int mode) {
+  if (c.schedule == SCHED_CHAIN) return 1;
+  return 1 + ((mode & MODE_PROX) ? 1 : 0) + ((mode & MODE_BWD) ? 4 : 0);
+}
+
 // Kernel launchers (kernels.cu).  prec: smpc_precision.
-LaunchCfg iter_config(int prec, const IterArgs& a, int num_sms);
+LaunchCfg iter_config(int prec, const IterArgs& a, int num_sms, int schedule = SCHED_CHAIN);
 int launch_iter(int prec, const IterArgs& a, const LaunchCfg& cfg, int nu, int mode, void* stream);
 int launch_pack(int prec, int n, int n_k, int n_v, const double* K, const double* Lam, const double* prob,
                 void* packs, long long pack_stride, void* stream);
@@ -167,6 +185,16 @@ int launch_init_duals(int prec, const IterArgs& a, int warm, void* stream);
 int launch_convert(int prec, const double* src, void* dst, long long count, void* stream);
 size_t vec_size(int prec);
 
+// Per-kernel timing of full iterations (smpc_profile_solve): kStageEvents events per
+// iteration, read once the solve has finished so that launches still run ahead.
+struct Profile {
+  static constexpr int kStageEvents = 7;
+  std::vector<cudaEvent_t> ev;  // capacity x kStageEvents
+  int capacity = 0;
+  int count = 0;
+  int stages = 0;
+};
+
 // The launch plan of one solve (api.cpp): iteration launches nu >= polish_from of a
 // SMPC_BF16 factor run the float32-pack kernel on the same vectors (args32, cfg32).
 struct IterPlan {
@@ -175,6 +203,7 @@ struct IterPlan {
   LaunchCfg cfg, cfg32;
   int polish_from = 0x7fffffff;
   int anchor_every = 0;  // > 0: anchored solve (SMPC_BF16)
+  Profile* profile = nullptr;
 };
 constexpr size_t kStateSize = 8;  // bytes per dual-state entry (float64, or two float32)
 size_t mat_size(int prec);
@@ -225,6 +254,9 @@ struct smpc_factor_t {
   cudaStream_t last_stream = nullptr;
   int last_launches = 0;
   int num_sms = 0;
+  int schedule = smpc::SCHED_CHAIN;  // iteration schedule in use
+  float tuned_ms[3] = {0, 0, 0};     // per schedule: ms per iteration measured when the factor chose
+  smpc::Profile* profile = nullptr;  // set while smpc_profile_solve runs
   bool solved_once = false;
 
   template <typename T>

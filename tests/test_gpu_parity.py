@@ -6,6 +6,7 @@ Tolerances:
 * float32 / bfloat16 packs: |rho_rel,gpu - rho_rel,oracle| <= 1e-4 at equal iteration
   counts, with the elementwise error of u and the coupling residual stated in the
   assertion messages.
+Both iteration schedules (1: one CTA per chain; 2: node-parallel launches) are run.
 """
 import numpy as np
 import pytest
@@ -19,9 +20,12 @@ pytestmark = pytest.mark.gpu
 FP64_TOL = 1e-9
 
 
-def compare_fp64(P, steps, iters):
+SCHEDULES = [1, 2]
+
+
+def compare_fp64(P, steps, iters, schedule=0):
     R = H.oracle_run(P, steps, iters)
-    g = H.Gpu(P, steps=steps)
+    g = H.Gpu(P, steps=steps, schedule=schedule)
     try:
         info = g.solve(iters)
         u, x, y = g.arrays()
@@ -35,19 +39,21 @@ def compare_fp64(P, steps, iters):
     return info, R
 
 
+@pytest.mark.parametrize("schedule", SCHEDULES)
 @pytest.mark.parametrize("iters", [1, 10, 500])
-def test_tiny_fp64(iters):
+def test_tiny_fp64(iters, schedule):
     P = synth.tiny(0)
-    compare_fp64(P, H.tiny_steps(P), iters)
+    compare_fp64(P, H.tiny_steps(P), iters, schedule)
 
 
+@pytest.mark.parametrize("schedule", SCHEDULES)
 @pytest.mark.parametrize("name", list(H.edge_instances()))
 @pytest.mark.parametrize("iters", [1, 10, 200])
-def test_edge_trees_fp64(name, iters):
+def test_edge_trees_fp64(name, iters, schedule):
     P = H.edge_instances()[name]
     tree, fac, _ = H.oracle_build(P)
     steps = oracle.jacobi_steps(fac, tree)
-    compare_fp64(P, steps, iters)
+    compare_fp64(P, steps, iters, schedule)
 
 
 @pytest.fixture(scope="module")
@@ -59,10 +65,11 @@ def barcelona_case():
     return P, H.closed_form_steps(fac, tree, lam)
 
 
+@pytest.mark.parametrize("schedule", SCHEDULES)
 @pytest.mark.parametrize("iters", [1, 10, 60])
-def test_barcelona_fp64_full_size(barcelona_case, iters):
+def test_barcelona_fp64_full_size(barcelona_case, iters, schedule):
     P, steps = barcelona_case
-    compare_fp64(P, steps, iters)
+    compare_fp64(P, steps, iters, schedule)
 
 
 def test_lambda_and_preconditioner_match_oracle():
@@ -116,14 +123,15 @@ def test_deterministic_and_warm_start():
     assert max(H.relerr(u, R.u), H.relerr(x, R.x), H.relerr(y, H.stack_y(R.y))) <= FP64_TOL
 
 
-def test_tolerance_stop_matches_oracle_history():
+@pytest.mark.parametrize("schedule", SCHEDULES)
+def test_tolerance_stop_matches_oracle_history(schedule):
     P = synth.tiny(0)
     steps = H.tiny_steps(P)
     R = H.oracle_run(P, steps, 3000)
     tol = 1e-3
     first = int(np.argmax(R.rho_rel <= tol))
     assert R.rho_rel[first] <= tol
-    g = H.Gpu(P, steps=steps)
+    g = H.Gpu(P, steps=steps, schedule=schedule)
     try:
         info = g.solve(3000, tol=tol, check_every=16)
         u, x, y = g.arrays()
@@ -161,13 +169,14 @@ def test_not_supported_and_invalid_on_device():
         smpc.smpc_tree_destroy(tree)
 
 
+@pytest.mark.parametrize("schedule", SCHEDULES)
 @pytest.mark.parametrize("precision", [1, 2])
-def test_reduced_precision_residual(precision):
+def test_reduced_precision_residual(precision, schedule):
     P = synth.tiny(0)
     steps = H.tiny_steps(P)
     iters = 500
     R = H.oracle_run(P, steps, iters)
-    g = H.Gpu(P, steps=steps, precision=precision)
+    g = H.Gpu(P, steps=steps, precision=precision, schedule=schedule)
     try:
         info = g.solve(iters)
         u, x, y = g.arrays()
@@ -198,3 +207,73 @@ def test_device_resident_step_data_matches_host_inputs():
             assert bool((a == b).all())
     finally:
         g.close()
+
+
+@pytest.mark.parametrize("precision", [0, 1, 2])
+def test_schedules_agree_full_size(barcelona_case, precision):
+    """The two iteration schedules compute the same iterates up to rounding."""
+    P, steps = barcelona_case
+    out = []
+    for schedule in SCHEDULES:
+        g = H.Gpu(P, steps=steps, precision=precision, schedule=schedule)
+        try:
+            info = g.solve(200)
+            assert g.smpc.smpc_factor_schedule(g.fac)[0] == schedule
+            out.append((info["rho_rel"],) + g.arrays())
+        finally:
+            g.close()
+    diffs = [H.relerr(a, b) for a, b in zip(out[0][1:], out[1][1:])]
+    if precision == 0:  # float64: the two summation orders agree to rounding
+        assert abs(out[0][0] - out[1][0]) <= 1e-9
+        assert max(diffs) <= 1e-9, diffs
+    else:  # reduced precision: the stated residual tolerance; arrays reported
+        assert abs(out[0][0] - out[1][0]) <= 1e-4, (out[0][0], out[1][0], diffs)
+
+
+def test_auto_schedule_times_both():
+    P = synth.barcelona(0)
+    g = H.Gpu(P, precision=1)
+    try:
+        sched, ms = g.smpc.smpc_factor_schedule(g.fac)
+    finally:
+        g.close()
+    assert sched in (1, 2)
+    assert ms[1] > 0 and ms[2] > 0
+    assert ms[sched] == min(ms[1], ms[2])
+
+
+@pytest.mark.parametrize("schedule", SCHEDULES)
+def test_profile_solve_reports_every_kernel(schedule):
+    P = synth.tiny(0)
+    g = H.Gpu(P, steps=H.tiny_steps(P), precision=1, schedule=schedule)
+    try:
+        ms = g.smpc.smpc_profile_solve(g.fac, P["p"], P["q"], P["dhat"], P["alpha2"], eps=P["eps"], iters=20)
+    finally:
+        g.close()
+    assert len(ms) == (1 if schedule == 1 else 6)
+    assert all(t > 0 for t in ms)
+
+
+@pytest.mark.parametrize("anchor_every,polish", [(1, 0), (16, 50), (64, 100)])
+def test_bf16_anchor_and_polish(anchor_every, polish):
+    """bfloat16 packs with float32 anchors (and a final float32 polish) stay within the
+    reduced-precision tolerance of the oracle; anchor_every = 1 is the float32 iteration."""
+    P = synth.tiny(0)
+    steps = H.tiny_steps(P)
+    R = H.oracle_run(P, steps, 500)
+    g = H.Gpu(P, steps=steps, precision=2)
+    try:
+        info = g.smpc.smpc_solve(g.fac, P["p"], P["q"], P["dhat"], P["alpha2"], eps=P["eps"], max_iters=500,
+                                 sync=1, u=g.u, x=g.x, y=g.y, polish_iters=polish, anchor_every=anchor_every)
+        u, x, _ = g.arrays()
+        with pytest.raises(g.smpc.SmpcError) as ei:
+            g.smpc.smpc_solve(g.fac, P["p"], P["q"], P["dhat"], P["alpha2"], eps=P["eps"], max_iters=10,
+                              sync=1, polish_iters=11)
+        assert ei.value.code == g.smpc.SMPC_EINVAL
+    finally:
+        g.close()
+    d = P["dhat"][P["tree"]["stage"]] + P["eps"]
+    coupling = np.abs(u @ P["net"]["E"].T + d @ P["net"]["Ed"].T).max()
+    assert abs(info["rho_rel"] - R.rho_rel[-1]) <= 1e-4, (info["rho_rel"], R.rho_rel[-1], H.relerr(u, R.u), coupling)
+    if polish:  # the last iterations ran on float32 packs: the demand coupling holds to float32 rounding
+        assert coupling <= 1e-5
