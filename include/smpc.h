@@ -57,6 +57,7 @@ typedef enum smpc_precision {
 
 typedef struct smpc_tree smpc_tree;
 typedef struct smpc_factor_t smpc_factor_t;
+typedef struct smpc_server smpc_server;
 
 /* Flow-based network model x+ = A x + B u + G_d d, 0 = E u + E_d d (Sec. II-A,
  * eqs. model and demand-control).  A may be NULL for the identity (tank mass
@@ -150,6 +151,8 @@ typedef struct smpc_result {
   double rho;           /* out: ||H z - t||_inf of the last iterate (Sec. IV-E) */
   double rho_rel;       /* out: rho / (1 + max(||H z||_inf, ||t||_inf)) */
   int32_t launches;     /* out: kernel launches the solve enqueued (set on return) */
+  double queue_ms;      /* out (smpc_poll only): submit to admission, host wall clock */
+  double run_ms;        /* out (smpc_poll only): admission to completion, host wall clock */
 } smpc_result;
 
 typedef struct smpc_tree_info {
@@ -242,6 +245,35 @@ int smpc_profile_solve(smpc_factor_t* fac, const smpc_step_data* data, int32_t i
  * rho_rel, u0_host, history_host) exactly as a synchronous solve would.
  * Errors: SMPC_EINVAL (no solve yet), SMPC_ECUDA, SMPC_ETIMEOUT, SMPC_EDIVERGED. */
 int smpc_solve_info(smpc_factor_t* fac, smpc_result* res);
+
+/* The device memory a factor holds (bytes): its packs, vectors and buffers.  This is
+ * the footprint a server admits requests by. */
+size_t smpc_factor_device_bytes(const smpc_factor_t* fac);
+
+/* Serving (the paper's closed loop, Alg. 2, run for many controllers at once).  A
+ * server owns max_slots execution slots, each a host worker thread with its own
+ * non-blocking CUDA stream on the device current at creation.  smpc_submit queues one
+ * solve of a factor and returns at once with a ticket; a queued request is admitted
+ * into a free slot, in arrival order among the requests that can run, when the device
+ * memory of the factors being solved plus its own factor's fits hbm_budget (bytes).
+ * Admitted solves run concurrently, their kernels overlapping on the GPU, while new
+ * requests keep arriving.  A factor is held from admission until smpc_poll returns its
+ * ticket as done, so later requests of the same factor wait (a controller's next step
+ * warm-starts, with opts->warm_start, from the duals of its previous one).  Step data
+ * (host or device memory) is copied at submission; opts->sync is ignored.
+ * Errors: smpc_server_create: SMPC_EINVAL, SMPC_ENOMEM, SMPC_ECUDA.
+ *         smpc_submit: SMPC_EINVAL; SMPC_EBUSY when the factor alone exceeds the budget. */
+int smpc_server_create(size_t hbm_budget, int32_t max_slots, smpc_server** out);
+int smpc_submit(smpc_server* server, smpc_factor_t* fac, const smpc_step_data* data, const smpc_solve_opts* opts,
+                uint64_t* ticket);
+/* Non-blocking.  *done = 0 while the ticket is queued or running.  Once done, fills the
+ * host outputs of res (iterations, rho, rho_rel, launches, queue_ms, run_ms, and u0_host /
+ * history_host when not NULL) and copies u, x, y to the device pointers of res that are
+ * not NULL, releases the ticket and the factor, and returns the solve's status.  res may
+ * be NULL.  Errors: SMPC_EINVAL (unknown ticket), the solve's own error, SMPC_ECUDA. */
+int smpc_poll(smpc_server* server, uint64_t ticket, smpc_result* res, int32_t* done);
+/* Waits for the admitted solves, drops the queued ones and releases the server. */
+void smpc_server_destroy(smpc_server* server);
 
 const char* smpc_status_string(int status);
 const char* smpc_last_error(void);

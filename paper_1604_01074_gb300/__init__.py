@@ -52,7 +52,8 @@ class smpc_solve_opts(ctypes.Structure):
 class smpc_result(ctypes.Structure):
     _fields_ = [("u", ctypes.c_void_p), ("x", ctypes.c_void_p), ("y", ctypes.c_void_p), ("u0_host", _dp),
                 ("history_host", _dp), ("iterations", ctypes.c_int32), ("rho", ctypes.c_double),
-                ("rho_rel", ctypes.c_double), ("launches", ctypes.c_int32)]
+                ("rho_rel", ctypes.c_double), ("launches", ctypes.c_int32), ("queue_ms", ctypes.c_double),
+                ("run_ms", ctypes.c_double)]
 
 
 class smpc_tree_info(ctypes.Structure):
@@ -70,6 +71,13 @@ SIGNATURES = {
     "smpc_factor_destroy": (None, [ctypes.c_void_p]),
     "smpc_factor_steps": (ctypes.c_int, [ctypes.c_void_p, _dp, _dp, _dp, _dp]),
     "smpc_factor_schedule": (ctypes.c_int, [ctypes.c_void_p, _dp]),
+    "smpc_factor_device_bytes": (ctypes.c_size_t, [ctypes.c_void_p]),
+    "smpc_server_create": (ctypes.c_int, [ctypes.c_size_t, ctypes.c_int32, ctypes.POINTER(ctypes.c_void_p)]),
+    "smpc_submit": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(smpc_step_data),
+                                   ctypes.POINTER(smpc_solve_opts), ctypes.POINTER(ctypes.c_uint64)]),
+    "smpc_poll": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64, ctypes.POINTER(smpc_result),
+                                 ctypes.POINTER(ctypes.c_int32)]),
+    "smpc_server_destroy": (None, [ctypes.c_void_p]),
     "smpc_profile_solve": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(smpc_step_data), ctypes.c_int32, _dp,
                                           ctypes.c_int32]),
     "smpc_solve": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(smpc_step_data), ctypes.POINTER(smpc_solve_opts),
@@ -259,6 +267,47 @@ def smpc_profile_solve(fac, p, q, dhat, alpha2, eps=None, iters=50):
     if n < 0:
         raise SmpcError(-n, smpc_last_error())
     return [out[i] for i in range(n)]
+
+
+def smpc_factor_device_bytes(fac):
+    return int(lib().smpc_factor_device_bytes(fac))
+
+
+def smpc_server_create(hbm_budget, max_slots):
+    h = ctypes.c_void_p()
+    _check(lib().smpc_server_create(int(hbm_budget), int(max_slots), ctypes.byref(h)), "smpc_server_create")
+    return h
+
+
+def smpc_server_destroy(server):
+    lib().smpc_server_destroy(server)
+
+
+def smpc_submit(server, fac, p, q, dhat, alpha2, eps=None, max_iters=500, tol=0.0, warm_start=0, check_every=0,
+                polish_iters=0, anchor_every=0):
+    """Queues one solve; returns its ticket.  Step data: numpy float64 arrays."""
+    k = _Keep()
+    D = smpc_step_data(k(p), k(q), k(dhat), k(eps), k(alpha2))
+    O = smpc_solve_opts(int(max_iters), float(tol), int(warm_start), int(check_every), 0, int(polish_iters),
+                        int(anchor_every))
+    t = ctypes.c_uint64()
+    _check(lib().smpc_submit(server, fac, ctypes.byref(D), ctypes.byref(O), ctypes.byref(t)), "smpc_submit")
+    return t.value
+
+
+def smpc_poll(server, ticket, u=None, x=None, y=None, u0_host=None, history_host=None):
+    """None while the ticket is queued or running; else the result dict (outputs copied)."""
+    def dptr(t):
+        return None if t is None else (t if isinstance(t, int) else t.data_ptr())
+
+    R = smpc_result(dptr(u), dptr(x), dptr(y), None if u0_host is None else u0_host.ctypes.data_as(_dp),
+                    None if history_host is None else history_host.ctypes.data_as(_dp), -1, 0.0, 0.0, 0, 0.0, 0.0)
+    done = ctypes.c_int32()
+    _check(lib().smpc_poll(server, ctypes.c_uint64(ticket), ctypes.byref(R), ctypes.byref(done)), "smpc_poll")
+    if not done.value:
+        return None
+    return {"iterations": R.iterations, "rho": R.rho, "rho_rel": R.rho_rel, "launches": R.launches,
+            "queue_ms": R.queue_ms, "run_ms": R.run_ms}
 
 
 def smpc_solve_info(fac, u0_host=None, history_host=None):

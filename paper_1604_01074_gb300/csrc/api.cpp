@@ -532,6 +532,13 @@ int plan_iters(const smpc_factor_t* f, const IterArgs& a, const smpc_solve_opts&
   return SMPC_OK;
 }
 
+int copy_final_y(smpc_factor_t* f, void* dst) {
+  IterArgs a = make_args(f);
+  TRY(launch_copy_final_y(f->prec, a, 0, dst, nullptr));
+  CK(cudaStreamSynchronize(nullptr));
+  return SMPC_OK;
+}
+
 int launch_planned(const IterPlan& plan, int nu, int mode, void* stream) {
   int prec = plan.prec;
   const IterArgs* a = &plan.args;
@@ -892,6 +899,8 @@ int smpc_factor(const smpc_tree* tree, const smpc_network* net, const smpc_cost*
 }
 
 void smpc_factor_destroy(smpc_factor_t* f) { delete f; }
+
+size_t smpc_factor_device_bytes(const smpc_factor_t* f) { return f ? f->device_bytes : 0; }
 
 int smpc_factor_schedule(const smpc_factor_t* f, double* ms_per_iter) {
   if (!f) {

@@ -1645,15 +1645,16 @@ LaunchCfg config_t(const IterArgs& a, int num_sms, int S_max, int schedule) {
 
 template <typename VT, typename MT>
 int launch_t(const IterArgs& a, const LaunchCfg& c, int nu, int mode, cudaStream_t s) {
-  static bool attr_set = false;
-  if (!attr_set) {
+  // once per process and instantiation; thread-safe (solves may run on several threads)
+  static const bool attr_set = [] {
     cudaFuncSetAttribute(apg_iter<VT, MT>, cudaFuncAttributeMaxDynamicSharedMemorySize, 232448);
     cudaFuncSetAttribute(node_mv<VT, MT, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 232448);
     cudaFuncSetAttribute(node_mv<VT, MT, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 232448);
     cudaFuncSetAttribute(prox_node<VT, MT>, cudaFuncAttributeMaxDynamicSharedMemorySize, 232448);
     cudaFuncSetAttribute(fwd_scan<VT, MT>, cudaFuncAttributeMaxDynamicSharedMemorySize, 232448);
-    attr_set = true;
-  }
+    return true;
+  }();
+  (void)attr_set;
   int ev = 0;
   auto mark = [&]() {
     if (c.events) cudaEventRecord(c.events[ev++], s);

@@ -215,6 +215,8 @@ namespace smpc {
 // does not fit the shared-memory pipeline.
 int plan_iters(const smpc_factor_t* f, const IterArgs& a, const smpc_solve_opts& opts, IterPlan* plan);
 int launch_planned(const IterPlan& plan, int nu, int mode, void* stream);
+// Copies the final dual of the factor's last solve (vector type) to dst; synchronous.
+int copy_final_y(smpc_factor_t* f, void* dst);
 }  // namespace smpc
 
 // Factor state shared by the solve entry points (api.cpp, noalloc.cu).
@@ -228,6 +230,7 @@ struct smpc_factor_t {
   double W_alpha = 0;
   smpc::HostFactor hf;
   std::vector<void*> allocs;
+  size_t device_bytes = 0;  // sum of this factor's device allocations
   // device
   void* packs = nullptr;
   void* packs32 = nullptr;    // SMPC_BF16 only: float32 packs (anchor and polish launches)
@@ -270,6 +273,7 @@ struct smpc_factor_t {
       return e == cudaErrorMemoryAllocation ? SMPC_ENOMEM : SMPC_ECUDA;
     }
     allocs.push_back(q);
+    device_bytes += bytes;
     *p = static_cast<T*>(q);
     return SMPC_OK;
   }
