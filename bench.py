@@ -474,6 +474,138 @@ def profile_solve(args):
     print(json.dumps({"profile_solve": args.profile_solve, "precision": args.precision, "info": info}))
 
 
+# --------------------------------------------------------------------- serving (closed loop)
+SERVE_WORKLOAD = ("64 closed-loop MPC sessions on 4 networks (n_x, n_u) in {(20,40),(35,65),(50,90),(63,114)}, "
+                  "N in {12,18,24}, 10-500 scenarios (249,644 nodes in all); Poisson arrivals")
+
+
+def _session_request(P, k, x, q):
+    """MPC step k of a session: measured state x, previous input q, forecast and prices
+    shifted by k hours from the instance's own start hour."""
+    import synth
+    from synth.problems import day_night_price
+    N = P["tree"]["horizon"]
+    dhat = synth.demand_forecast(P["net"], N, t0=k)
+    base = P["alpha2"] / np.maximum(day_night_price(N, 0)[:, None], 1e-300)
+    return {"p": x, "q": q, "dhat": dhat, "alpha2": day_night_price(N, t0=k)[:, None] * base}
+
+
+def _plant_step(P, x, u0, k, rng):
+    """Tank mass balance x+ = x + B u_0 + G_d d with the realised demand (forecast plus
+    10 % noise), clipped to the tank capacities."""
+    import synth
+    net = P["net"]
+    d = synth.demand_forecast(net, 1, t0=k)[0]
+    d = d * (1 + 0.1 * rng.standard_normal(d.shape))
+    return np.clip(x + net["B"] @ u0 + net["Gd"] @ d, 0.0, net["cap"])
+
+
+def run_serve(args):
+    import torch
+
+    import paper_1604_01074_gb300 as smpc
+    import synth
+    torch.cuda.set_device(0)
+    insts = synth.batch_instances(0)
+    log("serve: building", len(insts), "factors")
+    sess = []
+    for i, P in enumerate(insts):
+        t = P["tree"]
+        tree = smpc.smpc_tree_create(t["parent"], t["prob"])
+        prec = 1 if i % 2 == 0 else 2  # float32 and bfloat16 packs, mixed
+        fac = smpc.smpc_factor(tree, P["net"], P["cost"], precision=prec, precondition=1)
+        sess.append({"P": P, "tree": tree, "fac": fac, "prec": prec, "x": P["p"].copy(), "q": P["q"].copy(),
+                     "k": 0, "pending": [], "rng": np.random.default_rng(100 + i)})
+    total_bytes = sum(smpc.smpc_factor_device_bytes(s_["fac"]) for s_ in sess)
+    budget = int(args.serve_budget_gb * 1e9)
+    server = smpc.smpc_server_create(budget, args.serve_slots)
+    rng = np.random.default_rng(0)
+    lat, queue_ms, run_ms, its, reached = [], [], [], [], 0
+    offered = 0
+    t0 = time.perf_counter()
+    next_arrival = t0 + rng.exponential(1.0 / args.serve_rate)
+    arrivals_end = t0 + args.serve_seconds
+
+    def poll_all():
+        nonlocal reached
+        for s_ in sess:
+            while s_["pending"]:
+                tk, ts, k = s_["pending"][0]
+                u0 = np.zeros(s_["P"]["net"]["n_u"])
+                r = smpc.smpc_poll(server, tk, u0_host=u0)
+                if r is None:
+                    break
+                s_["pending"].pop(0)
+                lat.append(1000.0 * (time.perf_counter() - ts))
+                queue_ms.append(r["queue_ms"])
+                run_ms.append(r["run_ms"])
+                its.append(r["iterations"])
+                reached += r["rho_rel"] <= args.tol
+                s_["x"] = _plant_step(s_["P"], s_["x"], u0, k, s_["rng"])
+                s_["q"] = u0
+
+    while True:
+        now = time.perf_counter()
+        while now < arrivals_end and next_arrival <= now:
+            s_ = sess[int(rng.integers(len(sess)))]
+            req = _session_request(s_["P"], s_["k"], s_["x"], s_["q"])
+            tk = smpc.smpc_submit(server, s_["fac"], req["p"], req["q"], req["dhat"], req["alpha2"], eps=s_["P"]["eps"],
+                                  max_iters=args.serve_max_iters, tol=args.tol, warm_start=int(s_["k"] > 0))
+            s_["pending"].append((tk, time.perf_counter(), s_["k"]))
+            s_["k"] += 1
+            offered += 1
+            next_arrival += rng.exponential(1.0 / args.serve_rate)
+        poll_all()
+        outstanding = sum(len(s_["pending"]) for s_ in sess)
+        if now >= arrivals_end and (outstanding == 0 or now > arrivals_end + args.serve_drain):
+            break
+        time.sleep(0.0002)
+    elapsed = time.perf_counter() - t0
+    dropped = sum(len(s_["pending"]) for s_ in sess)
+    smpc.smpc_server_destroy(server)  # waits for the admitted solves; queued ones are dropped
+    done = len(lat)
+    result = {
+        "metric": "SMPC serving: solves/s and p50/p99 latency (ms), closed loop, tol 1e-3", "impl": "ours-serve",
+        "value": done / elapsed, "unit": "solves/s", "offered_rate": args.serve_rate, "offered": offered,
+        "completed": done, "unfinished_at_end": dropped, "seconds": elapsed,
+        "p50_ms": float(np.percentile(lat, 50)) if lat else None, "p99_ms": float(np.percentile(lat, 99)) if lat else None,
+        "queue_p50_ms": float(np.percentile(queue_ms, 50)) if lat else None,
+        "run_p50_ms": float(np.percentile(run_ms, 50)) if lat else None,
+        "iterations_mean": float(np.mean(its)) if its else None, "reached_tol": reached,
+        "config": {"workload": SERVE_WORKLOAD, "slots": args.serve_slots, "hbm_budget_bytes": budget,
+                   "factor_bytes_total": total_bytes, "precision": "fp32 and bf16 packs, alternating by session",
+                   "max_iters": args.serve_max_iters, "tol": args.tol, "warm_start": "each session's previous step"},
+    }
+    # baseline: the plain per-request FP64 solve, one at a time, on a sample of sessions
+    # (cold first step untimed, then two warm-started closed-loop steps timed)
+    base = []
+    for s_ in sess[: args.serve_baseline]:
+        P = s_["P"]
+        f64 = smpc.smpc_factor(s_["tree"], P["net"], P["cost"], precision=0, precondition=1)
+        x, q = P["p"].copy(), P["q"].copy()
+        for k in range(3):
+            req = _session_request(P, k, x, q)
+            u0 = np.zeros(P["net"]["n_u"])
+            torch.cuda.synchronize()
+            ts = time.perf_counter()
+            smpc.smpc_solve(f64, req["p"], req["q"], req["dhat"], req["alpha2"], eps=P["eps"],
+                            max_iters=args.serve_max_iters, tol=args.tol, warm_start=int(k > 0), sync=1, u0_host=u0)
+            if k > 0:
+                base.append(1000.0 * (time.perf_counter() - ts))
+            x = _plant_step(P, x, u0, k, s_["rng"])
+            q = u0
+        smpc.smpc_factor_destroy(f64)
+    if base:
+        result["fp64_per_request"] = {"mean_ms": float(np.mean(base)), "p50_ms": float(np.percentile(base, 50)),
+                                      "p99_ms": float(np.percentile(base, 99)),
+                                      "solves_per_s": 1000.0 / float(np.mean(base)),
+                                      "sample": f"{len(base)} warm-started steps of {args.serve_baseline} sessions"}
+    for s_ in sess:
+        smpc.smpc_factor_destroy(s_["fac"])
+        smpc.smpc_tree_destroy(s_["tree"])
+    return result
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return None
@@ -527,6 +659,14 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-other-precisions", dest="other_legs", action="store_false")
     ap.add_argument("--oracle-sample", type=int, default=0)
+    ap.add_argument("--serve", action="store_true", help="closed-loop serving workload (its own JSON line)")
+    ap.add_argument("--serve-rate", type=float, default=200.0)
+    ap.add_argument("--serve-seconds", type=float, default=20.0)
+    ap.add_argument("--serve-drain", type=float, default=30.0)
+    ap.add_argument("--serve-slots", type=int, default=4)
+    ap.add_argument("--serve-budget-gb", type=float, default=64.0)
+    ap.add_argument("--serve-max-iters", type=int, default=5000)
+    ap.add_argument("--serve-baseline", type=int, default=6)
     ap.add_argument("--profile-solve", type=int, default=0,
                     help="factor + one solve of this many iterations (tol 0) and exit: the case ncu captures")
     args = ap.parse_args()
@@ -535,6 +675,9 @@ def main():
         return
     if args.profile_solve:
         profile_solve(args)
+        return
+    if args.serve:
+        print(json.dumps(run_serve(args), default=_jsonable))
         return
     rank, world, local_rank = dist_env()
     if args.impl == "reference":

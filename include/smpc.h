@@ -103,6 +103,11 @@ typedef struct smpc_factor_opts {
   const double* step_s;
   const double* step_z;
   const double* step_p;
+  /* 1: one pack for all nodes - [Bbar; L] and Lambda are the same at every node, only the
+   * scale 1 / (2 p_n) differs and is applied to Lambda r - held in shared memory while the
+   * mat-vecs run, so that the matrices leave HBM traffic; 0: one pack per node (the
+   * node-indexed matrices of Alg. 1 and App. B).  Results agree to rounding. */
+  int32_t shared_packs;
   /* Iteration schedule: 1 = one launch per iteration with one CTA per chain (maximal
    * leaf path) of the tree; 2 = the backward sweep as subtree scans around per-node
    * mat-vec launches, one task per node; 0 = time both on this GPU when the factor is

@@ -36,7 +36,8 @@ class smpc_cost(ctypes.Structure):
 class smpc_factor_opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int32), ("precondition", ctypes.c_int32), ("lambda_", ctypes.c_double),
                 ("power_iters", ctypes.c_int32), ("lambda_margin", ctypes.c_double),
-                ("step_s", _dp), ("step_z", _dp), ("step_p", _dp), ("schedule", ctypes.c_int32)]
+                ("step_s", _dp), ("step_z", _dp), ("step_p", _dp), ("shared_packs", ctypes.c_int32),
+                ("schedule", ctypes.c_int32)]
 
 
 class smpc_step_data(ctypes.Structure):
@@ -163,7 +164,7 @@ def smpc_tree_destroy(tree):
 
 
 def smpc_factor(tree, net, cost, precision=SMPC_FP64, precondition=1, lam=0.0, power_iters=0, lambda_margin=0.0,
-                steps=None, safety_unweighted=0, schedule=0):
+                steps=None, safety_unweighted=0, schedule=0, shared_packs=0):
     """net / cost: dicts with the fields of smpc_network / smpc_cost (numpy arrays).
     steps: optional dict {'s': (n,), 'z': (n,), 'p': (n, n_u)} of explicit per-entry steps.
     schedule: 0 = time both iteration schedules and keep the faster, 1 = chain, 2 = node."""
@@ -178,7 +179,7 @@ def smpc_factor(tree, net, cost, precision=SMPC_FP64, precondition=1, lam=0.0, p
                   k(cost["x_min"]), k(cost["x_max"]), k(cost["x_s"]), k(cost["u_min"]), k(cost["u_max"]),
                   int(safety_unweighted))
     O = smpc_factor_opts(int(precision), int(precondition), float(lam), int(power_iters), float(lambda_margin),
-                         None, None, None, int(schedule))
+                         None, None, None, int(shared_packs), int(schedule))
     if steps is not None:
         O.step_s, O.step_z, O.step_p = k(steps["s"]), k(steps["z"]), k(steps["p"])
     h = ctypes.c_void_p()

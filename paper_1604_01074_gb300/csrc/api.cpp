@@ -253,6 +253,7 @@ IterArgs make_args(const smpc_factor_t* f) {
   a.path_off = t->dev.path_off;
   a.path_node = t->dev.path_node;
   a.packs = f->packs;
+  a.pscale = f->pscale;
   a.pack_stride = f->pack_stride;
   a.ybuf0 = f->ybuf0;
   a.ybuf1 = f->ybuf1;
@@ -735,16 +736,24 @@ int smpc_factor(const smpc_tree* tree, const smpc_network* net, const smpc_cost*
       (rc = up64(&f->Rhat, f->hf.Rhat.data(), f->hf.Rhat.size())) || (rc = up64(&f->L, f->hf.L.data(), f->hf.L.size())) ||
       (rc = up64(&f->alpha1, cost->alpha1, n_u)))
     return fail(rc);
-  // ---- packs
-  f->pack_stride = pack_entries(f->prec, n_k, n_v);
-  if ((rc = f->alloc(&f->packs, (size_t)n * f->pack_stride * f->ms))) return fail(rc);
-  if ((rc = launch_pack(f->prec, n, n_k, n_v, f->K64, f->Lam64, tree->dev.prob, f->packs, f->pack_stride, nullptr)))
-    return fail(rc);
-  if (f->prec == SMPC_BF16) {  // float32 packs for the polish iterations
-    f->pack_stride32 = pack_entries(SMPC_FP32, n_k, n_v);
-    if ((rc = f->alloc(&f->packs32, (size_t)n * f->pack_stride32 * sizeof(float)))) return fail(rc);
-    if ((rc = launch_pack(SMPC_FP32, n, n_k, n_v, f->K64, f->Lam64, tree->dev.prob, f->packs32, f->pack_stride32,
-                          nullptr)))
+  // ---- packs: one per node, or one shared pack (Lambda unscaled) and the node scales
+  f->shared_packs = o.shared_packs != 0;
+  const int np = f->shared_packs ? 1 : n;
+  const double* pprob = f->shared_packs ? nullptr : tree->dev.prob;
+  const long long pe = pack_entries(f->prec, n_k, n_v);
+  f->pack_stride = f->shared_packs ? 0 : pe;
+  if ((rc = f->alloc(&f->packs, (size_t)np * pe * f->ms))) return fail(rc);
+  if ((rc = launch_pack(f->prec, np, n_k, n_v, f->K64, f->Lam64, pprob, f->packs, pe, nullptr))) return fail(rc);
+  if (f->shared_packs) {
+    std::vector<double> sc(n);
+    for (int m = 0; m < n; ++m) sc[m] = 1.0 / (2.0 * tree->prob[m]);
+    if ((rc = f->alloc(&f->pscale, (size_t)n * f->vs)) || (rc = put_vec(f, f->pscale, sc.data(), n))) return fail(rc);
+  }
+  if (f->prec == SMPC_BF16) {  // float32 packs for the anchor and polish iterations
+    const long long pe32 = pack_entries(SMPC_FP32, n_k, n_v);
+    f->pack_stride32 = f->shared_packs ? 0 : pe32;
+    if ((rc = f->alloc(&f->packs32, (size_t)np * pe32 * sizeof(float)))) return fail(rc);
+    if ((rc = launch_pack(SMPC_FP32, np, n_k, n_v, f->K64, f->Lam64, pprob, f->packs32, pe32, nullptr)))
       return fail(rc);
     const size_t hb = sizeof(float) * (size_t)n * n_k;
     if ((rc = f->alloc(&f->ha, hb)) || (rc = f->alloc(&f->wa, hb))) return fail(rc);

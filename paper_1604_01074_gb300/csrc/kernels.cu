@@ -456,6 +456,13 @@ struct Kern {
     return reinterpret_cast<const MT*>(a.packs) + (long long)n * a.pack_stride;
   }
   __device__ bool linear() const { return (mode & MODE_LINEAR) != 0; }
+  // shared pack: the node scale 1 / (2 p_n) is applied to delta = Lambda r
+  __device__ void scale_delta(int m) {
+    if (!a.pscale) return;
+    const AT sc = (AT)cv(a.pscale)[m];
+    if (threadIdx.x < a.n_v) sm.dv[threadIdx.x] *= sc;
+    __syncthreads();
+  }
   // Anchored solves (bfloat16 packs): an anchor launch evaluates the solve step at
   // w_a = w^nu with the float32 packs (h_a, stored apart); the launches between run
   // the bfloat16 packs on w - w_a only, without the affine data, since the solve
@@ -1055,6 +1062,7 @@ struct Kern {
     const int ls = wait_l(p);
     if (abort_) return;
     matvec_t<MT, AT>(sm.Lm(ls), a.n_v, a.n_v, sm.ld, sm.rv, sm.dv, sm.part);  // Lambda is symmetric
+    scale_delta(m);
     if (refill) issue_l(p);
     matvec_n<MT, AT>(sm.K(ks), a.n_k, sm.ld, sm.dv, sm.yv);
     if (e < a.n_k) {
@@ -1414,6 +1422,9 @@ __global__ void __launch_bounds__(kThreads, 1) node_mv(const __grid_constant__ I
   }
   for (int j = a.n_v + tid; j < sm.ld; j += kThreads) sm.dv[j] = 0;
   __syncthreads();
+  // shared pack (pack_stride 0): one copy into slot 0, kept for every node
+  const bool shared = a.pack_stride == 0;
+  if (shared) S = 1;
   auto issue = [&](int q) {  // thread 0: copies of the q-th node into slot q % S
     const int m = blockIdx.x + q * G;
     const int slot = q % S;
@@ -1424,7 +1435,7 @@ __global__ void __launch_bounds__(kThreads, 1) node_mv(const __grid_constant__ I
     if (DH) bulk_g2s(sm.Lm(slot), src + kp * sizeof(MT), lb, &sm.barK[slot]);
   };
   if (tid == 0)
-    for (int q = 0; q < S && q < count; ++q) issue(q);
+    for (int q = 0; q < S && q < count && (!shared || q == 0); ++q) issue(q);
   const VT* wb = reinterpret_cast<const VT*>(a.wbuf);
   const VT* sp = reinterpret_cast<const VT*>(a.spub);
   VT* rp = reinterpret_cast<VT*>(a.rpub);
@@ -1438,13 +1449,18 @@ __global__ void __launch_bounds__(kThreads, 1) node_mv(const __grid_constant__ I
     } else if (tid < a.n_k) {
       sm.yv[tid] = tid < a.n_x ? (AT)sp[m * a.n_x + tid] : (AT)wb[m * a.n_k + tid];
     }
-    const bool ok = mbar_wait(&sm.barK[slot], (q / S) & 1);
+    const bool ok = (shared && q > 0) || mbar_wait(&sm.barK[slot], shared ? 0 : (q / S) & 1);
     if (__syncthreads_or(!ok)) {
       failed_at = q;
       break;
     }
     if (DH) {
       matvec_t<MT, AT>(sm.Lm(slot), a.n_v, a.n_v, sm.ld, sm.rv, sm.dv, sm.part);  // Lambda is symmetric
+      if (a.pscale) {  // shared pack: delta = (Lambda r) / (2 p_n)
+        const AT sc = (AT)reinterpret_cast<const VT*>(a.pscale)[m];
+        if (tid < a.n_v) sm.dv[tid] *= sc;
+        __syncthreads();
+      }
       matvec_n<MT, AT>(sm.K(slot), a.n_k, sm.ld, sm.dv, sm.yv);
       if (tid < a.n_k) {
         VT* h = reinterpret_cast<VT*>(a.h);
@@ -1460,13 +1476,13 @@ __global__ void __launch_bounds__(kThreads, 1) node_mv(const __grid_constant__ I
       if (tid < a.n_v) rp[m * a.n_v + tid] = (VT)sm.gv[tid];
     }
     __syncthreads();  // the slot and the vectors are free again
-    if (tid == 0 && q + S < count) issue(q + S);
+    if (tid == 0 && !shared && q + S < count) issue(q + S);
   }
   if (failed_at >= 0 && tid == 0) {
     // let this CTA's copies still in flight (nodes failed_at .. failed_at + S - 1) land,
     // each wait bounded, before leaving
     a.flags[1] = SMPC_ETIMEOUT;
-    const int end = min(count, failed_at + S);
+    const int end = shared ? min(count, 1) : min(count, failed_at + S);
     for (int q = failed_at; q < end; ++q) mbar_wait(&sm.barK[q % S], (q / S) & 1);
   }
 }
@@ -1479,7 +1495,7 @@ __global__ void pack_kernel(int n, int n_k, int n_v, const double* K, const doub
   const int ld = row_stride<MT>(n_v);
   for (int m = blockIdx.x; m < n; m += gridDim.x) {
     MT* dst = packs + (long long)m * stride;
-    const double inv = 1.0 / (2.0 * prob[m]);
+    const double inv = prob ? 1.0 / (2.0 * prob[m]) : 1.0;  // no prob: the shared pack, Lambda unscaled
     for (long long q = threadIdx.x; q < kp; q += blockDim.x) {
       const long long i = q / ld, j = q % ld;
       dst[q] = (MT)(i < n_k && j < n_v ? K[i * n_v + j] : 0.0);

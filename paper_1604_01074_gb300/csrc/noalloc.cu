@@ -238,6 +238,7 @@ extern "C" int smpc_solve_static(smpc_factor_t* f, const smpc_step_data* data, c
   a.top_expect = t->dev.top_expect;
   a.path_off = t->dev.path_off;
   a.path_node = t->dev.path_node;
+  a.pscale = f->pscale;
   a.packs = f->packs;
   a.pack_stride = f->pack_stride;
   a.ybuf0 = f->ybuf0;

@@ -79,7 +79,8 @@ struct IterArgs {
   const int* path_off;
   const int* path_node;
   const void* packs;             // per node: [Bbar; L] (n_k x n_v) then Lambda/(2 p_n) (n_v x n_v)
-  long long pack_stride;         // entries between consecutive nodes' packs
+  long long pack_stride;         // entries between consecutive nodes' packs (0: one shared pack)
+  const void* pscale;            // shared pack: per node 1 / (2 p_n), applied to Lambda r; else NULL
   void* ybuf0;                   // y^k for even k: n x (2 n_x + n_u) of the state type
   void* ybuf1;                   // y^k for odd k (float64, or float32 pairs hi + lo)
   void* wbuf;                    // w^nu restricted to (xi, psi): n x n_k
@@ -233,6 +234,8 @@ struct smpc_factor_t {
   size_t device_bytes = 0;  // sum of this factor's device allocations
   // device
   void* packs = nullptr;
+  bool shared_packs = false;  // one pack [Bbar; L | Lambda] for every node, scaled by pscale
+  void* pscale = nullptr;     // shared packs: per node 1 / (2 p_n), vector type
   void* packs32 = nullptr;    // SMPC_BF16 only: float32 packs (anchor and polish launches)
   long long pack_stride32 = 0;
   void *ha = nullptr, *wa = nullptr;  // SMPC_BF16 only: anchor h and w, n x n_k each

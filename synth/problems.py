@@ -116,3 +116,42 @@ def random_instance(seed, n_x=3, n_u=5, n_d=3, n_e=1, horizon=5, max_children=3)
     rng = np.random.default_rng(seed + 1000)
     tree = random_tree(rng, horizon, max_children=max_children)
     return custom(seed, n_x, n_u, n_d, n_e, tree)
+
+
+BATCH_NETWORKS = ((20, 40), (35, 65), (50, 90), (63, 114))
+
+
+def batch_network(k, seed=0):
+    """Network k (0..3) of the batched workload: n_d ~ 1.4 n_x, n_e ~ 0.15 n_u."""
+    n_x, n_u = BATCH_NETWORKS[k]
+    rng = np.random.default_rng(7000 + 31 * seed + k)
+    net = make_network(rng, n_x=n_x, n_u=n_u, n_d=int(round(1.4 * n_x)), n_e=int(round(0.15 * n_u)))
+    return net, rng
+
+
+def batch_instances(seed=0, count=64):
+    """Uneven trees on four shared networks: instance i uses network i % 4, a horizon
+    drawn from {12, 18, 24} and a scenario count uniform in [10, 500]; the tree branches
+    at stages 0-2 with fan-out ceil(S^(1/3)) and a near-even last branching stage that
+    reaches exactly S scenarios.  Barcelona-scale weights; per-instance state,
+    forecasts and deviations."""
+    nets = [batch_network(k, seed) for k in range(len(BATCH_NETWORKS))]
+    costs = [_barcelona_costs(rng, net) for net, rng in nets]
+    rng = np.random.default_rng(9000 + seed)
+    out = []
+    for i in range(count):
+        k = i % len(nets)
+        net = nets[k][0]
+        N = int(rng.choice([12, 18, 24]))
+        S = int(rng.integers(10, 501))
+        b = 1
+        while b ** 3 < S:
+            b += 1
+        tree = make_tree([b, b, b], N, S)
+        alpha1, pump_coef = costs[k]
+        P = assemble(net, tree, np.random.default_rng(10000 + 97 * seed + i), W_alpha=2e4,
+                     W_u=1e5 * np.eye(net["n_u"]), W_x=1e7, gamma_d=5e7, alpha1=alpha1, pump_coef=pump_coef,
+                     t0=int(rng.integers(0, 24)), name=f"batch{i}")
+        P["network"] = k
+        out.append(P)
+    return out

@@ -23,9 +23,9 @@ FP64_TOL = 1e-9
 SCHEDULES = [1, 2]
 
 
-def compare_fp64(P, steps, iters, schedule=0):
+def compare_fp64(P, steps, iters, schedule=0, shared_packs=0):
     R = H.oracle_run(P, steps, iters)
-    g = H.Gpu(P, steps=steps, schedule=schedule)
+    g = H.Gpu(P, steps=steps, schedule=schedule, shared_packs=shared_packs)
     try:
         info = g.solve(iters)
         u, x, y = g.arrays()
@@ -277,3 +277,39 @@ def test_bf16_anchor_and_polish(anchor_every, polish):
     assert abs(info["rho_rel"] - R.rho_rel[-1]) <= 1e-4, (info["rho_rel"], R.rho_rel[-1], H.relerr(u, R.u), coupling)
     if polish:  # the last iterations ran on float32 packs: the demand coupling holds to float32 rounding
         assert coupling <= 1e-5
+
+
+@pytest.mark.parametrize("schedule", SCHEDULES)
+@pytest.mark.parametrize("name", ["tiny", "late_branch", "random_a", "single_node"])
+def test_shared_packs_fp64(name, schedule):
+    """One pack for all nodes (Lambda scaled per node after the mat-vec) gives the
+    oracle's iterates to the float64 tolerance."""
+    P = synth.tiny(0) if name == "tiny" else H.edge_instances()[name]
+    tree, fac, _ = H.oracle_build(P)
+    compare_fp64(P, oracle.jacobi_steps(fac, tree), 200, schedule, shared_packs=1)
+
+
+@pytest.mark.parametrize("schedule", SCHEDULES)
+def test_shared_packs_full_size(barcelona_case, schedule):
+    P, steps = barcelona_case
+    compare_fp64(P, steps, 10, schedule, shared_packs=1)
+
+
+@pytest.mark.parametrize("precision", [1, 2])
+def test_shared_packs_reduced_precision(precision):
+    P = synth.tiny(0)
+    steps = H.tiny_steps(P)
+    R = H.oracle_run(P, steps, 500)
+    g = H.Gpu(P, steps=steps, precision=precision, shared_packs=1)
+    try:
+        info = g.solve(500)
+        small = g.smpc.smpc_factor_device_bytes(g.fac)
+    finally:
+        g.close()
+    g = H.Gpu(P, steps=steps, precision=precision)
+    try:
+        per_node = g.smpc.smpc_factor_device_bytes(g.fac)
+    finally:
+        g.close()
+    assert abs(info["rho_rel"] - R.rho_rel[-1]) <= 1e-4
+    assert small < per_node
