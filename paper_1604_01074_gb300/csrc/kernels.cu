@@ -1615,6 +1615,192 @@ int check_launch(const char* what) {
   return SMPC_OK;
 }
 
+// Shared pack (pack_stride 0): the pack is copied into shared memory once per CTA and
+// applied to kNB nodes per pass, so that each 16-byte matrix load feeds kNB nodes.
+//   gt: g_b = [Bbar; L]' y_b,  y_b = [s_b; psi_b]
+//   dh: delta_b = (Lambda r_b) / (2 p_b),  h_b = [Bbar; L] delta_b
+// The transposed products use the column-group layout of matvec_t (thread (g, p): the
+// V columns of group g over row slice p, slices added in a fixed order); [Bbar; L] delta
+// gives each thread one row and all kNB dot products.
+constexpr int kNB = 8;
+
+template <typename MT>
+__host__ __device__ inline int multi_slices(int n_v) {
+  const int ld = row_stride<MT>(n_v);
+  const int G = ld / (16 / (int)sizeof(MT));
+  int P = kThreads / G;
+  return P > 16 ? 16 : P;
+}
+template <typename MT>
+__host__ __device__ inline size_t multi_smem_bytes(int n_x, int n_u, int n_v, bool dh) {
+  using AT = typename Acc<MT>::T;
+  const int n_k = n_x + n_u, ld = row_stride<MT>(n_v);
+  size_t b = round_up((long long)kpad<MT>(n_k, n_v) * sizeof(MT), 16);
+  if (dh) b += round_up((long long)lpad<MT>(n_v) * sizeof(MT), 16);
+  b += 16;                                                          // mbarrier
+  const size_t ldk = round_up(n_k, 4);
+  b += (size_t)kNB * ((ldk > (size_t)ld ? ldk : (size_t)ld) + ld) * sizeof(AT);  // inputs, outputs
+  b += (size_t)multi_slices<MT>(n_v) * kNB * ld * sizeof(AT);       // slice partial sums
+  return round_up(b, 128);
+}
+
+// out[b][j] = sum_i A[i*ld + j] x[b][i] (i < R, j < C) for kNB vectors x[b] (stride xs)
+template <typename MT, typename AT>
+__device__ void multi_t(const MT* A, int R, int C, int ld, const AT* x, int xs, AT* out, int os, AT* part) {
+  constexpr int V = Vec<MT>::V;
+  const int t = threadIdx.x;
+  const int G = ld / V;
+  const int P = multi_slices<MT>(C);
+  const int rc = (R + P - 1) / P;
+  if (t < P * G) {
+    const int g = t % G, p = t / G;
+    const int i0 = p * rc, i1 = min(R, i0 + rc);
+    AT acc[kNB][V];
+#pragma unroll
+    for (int b = 0; b < kNB; ++b)
+#pragma unroll
+      for (int k = 0; k < V; ++k) acc[b][k] = 0;
+    const MT* col = A + g * V;
+#pragma unroll 2
+    for (int i = i0; i < i1; ++i) {
+      AT av[V];
+      ld16(col + (long long)i * ld, av);
+#pragma unroll
+      for (int b = 0; b < kNB; ++b) {
+        const AT xb = x[b * xs + i];
+#pragma unroll
+        for (int k = 0; k < V; ++k) acc[b][k] += av[k] * xb;
+      }
+    }
+#pragma unroll
+    for (int b = 0; b < kNB; ++b) {
+      AT* dst = part + ((long long)p * kNB + b) * ld + g * V;
+#pragma unroll
+      for (int k = 0; k < V; ++k) dst[k] = acc[b][k];
+    }
+  }
+  __syncthreads();
+  for (int q = t; q < kNB * C; q += kThreads) {
+    const int b = q / C, j = q % C;
+    AT s = 0;
+    for (int p = 0; p < P; ++p) s += part[((long long)p * kNB + b) * ld + j];  // fixed order
+    out[b * os + j] = s;
+  }
+  __syncthreads();
+}
+
+template <typename VT, typename MT, bool DH>
+__global__ void __launch_bounds__(kThreads, 1) node_mv_shared(const __grid_constant__ IterArgs a, int nu, int mode) {
+  using AT = typename Acc<MT>::T;
+  constexpr int V = Vec<MT>::V;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  __shared__ int flag[2];
+  if (early_exit(a, nu, mode, flag, false)) return;
+  const int tid = threadIdx.x;
+  const int n_k = a.n_k, n_v = a.n_v, ld = row_stride<MT>(n_v);
+  const size_t kb = (size_t)kpad<MT>(n_k, n_v) * sizeof(MT), lb = (size_t)lpad<MT>(n_v) * sizeof(MT);
+  unsigned char* p = smem_raw;
+  const MT* K = reinterpret_cast<const MT*>(p);
+  p += round_up((long long)kb, 16);
+  const MT* Lm = reinterpret_cast<const MT*>(p);
+  if (DH) p += round_up((long long)lb, 16);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(p);
+  p += 16;
+  const int ldk = (int)round_up(n_k, 4);
+  const int lx = ldk > ld ? ldk : ld;
+  AT* xin = reinterpret_cast<AT*>(p);  // GT: y (kNB x ldk); DH: r (kNB x ld)
+  AT* dv = xin + kNB * lx;             // GT: g; DH: delta (kNB x ld, zero beyond n_v)
+  p += (size_t)kNB * (lx + ld) * sizeof(AT);
+  AT* part = reinterpret_cast<AT*>(p);
+  if (tid == 0) {
+    mbar_init(bar, 1);
+    fence_barrier_init();
+    fence_proxy_async();
+    const unsigned char* src = reinterpret_cast<const unsigned char*>(a.packs);
+    mbar_expect_tx(bar, (uint32_t)(kb + (DH ? lb : 0)));
+    bulk_g2s(const_cast<MT*>(K), src, (uint32_t)kb, bar);
+    if (DH) bulk_g2s(const_cast<MT*>(Lm), src + kpad<MT>(n_k, n_v) * sizeof(MT), (uint32_t)lb, bar);
+  }
+  for (int q = tid; q < kNB * ld; q += kThreads) dv[q] = 0;
+  __syncthreads();
+  const bool ok = mbar_wait(bar, 0);
+  if (__syncthreads_or(!ok)) {
+    if (tid == 0) {
+      a.flags[1] = SMPC_ETIMEOUT;
+      mbar_wait(bar, 0);  // bounded: let the copy in flight land before leaving
+    }
+    return;
+  }
+  const VT* wb = reinterpret_cast<const VT*>(a.wbuf);
+  const VT* sp = reinterpret_cast<const VT*>(a.spub);
+  VT* rp = reinterpret_cast<VT*>(a.rpub);
+  const VT* ps = reinterpret_cast<const VT*>(a.pscale);
+  const int batches = (a.n + kNB - 1) / kNB;
+  for (int bt = blockIdx.x; bt < batches; bt += gridDim.x) {
+    const long long m0 = (long long)bt * kNB;
+    const int nb = min(kNB, a.n - (int)m0);  // nodes of this batch; the others read zeros
+    if (!DH) {
+      for (int q = tid; q < kNB * n_k; q += kThreads) {
+        const int b = q / n_k, i = q % n_k;
+        AT v = 0;
+        if (b < nb) v = i < a.n_x ? (AT)sp[(m0 + b) * a.n_x + i] : (AT)wb[(m0 + b) * n_k + i];
+        xin[b * ldk + i] = v;
+      }
+      __syncthreads();
+      multi_t<MT, AT>(K, n_k, n_v, ld, xin, ldk, dv, ld, part);
+      for (int q = tid; q < nb * n_v; q += kThreads) {
+        const int b = q / n_v, j = q % n_v;
+        rp[(m0 + b) * n_v + j] = (VT)dv[b * ld + j];
+      }
+      __syncthreads();
+    } else {
+      for (int q = tid; q < kNB * n_v; q += kThreads) {
+        const int b = q / n_v, j = q % n_v;
+        xin[b * ld + j] = b < nb ? (AT)rp[(m0 + b) * n_v + j] : (AT)0;
+      }
+      __syncthreads();
+      multi_t<MT, AT>(Lm, n_v, n_v, ld, xin, ld, dv, ld, part);  // Lambda is symmetric
+      for (int q = tid; q < kNB * n_v; q += kThreads) {
+        const int b = q / n_v, j = q % n_v;
+        dv[b * ld + j] *= b < nb ? (AT)ps[m0 + b] : (AT)0;
+      }
+      __syncthreads();
+      // h_b[i] = [Bbar; L]_i . delta_b: thread i, all kNB nodes per row chunk
+      if (tid < n_k) {
+        AT acc[kNB];
+#pragma unroll
+        for (int b = 0; b < kNB; ++b) acc[b] = 0;
+        const MT* row = K + (long long)tid * ld;
+        for (int g = 0; g < ld / V; ++g) {
+          AT av[V];
+          ld16(row + g * V, av);
+#pragma unroll
+          for (int b = 0; b < kNB; ++b) {
+            AT dvv[V];
+            ldx(dv + b * ld + g * V, dvv);
+#pragma unroll
+            for (int k = 0; k < V; ++k) acc[b] += av[k] * dvv[k];
+          }
+        }
+        VT* h = reinterpret_cast<VT*>(a.h);
+        VT* ha = reinterpret_cast<VT*>(a.ha);
+#pragma unroll
+        for (int b = 0; b < kNB; ++b) {
+          if (b >= nb) continue;
+          const long long q = (m0 + b) * n_k + tid;
+          if (mode & MODE_ANCHOR) {
+            ha[q] = (VT)acc[b];
+            h[q] = (VT)0;
+          } else {
+            h[q] = (VT)acc[b];
+          }
+        }
+      }
+      __syncthreads();
+    }
+  }
+}
+
 int optin_smem() {
   int dev = 0, optin = 0;
   cudaGetDevice(&dev);
@@ -1656,18 +1842,38 @@ LaunchCfg config_t(const IterArgs& a, int num_sms, int S_max, int schedule) {
   c.s_dh = S;
   c.smem_dh = iter_smem_bytes<MT>(S > 0 ? S : 1, a.n_x, a.n_u, a.n_v, true);
   if (c.s_gt < 1 || c.s_dh < 1) c.stages = 0;
+  // shared pack: kNB nodes per pass when the pack and the staging fit
+  c.multi_gt = c.multi_dh = false;
+  if (a.pack_stride == 0) {
+    c.smem_mgt = multi_smem_bytes<MT>(a.n_x, a.n_u, a.n_v, false);
+    c.smem_mdh = multi_smem_bytes<MT>(a.n_x, a.n_u, a.n_v, true);
+    c.multi_gt = c.smem_mgt + 256 <= (size_t)optin;  // room for the kernel's static shared memory
+    c.multi_dh = c.smem_mdh + 256 <= (size_t)optin;
+    const int batches = (a.n + kNB - 1) / kNB;
+    c.grid_multi = batches < num_sms ? batches : num_sms;
+  }
   return c;
 }
 
 template <typename VT, typename MT>
 int launch_t(const IterArgs& a, const LaunchCfg& c, int nu, int mode, cudaStream_t s) {
-  // once per process and instantiation; thread-safe (solves may run on several threads)
+  // once per process and instantiation; thread-safe (solves may run on several threads).
+  // Each kernel may use the opt-in shared memory minus its static shared memory.
   static const bool attr_set = [] {
-    cudaFuncSetAttribute(apg_iter<VT, MT>, cudaFuncAttributeMaxDynamicSharedMemorySize, 232448);
-    cudaFuncSetAttribute(node_mv<VT, MT, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 232448);
-    cudaFuncSetAttribute(node_mv<VT, MT, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 232448);
-    cudaFuncSetAttribute(prox_node<VT, MT>, cudaFuncAttributeMaxDynamicSharedMemorySize, 232448);
-    cudaFuncSetAttribute(fwd_scan<VT, MT>, cudaFuncAttributeMaxDynamicSharedMemorySize, 232448);
+    const int optin = optin_smem();
+    auto allow = [optin](auto fn) {
+      cudaFuncAttributes at{};
+      if (cudaFuncGetAttributes(&at, fn) == cudaSuccess)
+        cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - (int)at.sharedSizeBytes);
+    };
+    allow(apg_iter<VT, MT>);
+    allow(node_mv<VT, MT, false>);
+    allow(node_mv<VT, MT, true>);
+    allow(prox_node<VT, MT>);
+    allow(fwd_scan<VT, MT>);
+    allow(node_mv_shared<VT, MT, false>);
+    allow(node_mv_shared<VT, MT, true>);
+    cudaGetLastError();  // a refused attribute surfaces at the launch, not here
     return true;
   }();
   (void)attr_set;
@@ -1690,11 +1896,17 @@ int launch_t(const IterArgs& a, const LaunchCfg& c, int nu, int mode, cudaStream
   if (mode & MODE_BWD) {
     scan_kernel<VT><<<c.grid_scan, c.block, 0, s>>>(a, 0, nu, mode);
     mark();
-    node_mv<VT, MT, false><<<c.grid_mv, c.block, c.smem_gt, s>>>(a, c.s_gt, nu, mode);
+    if (c.multi_gt)
+      node_mv_shared<VT, MT, false><<<c.grid_multi, c.block, c.smem_mgt, s>>>(a, nu, mode);
+    else
+      node_mv<VT, MT, false><<<c.grid_mv, c.block, c.smem_gt, s>>>(a, c.s_gt, nu, mode);
     mark();
     scan_kernel<VT><<<c.grid_scan, c.block, 0, s>>>(a, 1, nu, mode);
     mark();
-    node_mv<VT, MT, true><<<c.grid_mv, c.block, c.smem_dh, s>>>(a, c.s_dh, nu, mode);
+    if (c.multi_dh)
+      node_mv_shared<VT, MT, true><<<c.grid_multi, c.block, c.smem_mdh, s>>>(a, nu, mode);
+    else
+      node_mv<VT, MT, true><<<c.grid_mv, c.block, c.smem_dh, s>>>(a, c.s_dh, nu, mode);
     mark();
   }
   return check_launch("node-parallel iteration");

@@ -140,6 +140,9 @@ struct LaunchCfg {
   int grid_prox = 1, grid_scan = 1, grid_mv = 1, grid_fwd = 1;
   size_t smem_prox = 0, smem_gt = 0, smem_dh = 0;
   int s_gt = 0, s_dh = 0;   // pack slots of the two mat-vec launches (0: does not fit)
+  bool multi_gt = false, multi_dh = false;  // shared pack: several nodes per pass over it
+  size_t smem_mgt = 0, smem_mdh = 0;
+  int grid_multi = 1;
   // profiling: when set, an event is recorded before the first and after every kernel
   // of a launch_iter call (kernels_per_call + 1 events)
   cudaEvent_t* events = nullptr;
