@@ -12,6 +12,9 @@
  *   smaller index and sits one stage up; the parents of the nodes of one stage are
  *   non-decreasing, so the children of a node are contiguous; all leaves are at the
  *   last stage N-1, where N (the horizon) is one more than the deepest stage.
+ * - A forest batches R independent problems on one network into one solve: nodes
+ *   0..R-1 are the roots (parent -1), and each tree's leaves are at its own last stage
+ *   N_r - 1.  Per-tree step data is stacked tree after tree (smpc_step_data).
  * - Node n at stage j holds the input u_n = u_j, the demand d_n = d_j and the
  *   state x_n = x_{j+1} of its branch; its dual block is
  *   y_n = (vsigma_n, zeta_n, psi_n) of length 2 n_x + n_u (Sec. IV-A); this is the
@@ -118,12 +121,13 @@ typedef struct smpc_factor_opts {
 /* Per-solve data (Alg. 2, steps 1-2).  float64; each pointer may address host or
  * device memory (unified addressing decides the copy direction). */
 typedef struct smpc_step_data {
-  const double* p;      /* n_x measured state x_0 */
-  const double* q;      /* n_u previous input u_{-1} */
-  const double* dhat;   /* N * n_d nominal forecast of stage j (eq. demand:tree) */
+  const double* p;      /* R * n_x measured state x_0 of each tree */
+  const double* q;      /* R * n_u previous input u_{-1} of each tree */
+  const double* dhat;   /* (N_0 + ... + N_{R-1}) * n_d nominal forecast (eq. demand:tree):
+                           row N_0 + ... + N_{r-1} + j is stage j of tree r */
   const double* eps;    /* n_nodes * n_d forecast errors of the nodes, or NULL to
                            keep those uploaded by the previous solve (zero at first) */
-  const double* alpha2; /* N * n_u time-varying price of stage j */
+  const double* alpha2; /* (N_0 + ... + N_{R-1}) * n_u time-varying price, rows as dhat */
 } smpc_step_data;
 
 typedef struct smpc_solve_opts {
@@ -150,10 +154,10 @@ typedef struct smpc_result {
   void* u;              /* device, n_nodes * n_u of the vector type: last z^nu inputs */
   void* x;              /* device, n_nodes * n_x: last z^nu states */
   void* y;              /* device, n_nodes * (2 n_x + n_u): final dual y^{nu+1} */
-  double* u0_host;      /* host, n_u: the root input u_0 (the move applied, Alg. 2 step 4) */
+  double* u0_host;      /* host, R * n_u: each root's input u_0 (the move applied, Alg. 2 step 4) */
   double* history_host; /* host, max_iters * 3: per iteration (rho, ||Hz||_inf, ||t||_inf) */
   int32_t iterations;   /* out: iterations run */
-  double rho;           /* out: ||H z - t||_inf of the last iterate (Sec. IV-E) */
+  double rho;           /* out: ||H z - t||_inf of the last iterate (Sec. IV-E), over all trees */
   double rho_rel;       /* out: rho / (1 + max(||H z||_inf, ||t||_inf)) */
   int32_t launches;     /* out: kernel launches the solve enqueued (set on return) */
   double queue_ms;      /* out (smpc_poll only): submit to admission, host wall clock */
@@ -162,6 +166,7 @@ typedef struct smpc_result {
 
 typedef struct smpc_tree_info {
   int32_t n_nodes, horizon, n_leaves, n_chains, n_top, max_chain_len;
+  int32_t n_trees;  /* trees of a forest (1 for a single scenario tree) */
 } smpc_tree_info;
 
 /* Validate a scenario tree (Sec. III-C) and upload it.  prob[n] is p_n, the

@@ -59,7 +59,7 @@ class smpc_result(ctypes.Structure):
 
 class smpc_tree_info(ctypes.Structure):
     _fields_ = [("n_nodes", ctypes.c_int32), ("horizon", ctypes.c_int32), ("n_leaves", ctypes.c_int32),
-                ("n_chains", ctypes.c_int32), ("n_top", ctypes.c_int32), ("max_chain_len", ctypes.c_int32)]
+                ("n_chains", ctypes.c_int32), ("n_top", ctypes.c_int32), ("max_chain_len", ctypes.c_int32), ("n_trees", ctypes.c_int32)]
 
 
 # symbol -> (restype, argtypes); every entry point declared in include/smpc.h

@@ -77,7 +77,7 @@ bool finite_if_host(const double* p, size_t n) { return !host_readable(p) || fin
 
 void free_tree_dev(smpc::DevTree& d) {
   void* ptrs[] = {d.parent, d.stage, d.child_begin, d.child_count, d.chain_off, d.chain_node, d.chain_parent,
-                  d.top_nodes, d.top_expect, d.path_off, d.path_node, d.prob, d.pbar};
+                  d.top_nodes, d.top_expect, d.path_off, d.path_node, d.tree_of, d.row, d.prob, d.pbar};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   d = smpc::DevTree();
@@ -96,7 +96,10 @@ int build_tree(int32_t n, const int32_t* parent, const double* prob, smpc_tree& 
   t.n = n;
   t.parent.assign(parent, parent + n);
   t.stage.assign(n, 0);
-  for (int m = 1; m < n; ++m) {
+  // a forest: the first R nodes are roots (parent -1), one per tree
+  t.R = 1;
+  while (t.R < n && parent[t.R] == -1) ++t.R;
+  for (int m = t.R; m < n; ++m) {
     const int p = parent[m];
     if (p < 0 || p >= m) {
       set_error("parent[%d] = %d: parents must precede their children", m, p);
@@ -107,7 +110,7 @@ int build_tree(int32_t n, const int32_t* parent, const double* prob, smpc_tree& 
       set_error("node %d: nodes must be grouped by stage (breadth-first order)", m);
       return SMPC_EINVAL;
     }
-    if (t.stage[m] == t.stage[m - 1] && m > 1 && p < parent[m - 1]) {
+    if (t.stage[m] == t.stage[m - 1] && m > t.R && p < parent[m - 1]) {
       set_error("node %d: parents of one stage must be non-decreasing", m);
       return SMPC_EINVAL;
     }
@@ -115,16 +118,30 @@ int build_tree(int32_t n, const int32_t* parent, const double* prob, smpc_tree& 
   t.N = t.stage[n - 1] + 1;
   t.child_begin.assign(n, 0);
   t.child_count.assign(n, 0);
-  for (int m = n - 1; m >= 1; --m) {
+  for (int m = n - 1; m >= t.R; --m) {
     t.child_begin[parent[m]] = m;
     t.child_count[parent[m]]++;
   }
+  // tree of every node, each tree's horizon (its deepest stage + 1) and data rows:
+  // tree r's stage j reads row row_off[r] + j of the stage-indexed step data
+  t.tree_of.assign(n, 0);
+  std::vector<int> depth(t.R, 0);
+  for (int m = 0; m < n; ++m) {
+    t.tree_of[m] = m < t.R ? m : t.tree_of[parent[m]];
+    depth[t.tree_of[m]] = std::max(depth[t.tree_of[m]], t.stage[m] + 1);
+  }
+  t.row_off.assign(t.R + 1, 0);
+  for (int r = 0; r < t.R; ++r) t.row_off[r + 1] = t.row_off[r] + depth[r];
+  t.rows = t.row_off[t.R];
+  t.row.assign(n, 0);
+  for (int m = 0; m < n; ++m) t.row[m] = t.row_off[t.tree_of[m]] + t.stage[m];
   t.n_leaves = 0;
   for (int m = 0; m < n; ++m)
     if (t.child_count[m] == 0) {
       ++t.n_leaves;
-      if (t.stage[m] != t.N - 1) {
-        set_error("leaf %d is at stage %d; all leaves must be at the last stage %d", m, t.stage[m], t.N - 1);
+      const int last = depth[t.tree_of[m]] - 1;
+      if (t.stage[m] != last) {
+        set_error("leaf %d is at stage %d; all leaves of its tree must be at its last stage %d", m, t.stage[m], last);
         return SMPC_EINVAL;
       }
     }
@@ -134,9 +151,9 @@ int build_tree(int32_t n, const int32_t* parent, const double* prob, smpc_tree& 
     std::vector<double> leaves(n, 0.0);
     for (int m = n - 1; m >= 0; --m) {
       if (t.child_count[m] == 0) leaves[m] = 1.0;
-      if (m > 0) leaves[parent[m]] += leaves[m];
+      if (m >= t.R) leaves[parent[m]] += leaves[m];
     }
-    for (int m = 0; m < n; ++m) t.prob[m] = leaves[m] / leaves[0];
+    for (int m = 0; m < n; ++m) t.prob[m] = leaves[m] / leaves[t.tree_of[m]];
   } else {
     for (int m = 0; m < n; ++m) {
       if (!(std::isfinite(prob[m]) && prob[m] > 0)) {
@@ -145,12 +162,13 @@ int build_tree(int32_t n, const int32_t* parent, const double* prob, smpc_tree& 
       }
       t.prob[m] = prob[m];
     }
-    if (std::fabs(prob[0] - 1.0) > 1e-12) {
-      set_error("root probability %.17g != 1", prob[0]);
-      return SMPC_EINVAL;
-    }
+    for (int r = 0; r < t.R; ++r)
+      if (std::fabs(prob[r] - 1.0) > 1e-12) {
+        set_error("root probability %.17g != 1 (root %d)", prob[r], r);
+        return SMPC_EINVAL;
+      }
     std::vector<double> csum(n, 0.0);
-    for (int m = 1; m < n; ++m) csum[parent[m]] += prob[m];
+    for (int m = t.R; m < n; ++m) csum[parent[m]] += prob[m];
     for (int m = 0; m < n; ++m)
       if (t.child_count[m] > 0 && std::fabs(csum[m] - prob[m]) > 1e-12 * prob[m]) {
         set_error("children of node %d have probability %.17g != %.17g", m, csum[m], prob[m]);
@@ -158,7 +176,7 @@ int build_tree(int32_t n, const int32_t* parent, const double* prob, smpc_tree& 
       }
   }
   t.pbar = t.prob;
-  for (int m = 1; m < n; ++m) t.pbar[parent[m]] += t.prob[m];
+  for (int m = t.R; m < n; ++m) t.pbar[parent[m]] += t.prob[m];
   // chains (subtrees that are paths) and top nodes
   std::vector<char> path_sub(n, 0);
   for (int m = n - 1; m >= 0; --m)
@@ -167,7 +185,7 @@ int build_tree(int32_t n, const int32_t* parent, const double* prob, smpc_tree& 
   std::vector<std::vector<int>> chains;
   for (int m = 0; m < n; ++m) {
     t.is_top[m] = !path_sub[m];
-    if (path_sub[m] && (m == 0 || !path_sub[parent[m]])) {
+    if (path_sub[m] && (parent[m] < 0 || !path_sub[parent[m]])) {
       std::vector<int> c;
       for (int k = m;; k = t.child_begin[k]) {
         c.push_back(k);
@@ -220,6 +238,8 @@ int upload_tree(smpc_tree& t) {
   TRY(dev_upload(&d.top_expect, t.top_expect.data(), t.n));
   TRY(dev_upload(&d.path_off, t.path_off.data(), t.n + 1));
   if (!t.path_node.empty()) TRY(dev_upload(&d.path_node, t.path_node.data(), t.path_node.size()));
+  TRY(dev_upload(&d.tree_of, t.tree_of.data(), t.n));
+  TRY(dev_upload(&d.row, t.row.data(), t.n));
   TRY(dev_upload(&d.prob, t.prob.data(), t.n));
   TRY(dev_upload(&d.pbar, t.pbar.data(), t.n));
   return SMPC_OK;
@@ -252,6 +272,7 @@ IterArgs make_args(const smpc_factor_t* f) {
   a.top_expect = t->dev.top_expect;
   a.path_off = t->dev.path_off;
   a.path_node = t->dev.path_node;
+  a.tree_of = t->dev.tree_of;
   a.packs = f->packs;
   a.pscale = f->pscale;
   a.pack_stride = f->pack_stride;
@@ -540,7 +561,7 @@ int copy_final_y(smpc_factor_t* f, void* dst) {
   return SMPC_OK;
 }
 
-int launch_planned(const IterPlan& plan, int nu, int mode, void* stream) {
+int launch_planned(IterPlan& plan, int nu, int mode, void* stream) {
   int prec = plan.prec;
   const IterArgs* a = &plan.args;
   LaunchCfg cfg = plan.cfg;
@@ -560,6 +581,7 @@ int launch_planned(const IterPlan& plan, int nu, int mode, void* stream) {
   const bool prof = pf && !anchor && (mode & MODE_BWD) && (mode & MODE_PROX) && nu >= 1 && pf->count < pf->capacity;
   if (prof) cfg.events = pf->ev.data() + (size_t)pf->count * Profile::kStageEvents;
   TRY(launch_iter(prec, *a, cfg, nu, mode, stream));
+  plan.kernels += kernels_per_call(cfg, mode);
   if (prof) {
     pf->stages = kernels_per_call(cfg, mode);
     ++pf->count;
@@ -615,6 +637,7 @@ int smpc_tree_info_get(const smpc_tree* t, smpc_tree_info* info) {
   }
   info->n_nodes = t->n;
   info->horizon = t->N;
+  info->n_trees = t->R;
   info->n_leaves = t->n_leaves;
   info->n_chains = (int)t->chain_parent.size();
   info->n_top = (int)t->top_nodes.size();
@@ -699,7 +722,8 @@ int smpc_factor(const smpc_tree* tree, const smpc_network* net, const smpc_cost*
   f->tree = tree;
   f->prec = o.precision;
   f->n = tree->n;
-  f->N = tree->N;
+  f->N = tree->rows;  // stage-indexed data rows: the sum of the trees' horizons
+  f->R = tree->R;
   f->n_x = n_x;
   f->n_u = n_u;
   f->n_d = n_d;
@@ -767,7 +791,7 @@ int smpc_factor(const smpc_tree* tree, const smpc_network* net, const smpc_cost*
   const size_t cnts[] = {(size_t)n * nd, (size_t)n * nd, (size_t)n * n_k, (size_t)n * n_k, (size_t)n * n_u,
                          (size_t)n * n_x, (size_t)n * n_v, (size_t)n * n_x, (size_t)n * n_v, (size_t)n * n_u,
                          (size_t)n * n_x, (size_t)n, (size_t)n, (size_t)n * n_u, (size_t)n, (size_t)n_x,
-                         (size_t)n_x, (size_t)n_x, (size_t)n_u, (size_t)n_u, (size_t)n_x, (size_t)n,
+                         (size_t)n_x, (size_t)n_x, (size_t)n_u, (size_t)n_u, (size_t)tree->R * n_x, (size_t)n,
                          (size_t)n, (size_t)n * n_u};
   static_assert(sizeof(vecs) / sizeof(vecs[0]) == sizeof(cnts) / sizeof(cnts[0]), "one count per vector");
   for (size_t i = 0; i < sizeof(cnts) / sizeof(cnts[0]); ++i) {
@@ -779,7 +803,7 @@ int smpc_factor(const smpc_tree* tree, const smpc_network* net, const smpc_cost*
     }
   }
   if ((rc = f->alloc(&f->uhat64, sizeof(double) * (size_t)n * n_u)) || (rc = f->alloc(&f->abar, sizeof(double) * (size_t)f->N * n_v)) ||
-      (rc = f->alloc(&f->d_p, sizeof(double) * n_x)) || (rc = f->alloc(&f->d_q, sizeof(double) * n_u)) ||
+      (rc = f->alloc(&f->d_p, sizeof(double) * tree->R * n_x)) || (rc = f->alloc(&f->d_q, sizeof(double) * tree->R * n_u)) ||
       (rc = f->alloc(&f->d_dhat, sizeof(double) * (size_t)f->N * std::max(n_d, 1))) ||
       (rc = f->alloc(&f->d_eps, sizeof(double) * (size_t)n * std::max(n_d, 1))) ||
       (rc = f->alloc(&f->d_alpha2, sizeof(double) * (size_t)f->N * n_u)) || (rc = f->alloc(&f->counters, sizeof(int) * n)) ||
@@ -950,7 +974,8 @@ int smpc_solve(smpc_factor_t* f, const smpc_step_data* data, const smpc_solve_op
     return SMPC_EINVAL;
   }
   const int n = f->n, N = f->N, n_x = f->n_x, n_u = f->n_u, n_d = f->n_d;
-  if (!finite_if_host(data->p, n_x) || !finite_if_host(data->q, n_u) || !finite_if_host(data->alpha2, (size_t)N * n_u) ||
+  if (!finite_if_host(data->p, (size_t)f->R * n_x) || !finite_if_host(data->q, (size_t)f->R * n_u) ||
+      !finite_if_host(data->alpha2, (size_t)N * n_u) ||
       (n_d && !finite_if_host(data->dhat, (size_t)N * n_d)) ||
       (data->eps && n_d && !finite_if_host(data->eps, (size_t)n * n_d))) {
     set_error("step data contains non-finite values");
@@ -961,13 +986,13 @@ int smpc_solve(smpc_factor_t* f, const smpc_step_data* data, const smpc_solve_op
   TRY(ensure_capacity(f, iters + 1));
   TRY(upload_cvec(f, iters + 1));
   // step data -> device (Alg. 2 steps 1-2)
-  CK(cudaMemcpyAsync(f->d_p, data->p, sizeof(double) * n_x, cudaMemcpyDefault, s));
-  CK(cudaMemcpyAsync(f->d_q, data->q, sizeof(double) * n_u, cudaMemcpyDefault, s));
+  CK(cudaMemcpyAsync(f->d_p, data->p, sizeof(double) * f->R * n_x, cudaMemcpyDefault, s));
+  CK(cudaMemcpyAsync(f->d_q, data->q, sizeof(double) * f->R * n_u, cudaMemcpyDefault, s));
   if (n_d) CK(cudaMemcpyAsync(f->d_dhat, data->dhat, sizeof(double) * (size_t)N * n_d, cudaMemcpyDefault, s));
   if (data->eps && n_d)
     CK(cudaMemcpyAsync(f->d_eps, data->eps, sizeof(double) * (size_t)n * n_d, cudaMemcpyDefault, s));
   CK(cudaMemcpyAsync(f->d_alpha2, data->alpha2, sizeof(double) * (size_t)N * n_u, cudaMemcpyDefault, s));
-  TRY(launch_convert(f->prec, f->d_p, f->p0, n_x, s));
+  TRY(launch_convert(f->prec, f->d_p, f->p0, (long long)f->R * n_x, s));
   CostArgs c;
   c.n = n;
   c.N = N;
@@ -976,7 +1001,8 @@ int smpc_solve(smpc_factor_t* f, const smpc_step_data* data, const smpc_solve_op
   c.n_d = n_d;
   c.n_v = f->n_v;
   c.parent = f->tree->dev.parent;
-  c.stage = f->tree->dev.stage;
+  c.stage = f->tree->dev.row;
+  c.tree_of = f->tree->dev.tree_of;
   c.child_begin = f->tree->dev.child_begin;
   c.child_count = f->tree->dev.child_count;
   c.prob = f->tree->dev.prob;
@@ -1033,7 +1059,7 @@ int smpc_solve(smpc_factor_t* f, const smpc_step_data* data, const smpc_solve_op
   if (res->x) CK(cudaMemcpyAsync(res->x, f->xout, (size_t)n * n_x * f->vs, cudaMemcpyDefault, s));
   f->solved_once = true;
   f->last_stream = s;
-  f->last_launches = 6 + launched + 1;  // convert, 3 cost update, init, iterations, tail, final
+  f->last_launches = 6 + plan.kernels + 1;  // convert, 3 cost update, init, iterations and tail, final y
   res->launches = f->last_launches;
   res->iterations = -1;
   if (!opts->sync) return SMPC_OK;
@@ -1117,7 +1143,7 @@ int smpc_solve_info(smpc_factor_t* f, smpc_result* res) {
     CK(cudaMemcpy(hist.data(), f->res, sizeof(unsigned long long) * hist.size(), cudaMemcpyDeviceToHost));
     std::memcpy(res->history_host, hist.data(), sizeof(double) * hist.size());
   }
-  if (res->u0_host) TRY(get_vec(f, res->u0_host, f->uout, n_u));
+  if (res->u0_host) TRY(get_vec(f, res->u0_host, f->uout, (size_t)f->R * n_u));  // the roots are nodes 0..R-1
   if (fl[1] != 0) {
     set_error("solve failed on the device: %s", smpc_status_string(fl[1]));
     return fl[1];

@@ -612,10 +612,11 @@ struct Kern {
       }
     }
   }
-  __device__ void path_init(int par, int e, AT& V, AT& X, AT& U) const {
+  // path sums down to top node par (inclusive) of tree `tree`, starting from its state p
+  __device__ void path_init(int par, int tree, int e, AT& V, AT& X, AT& U) const {
     V = 0;
     U = 0;
-    X = (e < a.n_x && !linear()) ? (AT)cv(a.p0)[e] : (AT)0;
+    X = (e < a.n_x && !linear()) ? (AT)cv(a.p0)[(long long)tree * a.n_x + e] : (AT)0;
     if (par < 0) return;
     path_add(a.path_node + a.path_off[par], a.path_off[par + 1] - a.path_off[par], e, V, X, U);
   }
@@ -648,7 +649,7 @@ struct Kern {
     VT* __restrict__ Xo = mv(a.xout);
     VT* __restrict__ Uo = mv(a.uout);
     AT V = 0, X = 0, U = 0;
-    if (e < a.n_k) path_init(par, e, V, X, U);
+    if (e < a.n_k) path_init(par, a.tree_of[nodes[0]], e, V, X, U);
     const AT xs = tank ? (AT)cv(a.x_s)[e] : (AT)0;
     const AT xlo = tank ? (AT)cv(a.x_min)[e] : (AT)0;
     const AT xhi = tank ? (AT)cv(a.x_max)[e] : (AT)0;
@@ -875,12 +876,12 @@ struct Kern {
     AT V = 0, X = 0, U = 0;
     if (b < a.n_top) {
       const int t = a.top_nodes[b];
-      path_init(t, e, V, X, U);
+      path_init(t, a.tree_of[t], e, V, X, U);
       store_xu(t, e, X, U);
       return;
     }
     const int c = b - a.n_top;
-    path_init(a.chain_parent[c], e, V, X, U);
+    path_init(a.chain_parent[c], a.tree_of[a.chain_node[a.chain_off[c]]], e, V, X, U);
     const int cb = a.chain_off[c], len = a.chain_off[c + 1] - cb;
     const bool tank = e < a.n_x, lin = linear();
     constexpr int B = 16;
@@ -1552,7 +1553,7 @@ __global__ void cost_beta_kernel(CostArgs a) {
     const int cb = a.child_begin[m], cc = a.child_count[m];
     for (int i = threadIdx.x; i < a.n_u; i += blockDim.x) {
       double D = a.pbar[m] * a.uhat64[(long long)m * a.n_u + i];
-      D -= pm * (par >= 0 ? a.uhat64[(long long)par * a.n_u + i] : a.q[i]);
+      D -= pm * (par >= 0 ? a.uhat64[(long long)par * a.n_u + i] : a.q[(long long)a.tree_of[m] * a.n_u + i]);
       for (int c = cb; c < cb + cc; ++c) D -= a.prob[c] * a.uhat64[(long long)c * a.n_u + i];
       Dsh[i] = D;
     }

@@ -136,7 +136,8 @@ extern "C" int smpc_solve_static(smpc_factor_t* f, const smpc_step_data* data, c
               L.total, kStaticScratchBytes);
     return SMPC_EINVAL;
   }
-  if (!finite_host(data->p, n_x) || !finite_host(data->q, n_u) || !finite_host(data->alpha2, (size_t)N * n_u) ||
+  if (!finite_host(data->p, (size_t)f->R * n_x) || !finite_host(data->q, (size_t)f->R * n_u) ||
+      !finite_host(data->alpha2, (size_t)N * n_u) ||
       (n_d && !finite_host(data->dhat, (size_t)N * n_d)) || (data->eps && n_d && !finite_host(data->eps, (size_t)n * n_d))) {
     set_error("step data contains non-finite values");
     return SMPC_EINVAL;
@@ -179,13 +180,13 @@ extern "C" int smpc_solve_static(smpc_factor_t* f, const smpc_step_data* data, c
     SCK(cudaGetLastError());
   }
   // step data -> the factor's device buffers (no allocation)
-  SCK(cudaMemcpyAsync(f->d_p, data->p, sizeof(double) * n_x, cudaMemcpyDefault, s));
-  SCK(cudaMemcpyAsync(f->d_q, data->q, sizeof(double) * n_u, cudaMemcpyDefault, s));
+  SCK(cudaMemcpyAsync(f->d_p, data->p, sizeof(double) * f->R * n_x, cudaMemcpyDefault, s));
+  SCK(cudaMemcpyAsync(f->d_q, data->q, sizeof(double) * f->R * n_u, cudaMemcpyDefault, s));
   if (n_d) SCK(cudaMemcpyAsync(f->d_dhat, data->dhat, sizeof(double) * (size_t)N * n_d, cudaMemcpyDefault, s));
   if (data->eps && n_d)
     SCK(cudaMemcpyAsync(f->d_eps, data->eps, sizeof(double) * (size_t)n * n_d, cudaMemcpyDefault, s));
   SCK(cudaMemcpyAsync(f->d_alpha2, data->alpha2, sizeof(double) * (size_t)N * n_u, cudaMemcpyDefault, s));
-  STRY(launch_convert(f->prec, f->d_p, f->p0, n_x, s));
+  STRY(launch_convert(f->prec, f->d_p, f->p0, (long long)f->R * n_x, s));
   CostArgs c;
   std::memset(&c, 0, sizeof c);
   c.n = n;
@@ -195,7 +196,8 @@ extern "C" int smpc_solve_static(smpc_factor_t* f, const smpc_step_data* data, c
   c.n_d = n_d;
   c.n_v = f->n_v;
   c.parent = f->tree->dev.parent;
-  c.stage = f->tree->dev.stage;
+  c.stage = f->tree->dev.row;
+  c.tree_of = f->tree->dev.tree_of;
   c.child_begin = f->tree->dev.child_begin;
   c.child_count = f->tree->dev.child_count;
   c.prob = f->tree->dev.prob;
@@ -238,6 +240,7 @@ extern "C" int smpc_solve_static(smpc_factor_t* f, const smpc_step_data* data, c
   a.top_expect = t->dev.top_expect;
   a.path_off = t->dev.path_off;
   a.path_node = t->dev.path_node;
+  a.tree_of = t->dev.tree_of;
   a.pscale = f->pscale;
   a.packs = f->packs;
   a.pack_stride = f->pack_stride;
@@ -306,7 +309,7 @@ extern "C" int smpc_solve_static(smpc_factor_t* f, const smpc_step_data* data, c
   if (res->x) SCK(cudaMemcpyAsync(res->x, f->xout, (size_t)n * n_x * f->vs, cudaMemcpyDefault, s));
   f->solved_once = true;
   f->last_stream = s;
-  f->last_launches = 6 + launched + 1 + (need_theta ? 1 : 0);
+  f->last_launches = 6 + plan.kernels + 1 + (need_theta ? 1 : 0);
   res->launches = f->last_launches;
   res->iterations = -1;
   if (!opts->sync) return SMPC_OK;
@@ -325,13 +328,17 @@ extern "C" int smpc_solve_static(smpc_factor_t* f, const smpc_step_data* data, c
     if (res->history_host)  // the residual history is stored as float64 bit patterns
       SCK(cudaMemcpy(res->history_host, resv, sizeof(double) * 3 * (size_t)fl[0], cudaMemcpyDeviceToHost));
   }
-  if (res->u0_host) {
-    if (f->prec == SMPC_FP64) {
-      SCK(cudaMemcpy(res->u0_host, f->uout, sizeof(double) * n_u, cudaMemcpyDeviceToHost));
-    } else {
-      float u0[256];  // n_u <= 256 is required by the iteration kernel
-      SCK(cudaMemcpy(u0, f->uout, sizeof(float) * n_u, cudaMemcpyDeviceToHost));
-      for (int i = 0; i < n_u; ++i) res->u0_host[i] = u0[i];
+  if (res->u0_host) {  // the roots' inputs (nodes 0..R-1), one tree at a time
+    for (int r = 0; r < f->R; ++r) {
+      if (f->prec == SMPC_FP64) {
+        SCK(cudaMemcpy(res->u0_host + (size_t)r * n_u, static_cast<const double*>(f->uout) + (size_t)r * n_u,
+                       sizeof(double) * n_u, cudaMemcpyDeviceToHost));
+      } else {
+        float u0[256];  // n_u <= 256 is required by the iteration kernel
+        SCK(cudaMemcpy(u0, static_cast<const float*>(f->uout) + (size_t)r * n_u, sizeof(float) * n_u,
+                       cudaMemcpyDeviceToHost));
+        for (int i = 0; i < n_u; ++i) res->u0_host[(size_t)r * n_u + i] = u0[i];
+      }
     }
   }
   if (fl[1] != 0) {

@@ -129,7 +129,7 @@ void smpc_server::worker(int slot) {
     d.dhat = stage(2, r->dhat);
     d.eps = r->has_eps ? stage(3, r->eps) : nullptr;
     d.alpha2 = stage(4, r->alpha2);
-    r->u0.assign(r->f->n_u, 0.0);
+    r->u0.assign((size_t)r->f->R * r->f->n_u, 0.0);
     r->history.assign((size_t)r->opts.max_iters * 3, 0.0);
     smpc_result res{};
     res.u0_host = r->u0.data();
@@ -231,7 +231,7 @@ int smpc_submit(smpc_server* sv, smpc_factor_t* f, const smpc_step_data* data, c
   r->f = f;
   r->opts = *opts;
   int rc = SMPC_OK;
-  if ((rc = copy_in(r->p, data->p, f->n_x)) || (rc = copy_in(r->q, data->q, f->n_u)) ||
+  if ((rc = copy_in(r->p, data->p, (size_t)f->R * f->n_x)) || (rc = copy_in(r->q, data->q, (size_t)f->R * f->n_u)) ||
       (rc = copy_in(r->alpha2, data->alpha2, (size_t)f->N * f->n_u)) ||
       (f->n_d && (rc = copy_in(r->dhat, data->dhat, (size_t)f->N * f->n_d))) ||
       (data->eps && f->n_d && (rc = copy_in(r->eps, data->eps, (size_t)f->n * f->n_d)))) {

@@ -46,6 +46,8 @@ struct DevTree {
   int* top_expect = nullptr;    // per node: arrivals a top node waits for (children + 1)
   int* path_off = nullptr;      // per node (n + 1): path of a top node, root .. node
   int* path_node = nullptr;
+  int* tree_of = nullptr;       // per node: its tree (the index of its root)
+  int* row = nullptr;           // per node: its row of the stage-indexed step data
   double* prob = nullptr;
   double* pbar = nullptr;       // p_n + sum of children's p (App. A)
 };
@@ -54,6 +56,9 @@ struct DevTree {
 
 struct smpc_tree {
   int n = 0, N = 0, n_leaves = 0, max_chain_len = 0, device = 0;
+  int R = 1;     // trees (roots are nodes 0 .. R-1)
+  int rows = 0;  // rows of stage-indexed step data: the sum of the trees' horizons
+  std::vector<int> tree_of, row, row_off;
   std::vector<int> parent, stage, child_begin, child_count;
   std::vector<double> prob, pbar;
   std::vector<int> chain_off, chain_node, chain_parent;
@@ -78,6 +83,7 @@ struct IterArgs {
   const int* top_expect;
   const int* path_off;
   const int* path_node;
+  const int* tree_of;            // per node: its tree (p0 has one state per tree)
   const void* packs;             // per node: [Bbar; L] (n_k x n_v) then Lambda/(2 p_n) (n_v x n_v)
   long long pack_stride;         // entries between consecutive nodes' packs (0: one shared pack)
   const void* pscale;            // shared pack: per node 1 / (2 p_n), applied to Lambda r; else NULL
@@ -159,9 +165,10 @@ int launch_iter(int prec, const IterArgs& a, const LaunchCfg& cfg, int nu, int m
 int launch_pack(int prec, int n, int n_k, int n_v, const double* K, const double* Lam, const double* prob,
                 void* packs, long long pack_stride, void* stream);
 struct CostArgs {
-  int n, N, n_x, n_u, n_d, n_v;
+  int n, N, n_x, n_u, n_d, n_v;  // N: rows of stage-indexed data (sum of the trees' horizons)
   const int* parent;
-  const int* stage;
+  const int* stage;              // per node: its row of the stage-indexed data
+  const int* tree_of;            // per node: its tree (q has one previous input per tree)
   const int* child_begin;
   const int* child_count;
   const double* prob;
@@ -208,6 +215,7 @@ struct IterPlan {
   int polish_from = 0x7fffffff;
   int anchor_every = 0;  // > 0: anchored solve (SMPC_BF16)
   Profile* profile = nullptr;
+  int kernels = 0;  // kernels enqueued through launch_planned
 };
 constexpr size_t kStateSize = 8;  // bytes per dual-state entry (float64, or two float32)
 size_t mat_size(int prec);
@@ -218,7 +226,7 @@ namespace smpc {
 // Validates polish_iters and the kernel configuration; SMPC_ENOTSUP when the network
 // does not fit the shared-memory pipeline.
 int plan_iters(const smpc_factor_t* f, const IterArgs& a, const smpc_solve_opts& opts, IterPlan* plan);
-int launch_planned(const IterPlan& plan, int nu, int mode, void* stream);
+int launch_planned(IterPlan& plan, int nu, int mode, void* stream);
 // Copies the final dual of the factor's last solve (vector type) to dst; synchronous.
 int copy_final_y(smpc_factor_t* f, void* dst);
 }  // namespace smpc
@@ -228,6 +236,7 @@ struct smpc_factor_t {
   const smpc_tree* tree = nullptr;
   int prec = SMPC_FP64;
   int n = 0, N = 0, n_x = 0, n_u = 0, n_d = 0, n_e = 0, n_v = 0, n_k = 0, nd = 0;
+  int R = 1;  // trees of the (forest) tree; N is the number of stage-indexed data rows
   size_t vs = 8, ms = 8;
   long long pack_stride = 0;
   double lambda = 0;

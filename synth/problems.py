@@ -155,3 +155,59 @@ def batch_instances(seed=0, count=64):
         P["network"] = k
         out.append(P)
     return out
+
+
+def forest_members(seed, count, n_x=3, n_u=5, n_d=3, n_e=1, max_horizon=6, max_children=3):
+    """`count` problems on one network and one cost: uneven random trees (horizons
+    3..max_horizon) with their own states, forecasts, prices and deviations."""
+    base = custom(seed, n_x, n_u, n_d, n_e, random_tree(np.random.default_rng(seed), 3, max_children))
+    rng = np.random.default_rng(20000 + seed)
+    out = []
+    for i in range(count):
+        N = int(rng.integers(3, max_horizon + 1))
+        tree = random_tree(np.random.default_rng(30000 + 31 * seed + i), N, max_children=max_children)
+        r = np.random.default_rng(40000 + 31 * seed + i)
+        P = assemble(base["net"], tree, r, W_alpha=base["cost"]["W_alpha"], W_u=base["cost"]["W_u"],
+                     W_x=base["cost"]["W_x"], gamma_d=base["cost"]["gamma_d"], alpha1=base["cost"]["alpha1"],
+                     pump_coef=base["alpha2"][0] / day_night_price(3)[0], t0=int(r.integers(0, 24)),
+                     p=r.uniform(2.0, 8.0, size=n_x), name=f"member{i}")
+        P["cost"] = base["cost"]
+        out.append(P)
+    return out
+
+
+def forest(problems):
+    """Stacks problems on one network into one forest problem: nodes in breadth-first
+    order over all trees (stage 0 holds the roots, tree after tree), per-tree step data
+    stacked tree after tree.  members[r][k] is the forest index of node k of tree r."""
+    R = len(problems)
+    trees = [P["tree"] for P in problems]
+    stages = [np.asarray(t["stage"]) for t in trees]
+    H = max(int(s.max()) + 1 for s in stages)
+    members = [np.zeros(len(t["parent"]), dtype=np.int64) for t in trees]
+    order = []
+    for j in range(H):
+        for r in range(R):
+            for k in np.nonzero(stages[r] == j)[0]:
+                members[r][k] = len(order)
+                order.append((r, int(k)))
+    n = len(order)
+    parent = np.full(n, -1, dtype=np.int32)
+    prob = np.zeros(n)
+    stage = np.zeros(n, dtype=np.int64)
+    for m, (r, k) in enumerate(order):
+        pk = trees[r]["parent"][k]
+        parent[m] = -1 if pk < 0 else members[r][pk]
+        prob[m] = trees[r]["prob"][k]
+        stage[m] = stages[r][k]
+    n_d = problems[0]["net"]["n_d"]
+    eps = np.zeros((n, n_d))
+    for r, P in enumerate(problems):
+        eps[members[r]] = P["eps"]
+    out = {"name": "forest", "net": problems[0]["net"], "cost": problems[0]["cost"],
+           "tree": {"parent": parent, "prob": prob, "stage": stage, "horizon": H},
+           "p": np.concatenate([P["p"] for P in problems]), "q": np.concatenate([P["q"] for P in problems]),
+           "dhat": np.concatenate([P["dhat"] for P in problems]),
+           "alpha2": np.concatenate([P["alpha2"] for P in problems]), "eps": eps,
+           "members": members}
+    return out

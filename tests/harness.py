@@ -99,7 +99,7 @@ class Gpu:
     def solve(self, iters, tol=0.0, warm=0, eps=True, check_every=0):
         P = self.P
         hist = np.zeros((iters, 3))
-        u0 = np.zeros(self.n_u)
+        u0 = np.zeros(self.smpc.smpc_tree_info_get(self.tree)["n_trees"] * self.n_u)
         info = self.smpc.smpc_solve(self.fac, P["p"], P["q"], P["dhat"], P["alpha2"], eps=P["eps"] if eps else None,
                                     max_iters=iters, tol=tol, warm_start=warm, check_every=check_every, sync=1,
                                     u=self.u, x=self.x, y=self.y, u0_host=u0, history_host=hist)

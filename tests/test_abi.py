@@ -56,6 +56,9 @@ def test_status_strings(lib):
     ([-1, 0, 0], [1.0, 0.5, -0.5], "positive"),
     ([-1, 0, 0], [0.9, 0.45, 0.45], "root"),
     ([], None, "n_nodes"),
+    ([-1, -1, 0, 1, -1], None, "precede"),              # forest: a root after the first non-root
+    ([-1, -1, 0, 0, 1, 2], None, "last stage"),         # forest: tree 0 has leaves at stages 1 and 2
+    ([-1, -1, 0, 1], [1.0, 0.5, 1.0, 1.0], "root"),     # forest: every root has probability 1
 ])
 def test_tree_validation(lib, parent, prob, msg):
     with pytest.raises(smpc.SmpcError) as ei:
