@@ -112,6 +112,24 @@ def algorithmic_bytes_per_iteration(n, n_x, n_u, n_v, prec):
     return n * (mat * ms + (vec_r + vec_w) * vs + state), n * mat, n * 2 * (n_k * n_v + n_v * n_v + n_k * n_v)
 
 
+STAGES = {1: ["apg_iter"], 2: ["fwd_scan", "prox_node", "scan_s", "node_mv_gt", "scan_r", "node_mv_dh"]}
+
+
+def stage_bytes(stage, n, n_x, n_u, n_v, prec, shared):
+    """Algorithmic bytes of one launch of a node-parallel kernel: the matrix entries it
+    applies (per node, unless the pack is shared) and its node vectors.  [Bbar; L]' y
+    reads [Bbar; L] (n_k x n_v); Lambda r and [Bbar; L] delta read Lambda and [Bbar; L]:
+    together the 43,747 entries per node of one iteration (n_x = 63, n_u = 114)."""
+    ms = {0: 8, 1: 4, 2: 2}[prec]
+    vs = 8 if prec == 0 else 4
+    n_k = n_x + n_u
+    if stage == "node_mv_gt":
+        return n * ((0 if shared else n_k * n_v * ms) + (n_k + n_v) * vs)
+    if stage == "node_mv_dh":
+        return n * ((0 if shared else (n_k * n_v + n_v * n_v) * ms) + (n_v + n_k) * vs)
+    return None
+
+
 # --------------------------------------------------------------------- CPU oracle leg
 def oracle_sample(config, iters):
     """Times the FP64 oracle (as it stands) for `iters` APG iterations; JSON to stdout."""
@@ -228,7 +246,7 @@ def aggregate(local_units, local_seconds, backend_device=None):
 
 # --------------------------------------------------------------------- our arm
 class Solver:
-    def __init__(self, P, precision, device, schedule=0):
+    def __init__(self, P, precision, device, schedule=0, shared_packs=0):
         import torch
 
         import paper_1604_01074_gb300 as smpc
@@ -237,7 +255,8 @@ class Solver:
         self.n, self.n_x, self.n_u = len(t["parent"]), net["n_x"], net["n_u"]
         self.tree = smpc.smpc_tree_create(t["parent"], t["prob"])
         self.info = smpc.smpc_tree_info_get(self.tree)
-        self.fac = smpc.smpc_factor(self.tree, net, P["cost"], precision=precision, precondition=1, schedule=schedule)
+        self.fac = smpc.smpc_factor(self.tree, net, P["cost"], precision=precision, precondition=1, schedule=schedule,
+                                    shared_packs=shared_packs)
         self.schedule, self.tuned_ms = smpc.smpc_factor_schedule(self.fac)
         dt = torch.float64 if precision == 0 else torch.float32
         self.u = torch.empty((self.n, self.n_u), dtype=dt, device=device)
@@ -350,22 +369,37 @@ def run_ours(args, rank, world, local_rank):
     ms_per_step = 1000.0 * local_s / args.steps
     clocks = clk.summary()
 
-    # kernel roofline: one iteration launch, differential timing
+    # kernel roofline: per-kernel device times from CUDA events between the launches of a
+    # live profiling solve of this factor (smpc_profile_solve), right after the timed region
     t_iter_ms = time_per_iteration(S, dev_in[0], stream, *((20, 60) if prec == 0 else (100, 400)))
-    log("ms per iteration launch", t_iter_ms)
+    log("ms per iteration", t_iter_ms)
     n_v = S.n_u - np.linalg.matrix_rank(P["net"]["E"])
     nbytes, mat_entries, flops = algorithmic_bytes_per_iteration(S.n, S.n_x, S.n_u, n_v, prec)
+    inp0 = inputs[0]
+    stage_ms = S.smpc.smpc_profile_solve(S.fac, inp0["p"], inp0["q"], inp0["dhat"], inp0["alpha2"], eps=P["eps"],
+                                         iters=200)
+    names = STAGES[S.schedule]
+    log("stage us", dict(zip(names, [1000 * t for t in stage_ms])))
     hbm, src = peaks()
-    if prec == 0:
-        achieved = flops / (t_iter_ms * 1e-3) / 1e12
+    if S.schedule == 1:
+        kern, k_ms, k_bytes = "apg_iter", stage_ms[0], nbytes
+    else:
+        k = int(np.argmax(stage_ms))
+        kern, k_ms = names[k], stage_ms[k]
+        k_bytes = stage_bytes(kern, S.n, S.n_x, S.n_u, n_v, prec, False)
+    if prec == 0 and S.schedule == 1:
+        achieved = flops / (k_ms * 1e-3) / 1e12
         roof = {"bound": "alu", "achieved": achieved, "peak": FP64_FMA_TFLOPS, "unit": "TFLOP/s",
                 "frac": achieved / FP64_FMA_TFLOPS, "traffic": recorded_traffic("fp64"),
                 "peak_source": "measured FP64 FMA microbenchmark on this pool's GB300"}
     else:
-        achieved = nbytes / (t_iter_ms * 1e-3) / 1e9
+        achieved = (k_bytes or 0) / (k_ms * 1e-3) / 1e9
         roof = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
-                "traffic": recorded_traffic(args.precision), "peak_source": f"{src} hbm_gbs"}
-    roof.update({"kernel": "apg_iter", "us_per_launch": 1000.0 * t_iter_ms, "bytes_per_launch": nbytes})
+                "traffic": recorded_traffic(f"{args.precision}_{kern}"), "peak_source": f"{src} hbm_gbs"}
+    roof.update({"kernel": kern, "us_per_launch": 1000.0 * k_ms, "bytes_per_launch": k_bytes,
+                 "timing": "CUDA events between the launches of a 200-iteration profiling solve",
+                 "stage_us": {n_: 1000.0 * t for n_, t in zip(names, stage_ms)},
+                 "us_per_iteration": 1000.0 * t_iter_ms})
 
     # end-to-end: host (pinned) inputs, device->host read of u_0 and the residual, wall clock
     pin_in = [S.pinned_inputs(i) for i in inputs]
@@ -389,6 +423,8 @@ def run_ours(args, rank, world, local_rank):
         "vs_baseline": None, "dtype": PREC_NAMES[prec], "data": "synthetic",
         "config": {"workload": WORKLOAD if args.config == "barcelona" else args.config, "solve": "cold start, tol 1e-3 on "
                    "rho_rel", "tol": args.tol, "max_iters": args.max_iters, "precision": args.precision,
+                   "packs": "per node", "schedule": {1: "chain", 2: "node-parallel"}[S.schedule],
+                   "schedule_tuning_ms": S.tuned_ms,
                    "l2": "256 MB buffer written between timed solves (L2 flushed)", "parallelism": f"replicas x{world}"},
         "iterations_mean": float(np.mean(iters)), "apg_iters_per_s": float(np.sum(iters)) / local_s * world,
         "p50_ms": float(np.percentile(times, 50)), "p99_ms": float(np.percentile(times, 99)),
@@ -403,6 +439,24 @@ def run_ours(args, rank, world, local_rank):
         # solve of the first step's input to the same tolerance
         legs = {}
         sols = {}
+        Sh = Solver(P, prec, device, args.schedule, shared_packs=1)
+        t_sh = time_per_iteration(Sh, dev_in[0], stream, lo=100, hi=400, reps=2)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        sh_t = []
+        for k in range(args.warmup, n_steps):
+            e0.record(stream)
+            Sh.solve(dev_in[k], args.max_iters, args.tol, stream)
+            e1.record(stream)
+            inf_sh = Sh.finish()
+            sh_t.append(e0.elapsed_time(e1))
+        legs[PREC_NAMES[prec] + "_shared_packs"] = {
+            "solves_per_s": 1000.0 * len(sh_t) / sum(sh_t), "ms_per_solve": float(np.mean(sh_t)),
+            "us_per_iteration": 1000.0 * t_sh, "schedule": {1: "chain", 2: "node-parallel"}[Sh.schedule],
+            "factor_device_bytes": Sh.smpc.smpc_factor_device_bytes(Sh.fac),
+            "note": "one pack per factor: the per-node matrices differ only by 1/(2 p_n), applied to Lambda r"}
+        log("leg shared", legs[PREC_NAMES[prec] + "_shared_packs"])
+        Sh.close()
         for other in (0, 1, 2):
             So = Solver(P, other, device)
             if other == prec:  # the headline precision on the legs' input, for the error statement
@@ -513,7 +567,7 @@ def run_serve(args):
         t = P["tree"]
         tree = smpc.smpc_tree_create(t["parent"], t["prob"])
         prec = 1 if i % 2 == 0 else 2  # float32 and bfloat16 packs, mixed
-        fac = smpc.smpc_factor(tree, P["net"], P["cost"], precision=prec, precondition=1)
+        fac = smpc.smpc_factor(tree, P["net"], P["cost"], precision=prec, precondition=1, shared_packs=1)
         sess.append({"P": P, "tree": tree, "fac": fac, "prec": prec, "x": P["p"].copy(), "q": P["q"].copy(),
                      "k": 0, "pending": [], "rng": np.random.default_rng(100 + i)})
     total_bytes = sum(smpc.smpc_factor_device_bytes(s_["fac"]) for s_ in sess)
@@ -606,6 +660,85 @@ def run_serve(args):
     return result
 
 
+# --------------------------------------------------------------------- batched (forests)
+def run_batched(args):
+    """The 64 instances as four forests (one per network), solved concurrently through the
+    server's slots: one set of launches per iteration serves each forest's 16 trees."""
+    import torch
+
+    import paper_1604_01074_gb300 as smpc
+    import synth
+    torch.cuda.set_device(0)
+    insts = synth.batch_instances(0)
+    groups = [[P for P in insts if P["network"] == k] for k in range(4)]
+    prec = {"fp64": 0, "fp32": 1, "bf16": 2}[args.batched_precision]
+    forests, facs, trees = [], [], []
+    t0 = time.perf_counter()
+    for grp in groups:
+        F = synth.forest(grp)
+        t = F["tree"]
+        tree = smpc.smpc_tree_create(t["parent"], t["prob"])
+        fac = smpc.smpc_factor(tree, F["net"], F["cost"], precision=prec, precondition=1, shared_packs=1)
+        forests.append(F)
+        facs.append(fac)
+        trees.append(tree)
+    setup_s = time.perf_counter() - t0
+    log("batched: factors ready in", setup_s, "s; schedules", [smpc.smpc_factor_schedule(f)[0] for f in facs])
+    server = smpc.smpc_server_create(int(200e9), len(facs))
+    runs = []
+    for rep_ in range(args.batched_reps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        tickets = [smpc.smpc_submit(server, fac, F["p"], F["q"], F["dhat"], F["alpha2"], eps=F["eps"],
+                                    max_iters=args.max_iters, tol=args.tol) for F, fac in zip(forests, facs)]
+        res = []
+        for tk in tickets:
+            while True:
+                r = smpc.smpc_poll(server, tk)
+                if r is not None:
+                    res.append(r)
+                    break
+                time.sleep(0.0002)
+        runs.append((time.perf_counter() - t0, res))
+        log("batched rep", rep_, runs[-1][0], [(r["iterations"], round(r["rho_rel"], 6)) for r in res])
+    smpc.smpc_server_destroy(server)
+    wall = min(w for w, _ in runs)
+    res = min(runs, key=lambda x: x[0])[1]
+    n_inst = sum(len(g) for g in groups)
+    out = {"metric": "SMPC solves/sec to 1e-3 primal-dual residual, batched (64 uneven trees on 4 networks)",
+           "impl": "ours-batched", "value": n_inst / wall, "unit": "solves/s", "wall_s": wall,
+           "forests": [{"trees": len(g), "nodes": int(len(F["tree"]["parent"])), "iterations": r["iterations"],
+                        "rho_rel": r["rho_rel"], "run_ms": r["run_ms"]} for g, F, r in zip(groups, forests, res)],
+           "config": {"workload": "64 instances, 4 networks (n_x, n_u) in {(20,40),(35,65),(50,90),(63,114)}, "
+                                  "N in {12,18,24}, 10-500 scenarios, 249,644 nodes",
+                      "precision": args.batched_precision, "packs": "shared (one per forest)",
+                      "forests_concurrent": len(facs), "tol": args.tol,
+                      "criterion": "each forest stops when its max-over-trees residual, relative to its largest "
+                                   "|Hz| or |t|, reaches tol", "factor_setup_s": setup_s}}
+    for f_, t_ in zip(facs, trees):
+        smpc.smpc_factor_destroy(f_)
+        smpc.smpc_tree_destroy(t_)
+    # the plain FP64 single-tree solve (one pack per node, one instance at a time) on a sample
+    base = []
+    for P in [groups[k][0] for k in range(4)][: args.batched_baseline]:
+        t = P["tree"]
+        tree = smpc.smpc_tree_create(t["parent"], t["prob"])
+        fac = smpc.smpc_factor(tree, P["net"], P["cost"], precision=0, precondition=1)
+        torch.cuda.synchronize()
+        ts = time.perf_counter()
+        info = smpc.smpc_solve(fac, P["p"], P["q"], P["dhat"], P["alpha2"], eps=P["eps"], max_iters=args.max_iters,
+                               tol=args.tol, sync=1)
+        base.append((time.perf_counter() - ts, info["iterations"], int(len(t["parent"]))))
+        smpc.smpc_factor_destroy(fac)
+        smpc.smpc_tree_destroy(tree)
+    if base:
+        mean_s = float(np.mean([b[0] for b in base]))
+        out["fp64_single_tree"] = {"solves_per_s": 1.0 / mean_s, "mean_s": mean_s,
+                                   "sample": [{"s": b[0], "iterations": b[1], "nodes": b[2]} for b in base]}
+        out["speedup_vs_fp64_single_tree"] = out["value"] / out["fp64_single_tree"]["solves_per_s"]
+    return out
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return None
@@ -667,6 +800,10 @@ def main():
     ap.add_argument("--serve-budget-gb", type=float, default=64.0)
     ap.add_argument("--serve-max-iters", type=int, default=5000)
     ap.add_argument("--serve-baseline", type=int, default=6)
+    ap.add_argument("--batched", action="store_true", help="the 64-instance batched workload (its own JSON line)")
+    ap.add_argument("--batched-precision", choices=["fp64", "fp32", "bf16"], default="bf16")
+    ap.add_argument("--batched-reps", type=int, default=2)
+    ap.add_argument("--batched-baseline", type=int, default=4)
     ap.add_argument("--profile-solve", type=int, default=0,
                     help="factor + one solve of this many iterations (tol 0) and exit: the case ncu captures")
     args = ap.parse_args()
@@ -678,6 +815,9 @@ def main():
         return
     if args.serve:
         print(json.dumps(run_serve(args), default=_jsonable))
+        return
+    if args.batched:
+        print(json.dumps(run_batched(args), default=_jsonable))
         return
     rank, world, local_rank = dist_env()
     if args.impl == "reference":
