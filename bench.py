@@ -112,7 +112,8 @@ def algorithmic_bytes_per_iteration(n, n_x, n_u, n_v, prec):
     return n * (mat * ms + (vec_r + vec_w) * vs + state), n * mat, n * 2 * (n_k * n_v + n_v * n_v + n_k * n_v)
 
 
-STAGES = {1: ["apg_iter"], 2: ["fwd_scan", "prox_node", "scan_s", "node_mv_gt", "scan_r", "node_mv_dh"]}
+STAGES = {1: ["apg_iter"], 2: ["fwd_scan", "prox_node", "scan_s", "node_mv_gt", "scan_r", "node_mv_dh"],
+          3: ["fwd_scan", "prox_node", "apg_iter_gt", "node_mv_dh"]}
 
 
 def stage_bytes(stage, n, n_x, n_u, n_v, prec, shared):
@@ -125,6 +126,8 @@ def stage_bytes(stage, n, n_x, n_u, n_v, prec, shared):
     n_k = n_x + n_u
     if stage == "node_mv_gt":
         return n * ((0 if shared else n_k * n_v * ms) + (n_k + n_v) * vs)
+    if stage == "apg_iter_gt":
+        return n * ((0 if shared else n_k * n_v * ms) + (n_k + n_x + 2 * n_v) * vs)
     if stage == "node_mv_dh":
         return n * ((0 if shared else (n_k * n_v + n_v * n_v) * ms) + (n_v + n_k) * vs)
     return None
@@ -423,7 +426,7 @@ def run_ours(args, rank, world, local_rank):
         "vs_baseline": None, "dtype": PREC_NAMES[prec], "data": "synthetic",
         "config": {"workload": WORKLOAD if args.config == "barcelona" else args.config, "solve": "cold start, tol 1e-3 on "
                    "rho_rel", "tol": args.tol, "max_iters": args.max_iters, "precision": args.precision,
-                   "packs": "per node", "schedule": {1: "chain", 2: "node-parallel"}[S.schedule],
+                   "packs": "per node", "schedule": {1: "chain", 2: "node-parallel", 3: "hybrid"}[S.schedule],
                    "schedule_tuning_ms": S.tuned_ms,
                    "l2": "256 MB buffer written between timed solves (L2 flushed)", "parallelism": f"replicas x{world}"},
         "iterations_mean": float(np.mean(iters)), "apg_iters_per_s": float(np.sum(iters)) / local_s * world,
@@ -452,7 +455,7 @@ def run_ours(args, rank, world, local_rank):
             sh_t.append(e0.elapsed_time(e1))
         legs[PREC_NAMES[prec] + "_shared_packs"] = {
             "solves_per_s": 1000.0 * len(sh_t) / sum(sh_t), "ms_per_solve": float(np.mean(sh_t)),
-            "us_per_iteration": 1000.0 * t_sh, "schedule": {1: "chain", 2: "node-parallel"}[Sh.schedule],
+            "us_per_iteration": 1000.0 * t_sh, "schedule": {1: "chain", 2: "node-parallel", 3: "hybrid"}[Sh.schedule],
             "factor_device_bytes": Sh.smpc.smpc_factor_device_bytes(Sh.fac),
             "note": "one pack per factor: the per-node matrices differ only by 1/(2 p_n), applied to Lambda r"}
         log("leg shared", legs[PREC_NAMES[prec] + "_shared_packs"])
@@ -786,7 +789,7 @@ def main():
     ap.add_argument("--precision", choices=["fp64", "fp32", "bf16"], default="fp32")
     ap.add_argument("--config", choices=["barcelona", "tiny", "large"], default="barcelona")
     ap.add_argument("--tol", type=float, default=1e-3)
-    ap.add_argument("--schedule", type=int, choices=[0, 1, 2], default=0,
+    ap.add_argument("--schedule", type=int, choices=[0, 1, 2, 3], default=0,
                     help="iteration schedule: 0 = the factor times both and keeps the faster")
     ap.add_argument("--max-iters", type=int, default=100000)
     ap.add_argument("--no-cpu-baseline", action="store_true")

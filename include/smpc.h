@@ -113,8 +113,9 @@ typedef struct smpc_factor_opts {
   int32_t shared_packs;
   /* Iteration schedule: 1 = one launch per iteration with one CTA per chain (maximal
    * leaf path) of the tree; 2 = the backward sweep as subtree scans around per-node
-   * mat-vec launches, one task per node; 0 = time both on this GPU when the factor is
-   * built and keep the faster.  Results agree to rounding. */
+   * mat-vec launches, one task per node; 3 = node-parallel forward sweep and prox, a chain
+   * pass up to r, and the node-parallel Lambda / [Bbar; L] launch; 0 = time all of them on
+   * this GPU when the factor is built and keep the fastest.  Results agree to rounding. */
   int32_t schedule;
 } smpc_factor_opts;
 
@@ -196,9 +197,9 @@ void smpc_factor_destroy(smpc_factor_t* fac);
  * shapes as in smpc_factor_opts). */
 int smpc_factor_steps(const smpc_factor_t* fac, double* lambda, double* step_s, double* step_z,
                       double* step_p);
-/* Returns the schedule the factor uses (1 or 2, see smpc_factor_opts.schedule), or minus
- * SMPC_EINVAL for a NULL factor.  When ms_per_iter is not NULL, ms_per_iter[0..1] receive the
- * measured ms per iteration of schedules 1 and 2 when the factor chose between them (0 when
+/* Returns the schedule the factor uses (1, 2 or 3, see smpc_factor_opts.schedule), or minus
+ * SMPC_EINVAL for a NULL factor.  When ms_per_iter is not NULL, ms_per_iter[0..2] receive the
+ * measured ms per iteration of schedules 1, 2 and 3 when the factor chose among them (0 when
  * it did not time them). */
 int smpc_factor_schedule(const smpc_factor_t* fac, double* ms_per_iter);
 
@@ -243,9 +244,10 @@ int smpc_solve_static(smpc_factor_t* fac, const smpc_step_data* data, const smpc
  * iterations (tol 0, legacy default stream) with a CUDA event between consecutive kernels
  * of every full iteration, and writes the mean device time in ms
  * of each kernel of an iteration to stage_ms[0 .. min(n, max_stages)).  n = 1 for schedule 1
- * (apg_iter) and 6 for schedule 2 (forward sweep, prox and dual update, subtree scan of s,
- * [Bbar; L]' mat-vec, subtree scan of r, Lambda and [Bbar; L] mat-vecs).  SMPC_BF16 anchor
- * iterations are not timed.  Leaves
+ * (apg_iter), 6 for schedule 2 (forward sweep, prox and dual update, subtree scan of s,
+ * [Bbar; L]' mat-vec, subtree scan of r, Lambda and [Bbar; L] mat-vecs) and 4 for schedule 3
+ * (forward sweep; prox and dual update; s, [Bbar; L]' mat-vecs and r along the chains; Lambda
+ * and [Bbar; L] mat-vecs).  SMPC_BF16 anchor iterations are not timed.  Leaves
  * the factor's duals as that solve ends.  Returns n, or minus an smpc_status. */
 int smpc_profile_solve(smpc_factor_t* fac, const smpc_step_data* data, int32_t iters, double* stage_ms,
                        int32_t max_stages);

@@ -167,7 +167,7 @@ def smpc_factor(tree, net, cost, precision=SMPC_FP64, precondition=1, lam=0.0, p
                 steps=None, safety_unweighted=0, schedule=0, shared_packs=0):
     """net / cost: dicts with the fields of smpc_network / smpc_cost (numpy arrays).
     steps: optional dict {'s': (n,), 'z': (n,), 'p': (n, n_u)} of explicit per-entry steps.
-    schedule: 0 = time both iteration schedules and keep the faster, 1 = chain, 2 = node."""
+    schedule: 0 = time the iteration schedules and keep the fastest, 1 = chain, 2 = node, 3 = hybrid."""
     k = _Keep()
     A = net.get("A")
     n_x, n_u = net["B"].shape
@@ -192,12 +192,12 @@ def smpc_factor_destroy(fac):
 
 
 def smpc_factor_schedule(fac):
-    """(schedule in use, {1: ms per iteration, 2: ms per iteration} as timed by the factor)."""
-    ms = (ctypes.c_double * 2)()
+    """(schedule in use, {schedule: ms per iteration} as timed by the factor)."""
+    ms = (ctypes.c_double * 3)()
     s = lib().smpc_factor_schedule(fac, ms)
     if s < 0:
         raise SmpcError(-s, smpc_last_error())
-    return s, {1: ms[0], 2: ms[1]}
+    return s, {1: ms[0], 2: ms[1], 3: ms[2]}
 
 
 def smpc_factor_steps(fac, n, n_u):

@@ -447,12 +447,12 @@ int power_iteration(smpc_factor_t* f, int iters, double* out) {
 
 namespace smpc {
 
-// Iteration schedule of a factor: the requested one, or (0) the faster of the two on
-// this GPU, timed with CUDA events over a few solve-mode iterations of the factor's
-// own tree and packs from a zero state; the state is cleared again afterwards.
+// Iteration schedule of a factor: the requested one, or (0) the fastest on this GPU,
+// timed with CUDA events over a few solve-mode iterations of the factor's own tree and
+// packs from a zero state; the state is cleared again afterwards.
 int choose_schedule(smpc_factor_t* f, int requested) {
-  if (requested < 0 || requested > SCHED_NODE) {
-    set_error("schedule must be 0 (auto), 1 (chain) or 2 (node)");
+  if (requested < 0 || requested > kSchedules) {
+    set_error("schedule must be 0 (auto), 1 (chain), 2 (node) or 3 (hybrid)");
     return SMPC_EINVAL;
   }
   IterArgs a = make_args(f);
@@ -462,8 +462,15 @@ int choose_schedule(smpc_factor_t* f, int requested) {
     a.wa = f->wa;
   }
   const int mode_extra = anchored ? MODE_DELTA : 0;
-  bool fits[3] = {false, false, false};
-  for (int s = SCHED_CHAIN; s <= SCHED_NODE; ++s) fits[s] = iter_config(f->prec, a, f->num_sms, s).stages > 0;
+  bool fits[kSchedules + 1] = {};
+  int n_fit = 0, only = SCHED_CHAIN;
+  for (int s = 1; s <= kSchedules; ++s) {
+    fits[s] = iter_config(f->prec, a, f->num_sms, s).stages > 0;
+    if (fits[s]) {
+      ++n_fit;
+      only = s;
+    }
+  }
   if (requested != 0) {
     if (!fits[requested]) {
       set_error("the requested schedule does not fit this network");
@@ -472,17 +479,18 @@ int choose_schedule(smpc_factor_t* f, int requested) {
     f->schedule = requested;
     return SMPC_OK;
   }
-  if (!fits[SCHED_CHAIN] || !fits[SCHED_NODE]) {
-    f->schedule = fits[SCHED_NODE] ? SCHED_NODE : SCHED_CHAIN;
+  if (n_fit <= 1) {
+    f->schedule = only;
     return SMPC_OK;
   }
   TRY(upload_cvec(f, 16));
   cudaEvent_t e0, e1;
   CK(cudaEventCreate(&e0));
   CK(cudaEventCreate(&e1));
-  float best = 0;
+  float best = -1;
   constexpr int kWarm = 2, kTimed = 6;
-  for (int s = SCHED_CHAIN; s <= SCHED_NODE; ++s) {
+  for (int s = 1; s <= kSchedules; ++s) {
+    if (!fits[s]) continue;
     const LaunchCfg cfg = iter_config(f->prec, a, f->num_sms, s);
     int rc = SMPC_OK;
     for (int nu = 1; nu <= kWarm && !rc; ++nu) rc = launch_iter(f->prec, a, cfg, nu, MODE_BWD | MODE_PROX | mode_extra, nullptr);
@@ -497,7 +505,7 @@ int choose_schedule(smpc_factor_t* f, int requested) {
       if (!rc) set_error("schedule timing failed: %s", cudaGetErrorString(cudaGetLastError()));
       return rc ? rc : SMPC_ECUDA;
     }
-    if (s == SCHED_CHAIN || ms < best) {
+    if (best < 0 || ms < best) {
       best = ms;
       f->schedule = s;
     }
@@ -943,6 +951,7 @@ int smpc_factor_schedule(const smpc_factor_t* f, double* ms_per_iter) {
   if (ms_per_iter) {
     ms_per_iter[0] = f->tuned_ms[SCHED_CHAIN];
     ms_per_iter[1] = f->tuned_ms[SCHED_NODE];
+    ms_per_iter[2] = f->tuned_ms[SCHED_HYBRID];
   }
   return f->schedule;
 }

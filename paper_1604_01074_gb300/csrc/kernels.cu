@@ -470,6 +470,7 @@ struct Kern {
   __device__ bool anchor() const { return (mode & MODE_ANCHOR) != 0; }
   __device__ bool delta() const { return (mode & MODE_DELTA) != 0; }
   __device__ bool no_affine() const { return (mode & (MODE_LINEAR | MODE_DELTA)) != 0; }
+  __device__ bool gt() const { return (mode & MODE_GT) != 0; }
   // h of node m, entry e, as the forward sweep sees it
   __device__ AT h_at(long long m, int e) const {
     const long long q = m * a.n_k + e;
@@ -548,7 +549,7 @@ struct Kern {
   __device__ void prime(Pipe& p) {
     for (int s = 0; s < S; ++s) {
       issue_k(p);
-      issue_l(p);
+      if (!gt()) issue_l(p);
     }
   }
   // wait for the next K (resp. Lambda) load; returns its slot; sets abort_ on timeout
@@ -1060,6 +1061,12 @@ struct Kern {
       rreg += sm.gv[e];
       sm.rv[e] = rreg;
     }
+    if (gt()) {  // r of every node, for the node-parallel Lambda / [Bbar; L] launch
+      if (e < a.n_v) mv(a.rpub)[(long long)m * a.n_v + e] = (VT)rreg;
+      if (refill) issue_k(p);
+      __syncthreads();  // yv is rewritten by the next node
+      return;
+    }
     const int ls = wait_l(p);
     if (abort_) return;
     matvec_t<MT, AT>(sm.Lm(ls), a.n_v, a.n_v, sm.ld, sm.rv, sm.dv, sm.part);  // Lambda is symmetric
@@ -1138,10 +1145,10 @@ struct Kern {
       if (threadIdx.x == 0) {
         fence_proxy_async();
         copy_k(p.kiss, t);
-        copy_l(p.liss, t);
+        if (!gt()) copy_l(p.liss, t);
       }
       ++p.kiss;
-      ++p.liss;
+      if (!gt()) ++p.liss;
       const int cb = a.child_begin[t], cc = a.child_count[t];
       AT sreg = 0, rreg = 0;
       if (e < a.n_k) {
@@ -1192,7 +1199,7 @@ struct Kern {
       const int t = a.top_nodes[ti];
       if (do_prox) phase_p(a.parent[t], a.top_nodes + ti, 1);
       if (do_bwd) {
-        if (!do_prox || linear()) {
+        if ((!do_prox || linear()) && !(mode & MODE_WREADY)) {
           w_only(a.top_nodes + ti, 1);
           __syncthreads();
         }
@@ -1206,7 +1213,7 @@ struct Kern {
       const int* nodes = a.chain_node + cb;
       if (do_prox) phase_p(a.chain_parent[ch], nodes, len);
       if (!do_bwd) continue;
-      if (!do_prox || linear()) {
+      if ((!do_prox || linear()) && !(mode & MODE_WREADY)) {
         w_only(nodes, len);
         __syncthreads();
       }
@@ -1827,6 +1834,13 @@ LaunchCfg config_t(const IterArgs& a, int num_sms, int S_max, int schedule) {
     return c;
   }
   c.stages = fits_threads ? 1 : 0;
+  if (schedule == SCHED_HYBRID) {
+    const LaunchCfg ch = config_t<VT, MT>(a, num_sms, S_max, SCHED_CHAIN);
+    c.grid_chain = ch.grid;
+    c.stages_chain = ch.stages;
+    c.smem_chain = ch.smem;
+    if (ch.stages < 1) c.stages = 0;
+  }
   c.smem_prox = iter_smem_bytes<MT>(0, a.n_x, a.n_u, a.n_v);  // barriers + vectors, no pack slot
   c.grid_prox = (a.n + kWarps - 1) / kWarps;  // one warp per node
   if (c.grid_prox > 8 * num_sms) c.grid_prox = 8 * num_sms;
@@ -1894,7 +1908,17 @@ int launch_t(const IterArgs& a, const LaunchCfg& c, int nu, int mode, cudaStream
   }
   prox_node<VT, MT><<<c.grid_prox, c.block, c.smem_prox, s>>>(a, nu, mode);
   mark();
-  if (mode & MODE_BWD) {
+  if ((mode & MODE_BWD) && c.schedule == SCHED_HYBRID) {
+    // s, [Bbar; L]'[s; psi] and r along the chains and up the top nodes, r of every node out
+    apg_iter<VT, MT><<<c.grid_chain, c.block, c.smem_chain, s>>>(a, c.stages_chain, nu,
+                                                                 (mode & ~MODE_PROX) | MODE_GT | MODE_WREADY);
+    mark();
+    if (c.multi_dh)
+      node_mv_shared<VT, MT, true><<<c.grid_multi, c.block, c.smem_mdh, s>>>(a, nu, mode);
+    else
+      node_mv<VT, MT, true><<<c.grid_mv, c.block, c.smem_dh, s>>>(a, c.s_dh, nu, mode);
+    mark();
+  } else if (mode & MODE_BWD) {
     scan_kernel<VT><<<c.grid_scan, c.block, 0, s>>>(a, 0, nu, mode);
     mark();
     if (c.multi_gt)

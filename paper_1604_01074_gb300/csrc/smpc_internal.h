@@ -129,13 +129,17 @@ enum KernelMode : int {
   MODE_LINEAR = 4,    // power iteration on the (scaled) dual Hessian: no affine data, no prox
   MODE_CHECK = 8,     // honour the stop flag / tolerance
   MODE_ANCHOR = 16,   // anchored solve: evaluate the whole solve step at w_a = w^nu into ha
-  MODE_DELTA = 32     // anchored solve: solve step on w^nu - w_a, without the affine data
+  MODE_DELTA = 32,    // anchored solve: solve step on w^nu - w_a, without the affine data
+  MODE_GT = 64,       // backward sweep up to r only: s, g = [Bbar; L]'[s; psi], r for every node
+  MODE_WREADY = 128   // w^nu was written by an earlier launch of the iteration
 };
 
 enum Schedule : int {
   SCHED_CHAIN = 1,  // one apg_iter launch per iteration, one CTA per chain
-  SCHED_NODE = 2    // five launches per iteration, one task per node in each
+  SCHED_NODE = 2,   // six launches per iteration, one task per node in each
+  SCHED_HYBRID = 3  // node-parallel forward sweep and prox, a chain pass up to r, node-parallel Lambda / [Bbar; L]
 };
+constexpr int kSchedules = 3;
 
 struct LaunchCfg {
   int schedule = SCHED_CHAIN;
@@ -149,6 +153,9 @@ struct LaunchCfg {
   bool multi_gt = false, multi_dh = false;  // shared pack: several nodes per pass over it
   size_t smem_mgt = 0, smem_mdh = 0;
   int grid_multi = 1;
+  // hybrid schedule: the backward sweep up to r runs as the chain kernel in MODE_GT
+  int grid_chain = 1, stages_chain = 0;
+  size_t smem_chain = 0;
   // profiling: when set, an event is recorded before the first and after every kernel
   // of a launch_iter call (kernels_per_call + 1 events)
   cudaEvent_t* events = nullptr;
@@ -156,7 +163,7 @@ struct LaunchCfg {
 // kernels one launch_iter call enqueues
 inline int kernels_per_call(const LaunchCfg& c, int mode) {
   if (c.schedule == SCHED_CHAIN) return 1;
-  return 1 + ((mode & MODE_PROX) ? 1 : 0) + ((mode & MODE_BWD) ? 4 : 0);
+  return 1 + ((mode & MODE_PROX) ? 1 : 0) + ((mode & MODE_BWD) ? (c.schedule == SCHED_HYBRID ? 2 : 4) : 0);
 }
 
 // Kernel launchers (kernels.cu).  prec: smpc_precision.
@@ -273,7 +280,7 @@ struct smpc_factor_t {
   int last_launches = 0;
   int num_sms = 0;
   int schedule = smpc::SCHED_CHAIN;  // iteration schedule in use
-  float tuned_ms[3] = {0, 0, 0};     // per schedule: ms per iteration measured when the factor chose
+  float tuned_ms[4] = {0, 0, 0, 0};  // per schedule: ms per iteration measured when the factor chose
   smpc::Profile* profile = nullptr;  // set while smpc_profile_solve runs
   bool solved_once = false;
 

@@ -30,7 +30,7 @@ def _forest_case(seed, count):
     return members, F, steps, per
 
 
-@pytest.mark.parametrize("schedule", [1, 2])
+@pytest.mark.parametrize("schedule", [1, 2, 3])
 @pytest.mark.parametrize("shared", [0, 1])
 def test_forest_matches_each_tree_alone(schedule, shared):
     members, F, steps, per = _forest_case(0, 5)
