@@ -1118,10 +1118,13 @@ struct Kern {
   }
 
   // Arrival at top node t (children and its own Phase P count); true for the last one.
+  // The block barrier then one fence by thread 0 publish the whole CTA's writes (spub,
+  // rpub, h, wbuf) before the arrival; the fence after the last arrival orders the reads
+  // of the children's results (ld.cg) after it.
   __device__ bool arrive(int t) {
-    __threadfence();  // every thread's writes (spub, rpub, h, wbuf) before the arrival
     __syncthreads();
     if (threadIdx.x == 0) {
+      __threadfence();
       const int old = atomicAdd(&a.counters[t], 1);
       const int last = (old == a.top_expect[t] - 1);
       if (last) {
@@ -1329,7 +1332,7 @@ __global__ void __launch_bounds__(kThreads) fwd_scan(const __grid_constant__ Ite
 }
 
 template <typename VT, typename MT>
-__global__ void __launch_bounds__(kThreads) prox_node(const __grid_constant__ IterArgs a, int nu, int mode) {
+__global__ void __launch_bounds__(kThreads, 4) prox_node(const __grid_constant__ IterArgs a, int nu, int mode) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   Smem<MT> sm = carve<MT>(smem_raw, 0, a.n_x, a.n_u, a.n_v);
   // the forward sweep (when there is one) already took the stop decision
@@ -1387,16 +1390,18 @@ __global__ void __launch_bounds__(kThreads) scan_kernel(const __grid_constant__ 
       }
     }
     for (int t = a.chain_parent[ch]; t >= 0; t = a.parent[t]) {
-      __threadfence();  // this CTA's outputs before its arrival
-      __syncthreads();
+      __syncthreads();  // this CTA's outputs, then one fence, before its arrival (as in arrive)
       if (e == 0) {
+        __threadfence();
         const int last = atomicAdd(&a.counters[t], 1) == a.child_count[t] - 1;
-        if (last) a.counters[t] = 0;
+        if (last) {
+          a.counters[t] = 0;
+          __threadfence();
+        }
         flag[1] = last;
       }
       __syncthreads();
       if (!flag[1]) break;
-      __threadfence();
       if (e < W) {
         VT v = in[(long long)t * is + e];
         if (with_beta) v += beta[(long long)t * a.n_v + e];
