@@ -523,7 +523,7 @@ def profile_solve(args):
     device = torch.device("cuda", 0)
     prec = {"fp64": 0, "fp32": 1, "bf16": 2}[args.precision]
     P = make_problem(args.config, seed=0)
-    S = Solver(P, prec, device, args.schedule)
+    S = Solver(P, prec, device, args.schedule, shared_packs=int(args.shared_packs))
     stream = torch.cuda.current_stream(device)
     S.solve(S.device_inputs(step_inputs(P, 0)), args.profile_solve, 0.0, stream)
     info = S.finish()
@@ -807,6 +807,7 @@ def main():
     ap.add_argument("--batched-precision", choices=["fp64", "fp32", "bf16"], default="bf16")
     ap.add_argument("--batched-reps", type=int, default=2)
     ap.add_argument("--batched-baseline", type=int, default=4)
+    ap.add_argument("--shared-packs", action="store_true", help="--profile-solve: one shared pack per factor")
     ap.add_argument("--profile-solve", type=int, default=0,
                     help="factor + one solve of this many iterations (tol 0) and exit: the case ncu captures")
     args = ap.parse_args()

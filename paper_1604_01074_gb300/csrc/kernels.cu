@@ -27,6 +27,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <type_traits>
 
 #include "smpc_internal.h"
 
@@ -1814,6 +1815,194 @@ __global__ void __launch_bounds__(kThreads, 1) node_mv_shared(const __grid_const
   }
 }
 
+// ------------------------------------------------------------------ tensor-core Lambda / [Bbar; L]
+// bfloat16 shared pack, anchored (delta) launches: for tn nodes at a time (16, 32 or 64) the
+// two products are dense GEMMs on the 5th-generation tensor cores,
+//   D1 = Lambda_pad (128 x Kp) . R (Kp x tn),   delta = D1 / (2 p_b) rounded to bfloat16,
+//   D2 = [Bbar; L]_pad (256 x Kp) . delta (Kp x tn)  (two 128-row tiles),
+// Kp = n_v rounded up to 16.  Operands sit in shared memory K-major without swizzle, in
+// 8-row x 16-byte core matrices; accumulators (float32) sit in tensor memory.  One thread
+// issues the MMAs and commits them to an mbarrier; every wait is bounded.  The vectors
+// are rounded to bfloat16 here: in a delta launch they are the changes since the anchor,
+// whose rounding is an error proportional to |w - w_a| (the anchors run in float32).
+constexpr int kTcMaxN = 64;     // nodes per GEMM (the N of the MMA): 16, 32 or 64
+constexpr int kTcCore = 128;    // bytes per core matrix
+
+__host__ __device__ inline int tc_kp(int n_v) { return (n_v + 15) / 16 * 16; }
+__host__ __device__ inline size_t tc_smem_bytes(int n_v, int tn) {
+  const size_t sbo = (size_t)tc_kp(n_v) / 8 * kTcCore;  // bytes per 8-row group
+  return (128 / 8) * sbo + (256 / 8) * sbo + 2 * (size_t)(tn / 8) * sbo + 64;
+}
+__host__ __device__ inline bool tc_fits(int n_x, int n_u, int n_v) { return n_v <= 128 && n_x + n_u <= 256; }
+
+__device__ __forceinline__ uint64_t umma_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+  uint64_t d = (uint64_t)((saddr >> 4) & 0x3FFF);
+  d |= (uint64_t)((lbo >> 4) & 0x3FFF) << 16;
+  d |= (uint64_t)((sbo >> 4) & 0x3FFF) << 32;
+  d |= (uint64_t)1 << 46;  // descriptor version; base offset 0, no swizzle
+  return d;
+}
+__device__ __forceinline__ void umma_bf16(uint32_t d_tmem, uint64_t da, uint64_t db, uint32_t idesc, uint32_t acc) {
+  asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+               " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+               "l"(da), "l"(db), "r"(idesc), "r"(acc));
+}
+__device__ __forceinline__ void umma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+               : "memory");
+}
+__device__ __forceinline__ void tmem_ld16(uint32_t addr, float (&v)[16]) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(addr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
+}
+__device__ __forceinline__ void tc_sync() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+// byte offset of element (row r, k) of a K-major operand in core-matrix layout
+__device__ __forceinline__ int tc_off(int r, int k, int sbo) {
+  return (r >> 3) * sbo + (k >> 3) * kTcCore + (r & 7) * 16 + (k & 7) * 2;
+}
+
+template <typename VT>
+__global__ void __launch_bounds__(128, 1) node_mv_tc(const __grid_constant__ IterArgs a, int tn, int nu, int mode) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  __shared__ int flag[2];
+  if (early_exit(a, nu, mode, flag, false)) return;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int n_k = a.n_k, n_v = a.n_v, Kp = tc_kp(n_v), ld = row_stride<__nv_bfloat16>(n_v);
+  const int sbo = Kp / 8 * kTcCore;
+  unsigned char* A1 = smem_raw;                   // Lambda, 128 rows
+  unsigned char* A2 = A1 + 16 * sbo;              // [Bbar; L], 256 rows
+  unsigned char* B1 = A2 + 32 * sbo;              // R (tn rows)
+  unsigned char* B2 = B1 + (tn / 8) * sbo;        // delta (tn rows)
+  uint64_t* bar = reinterpret_cast<uint64_t*>(B2 + (tn / 8) * sbo);
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(bar + 1);
+  // pack -> core-matrix layout, zero padding (16-byte chunks; the pack's rows are ld >= n_v wide)
+  const __nv_bfloat16* pk = reinterpret_cast<const __nv_bfloat16*>(a.packs);
+  const long long kp = kpad<__nv_bfloat16>(n_k, n_v);
+  const int kc = Kp / 8;
+  for (int q = tid; q < (128 + 256) * kc; q += blockDim.x) {
+    const int row = q / kc, c = q % kc;
+    uint4 v = make_uint4(0, 0, 0, 0);
+    unsigned char* dst;
+    if (row < 128) {
+      if (row < n_v && 8 * c < ld) v = *reinterpret_cast<const uint4*>(pk + kp + (long long)row * ld + 8 * c);
+      dst = A1 + tc_off(row, 8 * c, sbo);
+    } else {
+      const int r = row - 128;
+      if (r < n_k && 8 * c < ld) v = *reinterpret_cast<const uint4*>(pk + (long long)r * ld + 8 * c);
+      dst = A2 + tc_off(r, 8 * c, sbo);
+    }
+    *reinterpret_cast<uint4*>(dst) = v;
+  }
+  for (int q = tid; q < 2 * (tn / 8) * sbo / 16; q += blockDim.x)
+    reinterpret_cast<uint4*>(B1)[q] = make_uint4(0, 0, 0, 0);
+  if (tid == 0) {
+    mbar_init(bar, 1);
+    fence_barrier_init();
+  }
+  if (warp == 0) {  // 3 tn accumulator columns: D1, D2 rows 0-127, D2 rows 128-255 (tn <= 64)
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)), "r"(256));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  fence_proxy_async();
+  tc_sync();
+  const uint32_t tmem = *tslot;
+  const uint32_t d1 = tmem, d2a = tmem + tn, d2b = tmem + 2 * tn;
+  const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(tn >> 3) << 17) | (8u << 24);
+  const VT* rp = reinterpret_cast<const VT*>(a.rpub);
+  const VT* ps = reinterpret_cast<const VT*>(a.pscale);
+  VT* h = reinterpret_cast<VT*>(a.h);
+  uint32_t phase = 0;
+  bool failed = false;
+  const int batches = (a.n + tn - 1) / tn;
+  for (int bt = blockIdx.x; bt < batches && !failed; bt += gridDim.x) {
+    const long long m0 = (long long)bt * tn;
+    const int nb = min(tn, a.n - (int)m0);
+    // R: row b = node m0 + b, bfloat16
+    for (int q = tid; q < tn * n_v; q += blockDim.x) {
+      const int b = q / n_v, j = q % n_v;
+      const float v = b < nb ? (float)rp[(m0 + b) * n_v + j] : 0.f;
+      *reinterpret_cast<__nv_bfloat16*>(B1 + tc_off(b, j, sbo)) = __float2bfloat16_rn(v);
+    }
+    fence_proxy_async();
+    tc_sync();
+    if (tid == 0) {
+      for (int ks = 0; ks < Kp / 16; ++ks)
+        umma_bf16(d1, umma_desc(smem_u32(A1) + ks * 2 * kTcCore, kTcCore, sbo),
+                  umma_desc(smem_u32(B1) + ks * 2 * kTcCore, kTcCore, sbo), idesc, ks > 0);
+      umma_commit(bar);
+    }
+    if (!mbar_wait(bar, phase)) failed = true;
+    phase ^= 1;
+    if (__syncthreads_or(failed)) {
+      failed = true;
+      break;
+    }
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    // delta = D1 / (2 p_b): warp w holds rows 32w..32w+31 (the entries of delta)
+    {
+      const int i = 32 * warp + lane;
+      for (int c0 = 0; c0 < tn; c0 += 16) {
+        float v[16];
+        tmem_ld16(d1 + ((uint32_t)(32 * warp) << 16) + c0, v);
+        if (i < Kp) {
+#pragma unroll
+          for (int j = 0; j < 16; ++j) {
+            const int b = c0 + j;
+            const float sc = (b < nb && i < n_v) ? (float)ps[m0 + b] : 0.f;
+            *reinterpret_cast<__nv_bfloat16*>(B2 + tc_off(b, i, sbo)) = __float2bfloat16_rn(v[j] * sc);
+          }
+        }
+      }
+    }
+    fence_proxy_async();
+    tc_sync();
+    if (tid == 0) {
+      for (int t = 0; t < 2; ++t)
+        for (int ks = 0; ks < Kp / 16; ++ks)
+          umma_bf16(t ? d2b : d2a, umma_desc(smem_u32(A2) + t * 16 * sbo + ks * 2 * kTcCore, kTcCore, sbo),
+                    umma_desc(smem_u32(B2) + ks * 2 * kTcCore, kTcCore, sbo), idesc, ks > 0);
+      umma_commit(bar);
+    }
+    if (!mbar_wait(bar, phase)) failed = true;
+    phase ^= 1;
+    if (__syncthreads_or(failed)) {
+      failed = true;
+      break;
+    }
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    for (int t = 0; t < 2; ++t) {
+      const int i = 128 * t + 32 * warp + lane;  // row of [Bbar; L], entry of h
+      for (int c0 = 0; c0 < tn; c0 += 16) {
+        float v[16];
+        tmem_ld16((t ? d2b : d2a) + ((uint32_t)(32 * warp) << 16) + c0, v);
+        if (i < n_k) {
+#pragma unroll
+          for (int j = 0; j < 16; ++j)
+            if (c0 + j < nb) h[(m0 + c0 + j) * n_k + i] = (VT)v[j];
+        }
+      }
+    }
+    tc_sync();  // B1, B2 and the accumulators are free for the next batch
+  }
+  if (failed && tid == 0) {
+    a.flags[1] = SMPC_ETIMEOUT;
+    mbar_wait(bar, phase ^ 1);  // bounded: let the MMAs in flight finish before freeing tensor memory
+  }
+  tc_sync();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(256));
+}
+
 int optin_smem() {
   int dev = 0, optin = 0;
   cudaGetDevice(&dev);
@@ -1864,6 +2053,17 @@ LaunchCfg config_t(const IterArgs& a, int num_sms, int S_max, int schedule) {
   if (c.s_gt < 1 || c.s_dh < 1) c.stages = 0;
   // shared pack: kNB nodes per pass when the pack and the staging fit
   c.multi_gt = c.multi_dh = false;
+  c.tc = false;
+  if (a.pack_stride == 0 && std::is_same<MT, __nv_bfloat16>::value && tc_fits(a.n_x, a.n_u, a.n_v) &&
+      tc_smem_bytes(a.n_v, kTcMaxN) + 256 <= (size_t)optin) {
+    // the widest GEMM (16, 32 or 64 nodes) that still gives every SM a batch
+    c.tc = true;
+    c.tn = 16;
+    while (c.tn < kTcMaxN && a.n >= 2 * c.tn * num_sms) c.tn *= 2;
+    c.smem_tc = tc_smem_bytes(a.n_v, c.tn);
+    const int batches = (a.n + c.tn - 1) / c.tn;
+    c.grid_tc = batches < num_sms ? batches : num_sms;
+  }
   if (a.pack_stride == 0) {
     c.smem_mgt = multi_smem_bytes<MT>(a.n_x, a.n_u, a.n_v, false);
     c.smem_mdh = multi_smem_bytes<MT>(a.n_x, a.n_u, a.n_v, true);
@@ -1893,6 +2093,7 @@ int launch_t(const IterArgs& a, const LaunchCfg& c, int nu, int mode, cudaStream
     allow(fwd_scan<VT, MT>);
     allow(node_mv_shared<VT, MT, false>);
     allow(node_mv_shared<VT, MT, true>);
+    if constexpr (std::is_same<MT, __nv_bfloat16>::value) allow(node_mv_tc<VT>);
     cudaGetLastError();  // a refused attribute surfaces at the launch, not here
     return true;
   }();
@@ -1918,10 +2119,20 @@ int launch_t(const IterArgs& a, const LaunchCfg& c, int nu, int mode, cudaStream
     apg_iter<VT, MT><<<c.grid_chain, c.block, c.smem_chain, s>>>(a, c.stages_chain, nu,
                                                                  (mode & ~MODE_PROX) | MODE_GT | MODE_WREADY);
     mark();
-    if (c.multi_dh)
-      node_mv_shared<VT, MT, true><<<c.grid_multi, c.block, c.smem_mdh, s>>>(a, nu, mode);
-    else
-      node_mv<VT, MT, true><<<c.grid_mv, c.block, c.smem_dh, s>>>(a, c.s_dh, nu, mode);
+    if constexpr (std::is_same<MT, __nv_bfloat16>::value) {
+      if (c.tc && (mode & MODE_DELTA)) {
+        node_mv_tc<VT><<<c.grid_tc, 128, c.smem_tc, s>>>(a, c.tn, nu, mode);
+      } else if (c.multi_dh) {
+        node_mv_shared<VT, MT, true><<<c.grid_multi, c.block, c.smem_mdh, s>>>(a, nu, mode);
+      } else {
+        node_mv<VT, MT, true><<<c.grid_mv, c.block, c.smem_dh, s>>>(a, c.s_dh, nu, mode);
+      }
+    } else {
+      if (c.multi_dh)
+        node_mv_shared<VT, MT, true><<<c.grid_multi, c.block, c.smem_mdh, s>>>(a, nu, mode);
+      else
+        node_mv<VT, MT, true><<<c.grid_mv, c.block, c.smem_dh, s>>>(a, c.s_dh, nu, mode);
+    }
     mark();
   } else if (mode & MODE_BWD) {
     scan_kernel<VT><<<c.grid_scan, c.block, 0, s>>>(a, 0, nu, mode);
@@ -1933,10 +2144,20 @@ int launch_t(const IterArgs& a, const LaunchCfg& c, int nu, int mode, cudaStream
     mark();
     scan_kernel<VT><<<c.grid_scan, c.block, 0, s>>>(a, 1, nu, mode);
     mark();
-    if (c.multi_dh)
-      node_mv_shared<VT, MT, true><<<c.grid_multi, c.block, c.smem_mdh, s>>>(a, nu, mode);
-    else
-      node_mv<VT, MT, true><<<c.grid_mv, c.block, c.smem_dh, s>>>(a, c.s_dh, nu, mode);
+    if constexpr (std::is_same<MT, __nv_bfloat16>::value) {
+      if (c.tc && (mode & MODE_DELTA)) {
+        node_mv_tc<VT><<<c.grid_tc, 128, c.smem_tc, s>>>(a, c.tn, nu, mode);
+      } else if (c.multi_dh) {
+        node_mv_shared<VT, MT, true><<<c.grid_multi, c.block, c.smem_mdh, s>>>(a, nu, mode);
+      } else {
+        node_mv<VT, MT, true><<<c.grid_mv, c.block, c.smem_dh, s>>>(a, c.s_dh, nu, mode);
+      }
+    } else {
+      if (c.multi_dh)
+        node_mv_shared<VT, MT, true><<<c.grid_multi, c.block, c.smem_mdh, s>>>(a, nu, mode);
+      else
+        node_mv<VT, MT, true><<<c.grid_mv, c.block, c.smem_dh, s>>>(a, c.s_dh, nu, mode);
+    }
     mark();
   }
   return check_launch("node-parallel iteration");

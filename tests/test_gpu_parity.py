@@ -313,3 +313,27 @@ def test_shared_packs_reduced_precision(precision):
         g.close()
     assert abs(info["rho_rel"] - R.rho_rel[-1]) <= 1e-4
     assert small < per_node
+
+
+def test_bf16_shared_tensor_core_solve_full_size():
+    """bfloat16 shared packs: the Lambda / [Bbar; L] products of every delta launch run on the
+    tensor cores (tcgen05), the anchors in float32.  The solve still reaches rho_rel <= 1e-3
+    in about the float64 iteration count and lands near the float64 solution."""
+    import json
+    import os
+    P = synth.barcelona(0)
+    golden = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "oracle_iters_to_tol.json")))
+    ref_iters = golden["barcelona"]["iterations"]
+    res = {}
+    for prec, shared in ((0, 0), (2, 1)):
+        g = H.Gpu(P, precision=prec, shared_packs=shared)
+        try:
+            info = g.solve(40000, tol=1e-3, check_every=256)
+            res[prec] = (info, g.arrays())
+        finally:
+            g.close()
+    info, (u, x, _) = res[2]
+    assert info["rho_rel"] <= 1e-3
+    assert info["iterations"] <= 1.02 * ref_iters, info["iterations"]
+    u64, x64, _ = res[0][1]
+    assert H.relerr(u, u64) <= 1e-3 and H.relerr(x, x64) <= 1e-3, (H.relerr(u, u64), H.relerr(x, x64))
