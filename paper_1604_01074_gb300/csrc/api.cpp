@@ -77,7 +77,7 @@ bool finite_if_host(const double* p, size_t n) { return !host_readable(p) || fin
 
 void free_tree_dev(smpc::DevTree& d) {
   void* ptrs[] = {d.parent, d.stage, d.child_begin, d.child_count, d.chain_off, d.chain_node, d.chain_parent,
-                  d.top_nodes, d.top_expect, d.path_off, d.path_node, d.tree_of, d.row, d.prob, d.pbar};
+                  d.top_nodes, d.top_expect, d.path_off, d.path_node, d.tree_of, d.row, d.seg, d.prob, d.pbar};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   d = smpc::DevTree();
@@ -221,6 +221,20 @@ int build_tree(int32_t n, const int32_t* parent, const double* prob, smpc_tree& 
     }
   }
   t.path_off[n] = (int)t.path_node.size();
+  const int n_seg = (int)(t.top_nodes.size() + t.chain_parent.size());
+  t.seg.assign((size_t)n_seg * smpc::kSegInts, 0);
+  for (int b = 0; b < n_seg; ++b) {
+    int* d = t.seg.data() + (size_t)b * smpc::kSegInts;
+    const bool top = b < (int)t.top_nodes.size();
+    const int c = b - (int)t.top_nodes.size();
+    const int par = top ? t.top_nodes[b] : t.chain_parent[c];
+    d[0] = par;
+    d[1] = par >= 0 ? t.path_off[par] : 0;
+    d[2] = par >= 0 ? t.path_off[par + 1] - t.path_off[par] : 0;
+    d[3] = top ? t.tree_of[par] : t.tree_of[t.chain_node[t.chain_off[c]]];
+    d[4] = top ? 0 : t.chain_off[c];
+    d[5] = top ? 0 : t.chain_off[c + 1] - t.chain_off[c];
+  }
   return SMPC_OK;
 }
 
@@ -240,6 +254,7 @@ int upload_tree(smpc_tree& t) {
   if (!t.path_node.empty()) TRY(dev_upload(&d.path_node, t.path_node.data(), t.path_node.size()));
   TRY(dev_upload(&d.tree_of, t.tree_of.data(), t.n));
   TRY(dev_upload(&d.row, t.row.data(), t.n));
+  TRY(dev_upload(&d.seg, t.seg.data(), t.seg.size()));
   TRY(dev_upload(&d.prob, t.prob.data(), t.n));
   TRY(dev_upload(&d.pbar, t.pbar.data(), t.n));
   return SMPC_OK;
@@ -273,6 +288,7 @@ IterArgs make_args(const smpc_factor_t* f) {
   a.path_off = t->dev.path_off;
   a.path_node = t->dev.path_node;
   a.tree_of = t->dev.tree_of;
+  a.seg = t->dev.seg;
   a.packs = f->packs;
   a.pscale = f->pscale;
   a.pack_stride = f->pack_stride;

@@ -76,6 +76,22 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
       "l"(src), "r"(bytes), "r"(smem_u32(b))
       : "memory");
 }
+// One 4- or 8-byte element copied into shared memory by cp.async: the copies of a
+// thread are issued back to back without holding registers and complete at
+// cp_async_wait_all, after which the issuing thread sees them (others after a barrier).
+template <typename T>
+__device__ __forceinline__ void cp_async_elem(T* dst, const T* src) {
+  static_assert(sizeof(T) == 4 || sizeof(T) == 8, "4- or 8-byte elements");
+  asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(smem_u32(dst)),
+               "l"((unsigned long long)__cvta_generic_to_global(src)), "n"((int)sizeof(T))
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+// Release / acquire fence at GPU scope for the arrival counters: after a block barrier,
+// thread 0's fence makes the whole CTA's prior writes visible before its arrival (the
+// fence is cumulative over what the barrier ordered before it), and the last arriver's
+// fence orders its reads of the other CTAs' results after their arrivals.
+__device__ __forceinline__ void fence_acq_rel_gpu() { asm volatile("fence.acq_rel.gpu;" ::: "memory"); }
 __device__ __forceinline__ bool mbar_test(uint64_t* b, uint32_t parity) {
   uint32_t ok;
   asm volatile(
@@ -860,64 +876,12 @@ struct Kern {
     }
   }
 
-  // ---------------------------------------------------------- forward sweep alone
-  // Segment b of the node-parallel schedule: top node b (b < n_top), else chain
-  // b - n_top.  Thread e sums entry e of [x; u] down the segment's path and writes the
-  // forward-sweep result of every node of the segment to xout / uout.
-  __device__ void store_xu(long long m, int e, AT X, AT U) const {
-    if (e < a.n_x) {
-      mv(a.xout)[m * a.n_x + e] = (VT)X;
-    } else {
-      const int i = e - a.n_x;
-      mv(a.uout)[m * a.n_u + i] = (VT)(U + (linear() ? (AT)0 : (AT)cv(a.uhat)[m * a.n_u + i]));
-    }
-  }
-  __device__ void fwd_segment(int b) const {
-    const int e = threadIdx.x;
-    if (e >= a.n_k) return;
-    AT V = 0, X = 0, U = 0;
-    if (b < a.n_top) {
-      const int t = a.top_nodes[b];
-      path_init(t, a.tree_of[t], e, V, X, U);
-      store_xu(t, e, X, U);
-      return;
-    }
-    const int c = b - a.n_top;
-    path_init(a.chain_parent[c], a.tree_of[a.chain_node[a.chain_off[c]]], e, V, X, U);
-    const int cb = a.chain_off[c], len = a.chain_off[c + 1] - cb;
-    const bool tank = e < a.n_x, lin = linear();
-    constexpr int B = 16;
-    for (int k0 = 0; k0 < len; k0 += B) {
-      AT hv[B], ev[B];
-#pragma unroll
-      for (int j = 0; j < B; ++j) {
-        hv[j] = ev[j] = 0;
-        if (k0 + j < len) {
-          const int m = a.chain_node[cb + k0 + j];
-          hv[j] = h_at(m, e);
-          if (tank && !lin) ev[j] = (AT)cv(a.e)[(long long)m * a.n_x + e];
-        }
-      }
-#pragma unroll
-      for (int j = 0; j < B; ++j) {
-        if (k0 + j >= len) break;
-        if (tank) {
-          V += hv[j];
-          X += V + ev[j];
-        } else {
-          U += hv[j];
-        }
-        store_xu(a.chain_node[cb + k0 + j], e, X, U);
-      }
-    }
-  }
-
   // ---------------------------------------------------------- warp-level Phase P
   // Node m alone on one warp (node-parallel schedule): lane l owns the entries
   // e = l + 32 k of [x; u].  The arithmetic of phase_p, with warp reductions only,
   // so the warps of a CTA run independent nodes without block barriers.
   static constexpr int kEPL = kThreads / 32;  // entries per lane (n_k <= kThreads)
-  // x and u of node m come from the forward sweep (fwd_segment, previous launch).
+  // x and u of node m come from the forward sweep (fwd_scan, previous launch).
   __device__ void warp_prox(int m, bool do_prox, bool do_w) {
     const int lane = threadIdx.x & 31;
     const bool lin = linear();
@@ -1125,12 +1089,12 @@ struct Kern {
   __device__ bool arrive(int t) {
     __syncthreads();
     if (threadIdx.x == 0) {
-      __threadfence();
+      fence_acq_rel_gpu();
       const int old = atomicAdd(&a.counters[t], 1);
       const int last = (old == a.top_expect[t] - 1);
       if (last) {
         a.counters[t] = 0;  // nobody else touches it again in this launch
-        __threadfence();
+        fence_acq_rel_gpu();
       }
       sm.flag[0] = last;
     }
@@ -1281,13 +1245,21 @@ __device__ bool early_exit(const IterArgs& a, int nu, int mode, int* flag, bool 
   if (threadIdx.x == 0) {
     int stop = 0;
     if (mode & MODE_CHECK) {
+      // the flags and the residuals are loaded together (one round trip)
+      const bool test = decide && a.tol > 0 && nu >= 2;
+      const unsigned long long* r = a.res + 3ll * (test ? nu - 2 : 0);
       const int done = ldcg(a.flags + 0), err = ldcg(a.flags + 1);
+      unsigned long long r0 = 0, r1 = 0, r2 = 0;
+      if (test) {
+        r0 = ldcg(r + 0);
+        r1 = ldcg(r + 1);
+        r2 = ldcg(r + 2);
+      }
       if (done >= 0 || err != 0) stop = 1;
-      if (decide && !stop && a.tol > 0 && nu >= 2) {
-        const unsigned long long* r = a.res + 3ll * (nu - 2);
-        const double rho = __longlong_as_double((long long)ldcg(r + 0));
-        const double hz = __longlong_as_double((long long)ldcg(r + 1));
-        const double tt = __longlong_as_double((long long)ldcg(r + 2));
+      if (test && !stop) {
+        const double rho = __longlong_as_double((long long)r0);
+        const double hz = __longlong_as_double((long long)r1);
+        const double tt = __longlong_as_double((long long)r2);
         if (rho / (1.0 + fmax(hz, tt)) <= a.tol) {
           stop = 1;
           if (blockIdx.x == 0) a.flags[0] = nu - 1;
@@ -1322,14 +1294,78 @@ __global__ void __launch_bounds__(kThreads, 1)
 // [Bbar; L] is read twice per iteration instead of once, but each launch has one
 // independent task per node instead of one sequential task per chain.
 
-// forward sweep of iteration nu - 1: one CTA per top node and per chain
+// Forward sweep of iteration nu - 1: one CTA per segment (a top node with its path
+// from the root, or a chain with the path above it).  The vectors (h, h_a, e or u_hat)
+// of up to fwd_chunk nodes are staged in shared memory by cp.async, issued back to
+// back with one wait, so a chunk costs about one load latency; thread e then sums
+// entry e down the chunk from shared memory (it reads only what it copied itself)
+// and stores x (tank entries) or u (inputs) of the segment's own nodes.
+template <typename VT>
+__host__ __device__ constexpr int fwd_chunk() { return sizeof(VT) == 4 ? 32 : 16; }
+template <typename VT>
+size_t fwd_smem_bytes(int n_k) { return (size_t)3 * fwd_chunk<VT>() * n_k * sizeof(VT); }
+
 template <typename VT, typename MT>
 __global__ void __launch_bounds__(kThreads) fwd_scan(const __grid_constant__ IterArgs a, int nu, int mode) {
+  using AT = typename Acc<MT>::T;
+  constexpr int KC = fwd_chunk<VT>();
   extern __shared__ __align__(128) unsigned char smem_raw[];
-  Smem<MT> sm = carve<MT>(smem_raw, 0, a.n_x, a.n_u, a.n_v);
-  if (early_exit(a, nu, mode, sm.flag + 1, true)) return;
-  Kern<VT, MT> k(a, sm, 0, nu, mode);
-  for (int b = blockIdx.x; b < a.n_top + a.n_chains; b += gridDim.x) k.fwd_segment(b);
+  __shared__ int flag[2];
+  __shared__ int sid[KC];
+  if (early_exit(a, nu, mode, flag, true)) return;
+  const int n_k = a.n_k, e = threadIdx.x, i = e - a.n_x;
+  const bool act = e < n_k, tank = e < a.n_x, lin = (mode & MODE_LINEAR) != 0;
+  VT* sh = reinterpret_cast<VT*>(smem_raw);  // KC x n_k each: h, h_a, e or u_hat
+  VT* sa = sh + KC * n_k;
+  VT* se = sa + KC * n_k;
+  const VT* H = reinterpret_cast<const VT*>(a.h);
+  const VT* HA = reinterpret_cast<const VT*>(a.ha);
+  const VT* E = reinterpret_cast<const VT*>(a.e);
+  const VT* UH = reinterpret_cast<const VT*>(a.uhat);
+  VT* XO = reinterpret_cast<VT*>(a.xout);
+  VT* UO = reinterpret_cast<VT*>(a.uout);
+  for (int b = blockIdx.x; b < a.n_top + a.n_chains; b += gridDim.x) {
+    const int4 d0 = *reinterpret_cast<const int4*>(a.seg + (long long)kSegInts * b);
+    const int4 d1 = *reinterpret_cast<const int4*>(a.seg + (long long)kSegInts * b + 4);
+    const int pb = d0.y, pl = d0.z, cb = d1.x, len = d1.y;
+    const int L = pl + len;  // the path (root .. par), then the chain
+    AT V = 0, U = 0;
+    AT X = (act && tank && !lin) ? (AT)reinterpret_cast<const VT*>(a.p0)[(long long)d0.w * a.n_x + e] : (AT)0;
+    for (int k0 = 0; k0 < L; k0 += KC) {
+      const int q = min(KC, L - k0);
+      __syncthreads();  // the previous chunk's node ids are consumed
+      if (e < q) sid[e] = k0 + e < pl ? a.path_node[pb + k0 + e] : a.chain_node[cb + k0 + e - pl];
+      __syncthreads();
+      if (!act) continue;
+      for (int r = 0; r < q; ++r) {
+        const long long m = sid[r];
+        cp_async_elem(sh + r * n_k + e, H + m * n_k + e);
+        if (HA) cp_async_elem(sa + r * n_k + e, HA + m * n_k + e);
+        if (!lin) cp_async_elem(se + r * n_k + e, tank ? E + m * a.n_x + e : UH + m * a.n_u + i);
+      }
+      cp_async_wait_all();
+      for (int r = 0; r < q; ++r) {
+        const int k = k0 + r;
+        AT hv = (AT)sh[r * n_k + e];
+        if (HA) hv += (AT)sa[r * n_k + e];
+        const AT ev = lin ? (AT)0 : (AT)se[r * n_k + e];
+        if (tank) {
+          V += hv;
+          X += V + ev;
+        } else {
+          U += hv;
+        }
+        // the segment's own nodes: the chain, or the top node that ends the path
+        if (k >= pl || (len == 0 && k == pl - 1)) {
+          const long long m = sid[r];
+          if (tank)
+            XO[m * a.n_x + e] = (VT)X;
+          else
+            UO[m * a.n_u + i] = (VT)(U + ev);
+        }
+      }
+    }
+  }
 }
 
 template <typename VT, typename MT>
@@ -1364,52 +1400,68 @@ __global__ void __launch_bounds__(kThreads) scan_kernel(const __grid_constant__ 
   const VT* beta = reinterpret_cast<const VT*>(a.beta);
   const long long is = which == 0 ? a.n_k : a.n_v, os = W;
   constexpr int B = 32;  // chain nodes whose loads are in flight together
+  constexpr int C = 8;   // children of a top node loaded together
   for (int ch = blockIdx.x; ch < a.n_chains; ch += gridDim.x) {
     const int cb = a.chain_off[ch], len = a.chain_off[ch + 1] - cb;
+    int t = a.chain_parent[ch];
     if (e < W) {
       VT acc = 0;
-      for (int k1 = len; k1 > 0; k1 -= B) {  // nodes k1-1 .. k1-B, bottom-up, loads batched
+      for (int k1 = len; k1 > 0; k1 -= B) {  // nodes k1-1 .. k1-B, bottom-up: ids, then vectors, then sums
+        int id[B];
         VT v[B];
+#pragma unroll
+        for (int j = 0; j < B; ++j) id[j] = k1 - 1 - j >= 0 ? a.chain_node[cb + k1 - 1 - j] : -1;
 #pragma unroll
         for (int j = 0; j < B; ++j) {
           v[j] = 0;
-          const int k = k1 - 1 - j;
-          if (k >= 0) {
-            const long long m = a.chain_node[cb + k];
-            v[j] = in[m * is + e];
-            if (with_beta) v[j] += beta[m * a.n_v + e];
+          if (id[j] >= 0) {
+            v[j] = in[(long long)id[j] * is + e];
+            if (with_beta) v[j] += beta[(long long)id[j] * a.n_v + e];
           }
         }
 #pragma unroll
         for (int j = 0; j < B; ++j) {
-          const int k = k1 - 1 - j;
-          if (k >= 0) {
+          if (id[j] >= 0) {
             acc += v[j];
-            out[(long long)a.chain_node[cb + k] * os + e] = acc;
+            out[(long long)id[j] * os + e] = acc;
           }
         }
       }
     }
-    for (int t = a.chain_parent[ch]; t >= 0; t = a.parent[t]) {
+    while (t >= 0) {
+      // the top node's own term and its children's range are loaded before the arrival
+      // (only the last arriving CTA uses them, and only it writes out[t], after every
+      // arrival); the children's sums, written by other CTAs, after it
+      const int c0 = a.child_begin[t], cc = a.child_count[t], up = a.parent[t];
+      VT v = 0;
+      if (e < W) {
+        v = in[(long long)t * is + e];
+        if (with_beta) v += beta[(long long)t * a.n_v + e];
+      }
       __syncthreads();  // this CTA's outputs, then one fence, before its arrival (as in arrive)
       if (e == 0) {
-        __threadfence();
-        const int last = atomicAdd(&a.counters[t], 1) == a.child_count[t] - 1;
+        fence_acq_rel_gpu();
+        const int last = atomicAdd(&a.counters[t], 1) == cc - 1;
         if (last) {
           a.counters[t] = 0;
-          __threadfence();
+          fence_acq_rel_gpu();
         }
         flag[1] = last;
       }
       __syncthreads();
       if (!flag[1]) break;
       if (e < W) {
-        VT v = in[(long long)t * is + e];
-        if (with_beta) v += beta[(long long)t * a.n_v + e];
-        const int c0 = a.child_begin[t], c1 = c0 + a.child_count[t];
-        for (int c = c0; c < c1; ++c) v += ldcg(out + (long long)c * os + e);
+        for (int q = 0; q < cc; q += C) {
+          VT cv8[C];
+#pragma unroll
+          for (int j = 0; j < C; ++j) cv8[j] = q + j < cc ? ldcg(out + (long long)(c0 + q + j) * os + e) : (VT)0;
+#pragma unroll
+          for (int j = 0; j < C; ++j)
+            if (q + j < cc) v += cv8[j];
+        }
         out[(long long)t * os + e] = v;
       }
+      t = up;
     }
   }
 }
@@ -2042,6 +2094,8 @@ LaunchCfg config_t(const IterArgs& a, int num_sms, int S_max, int schedule) {
   c.grid_fwd = a.n_top + a.n_chains < 8 * num_sms ? a.n_top + a.n_chains : 8 * num_sms;
   c.grid_mv = a.n < num_sms ? a.n : num_sms;
   if (c.grid_scan < 1) c.grid_scan = 1;
+  c.smem_fwd = fwd_smem_bytes<VT>(a.n_k);
+  if (c.smem_fwd + 1024 > (size_t)optin) c.stages = 0;
   int S = kMaxSlots;
   while (S > 0 && iter_smem_bytes<MT>(S, a.n_x, a.n_u, a.n_v, false) > (size_t)optin) --S;
   c.s_gt = S;
@@ -2109,7 +2163,7 @@ int launch_t(const IterArgs& a, const LaunchCfg& c, int nu, int mode, cudaStream
     return check_launch("apg_iter");
   }
   if ((mode & MODE_PROX) && nu >= 1) {
-    fwd_scan<VT, MT><<<c.grid_fwd, c.block, c.smem_prox, s>>>(a, nu, mode);
+    fwd_scan<VT, MT><<<c.grid_fwd, c.block, c.smem_fwd, s>>>(a, nu, mode);
     mark();
   }
   prox_node<VT, MT><<<c.grid_prox, c.block, c.smem_prox, s>>>(a, nu, mode);

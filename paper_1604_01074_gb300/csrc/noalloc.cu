@@ -241,6 +241,7 @@ extern "C" int smpc_solve_static(smpc_factor_t* f, const smpc_step_data* data, c
   a.path_off = t->dev.path_off;
   a.path_node = t->dev.path_node;
   a.tree_of = t->dev.tree_of;
+  a.seg = t->dev.seg;
   a.pscale = f->pscale;
   a.packs = f->packs;
   a.pack_stride = f->pack_stride;

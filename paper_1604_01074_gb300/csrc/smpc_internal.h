@@ -34,6 +34,12 @@ int host_factor(const smpc_network& net, const double* W_u, HostFactor& out);
 
 // ---------------------------------------------------------------------------
 // Tree structure after validation (host copy + device mirrors).
+// Forward-sweep segment b (top nodes first, then chains), kSegInts ints:
+// {par, path begin, path length, tree, chain begin, chain length, 0, 0}.  par is the
+// top node itself for a top segment (chain length 0) and the top node above the
+// chain head for a chain (-1 when the chain starts at a root).
+constexpr int kSegInts = 8;
+
 struct DevTree {
   int* parent = nullptr;
   int* stage = nullptr;
@@ -48,6 +54,7 @@ struct DevTree {
   int* path_node = nullptr;
   int* tree_of = nullptr;       // per node: its tree (the index of its root)
   int* row = nullptr;           // per node: its row of the stage-indexed step data
+  int* seg = nullptr;           // kSegInts per forward-sweep segment (top nodes, then chains)
   double* prob = nullptr;
   double* pbar = nullptr;       // p_n + sum of children's p (App. A)
 };
@@ -64,6 +71,7 @@ struct smpc_tree {
   std::vector<int> chain_off, chain_node, chain_parent;
   std::vector<int> top_nodes, is_top, top_expect;
   std::vector<int> path_off, path_node;
+  std::vector<int> seg;  // forward-sweep segment descriptors (kSegInts each)
   smpc::DevTree dev;
 };
 
@@ -84,6 +92,7 @@ struct IterArgs {
   const int* path_off;
   const int* path_node;
   const int* tree_of;            // per node: its tree (p0 has one state per tree)
+  const int* seg;                // kSegInts per forward-sweep segment, 32-byte aligned
   const void* packs;             // per node: [Bbar; L] (n_k x n_v) then Lambda/(2 p_n) (n_v x n_v)
   long long pack_stride;         // entries between consecutive nodes' packs (0: one shared pack)
   const void* pscale;            // shared pack: per node 1 / (2 p_n), applied to Lambda r; else NULL
@@ -149,6 +158,7 @@ struct LaunchCfg {
   // node schedule
   int grid_prox = 1, grid_scan = 1, grid_mv = 1, grid_fwd = 1;
   size_t smem_prox = 0, smem_gt = 0, smem_dh = 0;
+  size_t smem_fwd = 0;   // forward sweep: staged node vectors
   int s_gt = 0, s_dh = 0;   // pack slots of the two mat-vec launches (0: does not fit)
   bool multi_gt = false, multi_dh = false;  // shared pack: several nodes per pass over it
   bool tc = false;          // bfloat16 shared pack: Lambda / [Bbar; L] of delta launches on tensor cores
