@@ -87,6 +87,14 @@ __device__ __forceinline__ void cp_async_elem(T* dst, const T* src) {
                : "memory");
 }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+// Programmatic dependent launch: the iteration kernels let the next kernel of the
+// stream be scheduled as soon as they start (its CTAs take free SM slots while this
+// grid drains), and each waits for the previous grid to complete, with its memory
+// visible, before it touches anything.  Without the launch attribute both are no-ops.
+__device__ __forceinline__ void grid_dep_sync() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+}
 // Release / acquire fence at GPU scope for the arrival counters: after a block barrier,
 // thread 0's fence makes the whole CTA's prior writes visible before its arrival (the
 // fence is cumulative over what the barrier ordered before it), and the last arriver's
@@ -494,6 +502,16 @@ struct Kern {
     AT v = (AT)hb()[q];
     if (a.ha) v += (AT)cv(a.ha)[q];
     return v;
+  }
+  // put_w with the flat index q = m n_k + e and w_a[q] loaded beforehand (delta launches)
+  __device__ void put_w_at(long long q, ST w, AT wa_q) const {
+    if (delta()) {
+      wb()[q] = (VT)st_val(st_sub(w, st_from<ST>((double)wa_q)));
+    } else {
+      const VT v = (VT)st_val(w);
+      wb()[q] = v;
+      if (anchor()) mv(a.wa)[q] = v;
+    }
   }
   // stores w^nu (entry e of node m) for the backward sweep of this launch
   __device__ void put_w(long long m, int e, ST w) const {
@@ -1013,6 +1031,108 @@ struct Kern {
     }
   }
 
+  // The prox step of warp_prox (non-linear iterations) with the node's data staged in
+  // shared memory: each lane copies its own entries by cp.async (issued back to back,
+  // one wait), then the entries are processed in a rolled loop from shared memory, so
+  // the launch pays one load latency per node and its code stays small.  stage: this
+  // warp's region of prox_stage_bytes; bnd: x_s, x_max, x_min, u_max, u_min in shared
+  // memory, kThreads apart.
+  __device__ void warp_prox_staged(int m, const AT* bnd, unsigned char* stage) {
+    const int lane = threadIdx.x & 31;
+    const int n_x = a.n_x, n_k = a.n_k, n_u = a.n_u;
+    ST* Q0 = reinterpret_cast<ST*>(stage);  // y1, y2 of entry e's (first) block: n_k each
+    ST* Q1 = Q0 + n_k;
+    ST* Q2 = Q1 + n_k;                      // y1, y2 of a tank's second block: n_x each
+    ST* Q3 = Q2 + n_x;
+    VT* Z = reinterpret_cast<VT*>(Q3 + n_x);  // x or u: n_k
+    VT* SP = Z + n_k;                         // step_p, 1 / step_p: n_u each
+    VT* IP = SP + n_u;
+    VT* WA = IP + n_u;                        // w_a (delta launches): n_k
+    const int it = nu - 1;
+    const ST* y1 = ys(it) + (long long)m * nd;
+    ST* y2 = ys(it + 1) + (long long)m * nd;
+    const long long mk = (long long)m * n_k;
+    const bool dl = delta();
+    for (int e = lane; e < n_k; e += 32) {
+      if (e < n_x) {
+        cp_async_elem(Z + e, cv(a.xout) + (long long)m * n_x + e);
+        cp_async_elem(Q0 + e, y1 + e);
+        cp_async_elem(Q1 + e, y2 + e);
+        cp_async_elem(Q2 + e, y1 + n_x + e);
+        cp_async_elem(Q3 + e, y2 + n_x + e);
+      } else {
+        const int i = e - n_x;
+        cp_async_elem(Z + e, cv(a.uout) + (long long)m * n_u + i);
+        cp_async_elem(Q0 + e, y1 + 2 * n_x + i);
+        cp_async_elem(Q1 + e, y2 + 2 * n_x + i);
+        cp_async_elem(SP + i, cv(a.step_p) + (long long)m * n_u + i);
+        cp_async_elem(IP + i, cv(a.inv_p) + (long long)m * n_u + i);
+      }
+      if (dl) cp_async_elem(WA + e, cv(a.wa) + mk + e);
+    }
+    const AT c = (AT)a.cvec[it], cn = (AT)a.cvec[it + 1];
+    const AT ls = (AT)cv(a.step_s)[m], lz = (AT)cv(a.step_z)[m];
+    const AT mus = (AT)cv(a.mu_s)[m], muz = (AT)a.gamma_d;
+    const AT is = (AT)cv(a.inv_s)[m], iz = (AT)cv(a.inv_z)[m];
+    const ST zero = st_from<ST>(0.0);
+    cp_async_wait_all();
+    // block norms ||lambda r|| of the two distance blocks
+    AT ps = 0, pz = 0;
+#pragma unroll 1
+    for (int e = lane; e < n_x; e += 32) {
+      const AT x = (AT)Z[e];
+      const ST ws = st_extrap(Q0[e], Q1[e], c), wz = st_extrap(Q2[e], Q3[e], c);
+      const ST qs = st_axpy(ws, ls, x - bnd[e]);
+      const AT rs = st_neg(qs) ? (AT)st_val(qs) : (AT)0;
+      const AT rz = (AT)st_val(box_lr(st_axpy(wz, lz, x - bnd[kThreads + e]), st_axpy(wz, lz, x - bnd[2 * kThreads + e])));
+      ps += rs * rs;
+      pz += rz * rz;
+    }
+    ps = warp_sum(ps);
+    pz = warp_sum(pz);
+    const AT ds = sqrt(ps), dz = sqrt(pz);
+    const AT ks = ds > mus ? mus / ds : (AT)1, kz = dz > muz ? muz / dz : (AT)1;
+    AT rm = 0, hm = 0, tm = 0;
+#pragma unroll 1
+    for (int e = lane; e < n_k; e += 32) {
+      const AT wa_e = dl ? (AT)WA[e] : (AT)0;
+      if (e < n_x) {
+        const AT x = (AT)Z[e];
+        const ST v1 = Q0[e], w1 = Q2[e];
+        const ST ws = st_extrap(v1, Q1[e], c), wz = st_extrap(w1, Q3[e], c);
+        const ST qs = st_axpy(ws, ls, x - bnd[e]);
+        const ST ysn = st_scale(st_neg(qs) ? qs : zero, ks);
+        const ST yzn = st_scale(box_lr(st_axpy(wz, lz, x - bnd[kThreads + e]), st_axpy(wz, lz, x - bnd[2 * kThreads + e])), kz);
+        const AT es = (AT)st_val(st_sub(ysn, ws)) * is;
+        const AT ez = (AT)st_val(st_sub(yzn, wz)) * iz;
+        y2[e] = ysn;
+        y2[n_x + e] = yzn;
+        put_w_at(mk + e, st_add(st_extrap(ysn, v1, cn), st_extrap(yzn, w1, cn)), wa_e);
+        rm = fmax(rm, fmax(fabs(es), fabs(ez)));
+        hm = fmax(hm, fabs(x));
+        tm = fmax(tm, fmax(fabs(x - es), fabs(x - ez)));
+        if (!isfinite(st_val(ysn)) || !isfinite(st_val(yzn))) a.flags[1] = SMPC_EDIVERGED;
+      } else {
+        const int i = e - n_x;
+        const AT u = (AT)Z[e];
+        const ST p1 = Q0[e];
+        const ST wp = st_extrap(p1, Q1[e], c);
+        const AT lp = (AT)SP[i];
+        const ST ypn = box_lr(st_axpy(wp, lp, u - bnd[3 * kThreads + i]), st_axpy(wp, lp, u - bnd[4 * kThreads + i]));
+        const AT ep = (AT)st_val(st_sub(ypn, wp)) * (AT)IP[i];
+        y2[2 * n_x + i] = ypn;
+        put_w_at(mk + e, st_extrap(ypn, p1, cn), wa_e);
+        rm = fmax(rm, fabs(ep));
+        hm = fmax(hm, fabs(u));
+        tm = fmax(tm, fabs(u - ep));
+        if (!isfinite(st_val(ypn))) a.flags[1] = SMPC_EDIVERGED;
+      }
+    }
+    rmax = fmax(rmax, (double)rm);
+    hzmax = fmax(hzmax, (double)hm);
+    tmax = fmax(tmax, (double)tm);
+  }
+
   // ---------------------------------------------------------- backward sweep
   // One node's backward step with its pack in slots (K, L):
   //   r += [Bbar; L]' [s; psi];  delta = Lambda r;  h = [Bbar; L] delta.
@@ -1275,6 +1395,7 @@ __device__ bool early_exit(const IterArgs& a, int nu, int mode, int* flag, bool 
 template <typename VT, typename MT>
 __global__ void __launch_bounds__(kThreads, 1)
     apg_iter(const __grid_constant__ IterArgs a, int S, int nu, int mode) {
+  grid_dep_sync();
   extern __shared__ __align__(128) unsigned char smem_raw[];
   Smem<MT> sm = carve<MT>(smem_raw, S, a.n_x, a.n_u, a.n_v);
   if (early_exit(a, nu, mode, sm.flag + 1, true)) return;
@@ -1307,6 +1428,7 @@ size_t fwd_smem_bytes(int n_k) { return (size_t)3 * fwd_chunk<VT>() * n_k * size
 
 template <typename VT, typename MT>
 __global__ void __launch_bounds__(kThreads) fwd_scan(const __grid_constant__ IterArgs a, int nu, int mode) {
+  grid_dep_sync();
   using AT = typename Acc<MT>::T;
   constexpr int KC = fwd_chunk<VT>();
   extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -1368,9 +1490,21 @@ __global__ void __launch_bounds__(kThreads) fwd_scan(const __grid_constant__ Ite
   }
 }
 
+// Per-warp staging of prox_node (warp_prox_staged), 16-byte multiple.
+template <typename VT>
+__host__ __device__ size_t prox_stage_bytes(int n_x, int n_u) {
+  const int n_k = n_x + n_u;
+  return round_up((size_t)(2 * n_k + 2 * n_x) * 8 + (size_t)(2 * n_k + 2 * n_u) * sizeof(VT), 16);
+}
+
+// Phase P, node-parallel: one warp per node.  Dynamic shared memory: the barriers and
+// vectors of carve (no pack slot), then kWarps staging regions (prox_stage_bytes).
 template <typename VT, typename MT>
-__global__ void __launch_bounds__(kThreads, 4) prox_node(const __grid_constant__ IterArgs a, int nu, int mode) {
+__global__ void __launch_bounds__(kThreads, 3) prox_node(const __grid_constant__ IterArgs a, int nu, int mode) {
+  grid_dep_sync();
+  using AT = typename Acc<MT>::T;
   extern __shared__ __align__(128) unsigned char smem_raw[];
+  __shared__ AT bnd[5 * kThreads];  // x_s, x_max, x_min, u_max, u_min
   Smem<MT> sm = carve<MT>(smem_raw, 0, a.n_x, a.n_u, a.n_v);
   // the forward sweep (when there is one) already took the stop decision
   const bool decide = !((mode & MODE_PROX) && nu >= 1);
@@ -1379,8 +1513,28 @@ __global__ void __launch_bounds__(kThreads, 4) prox_node(const __grid_constant__
   const bool do_prox = (mode & MODE_PROX) != 0 && nu >= 1;
   const bool do_bwd = (mode & MODE_BWD) != 0;
   const int warp = threadIdx.x >> 5;
-  for (int m = blockIdx.x * kWarps + warp; m < a.n; m += gridDim.x * kWarps)
-    k.warp_prox(m, do_prox, do_bwd && (!do_prox || k.linear()));
+  if (do_prox && !k.linear()) {
+    const int t = threadIdx.x;
+    if (t < a.n_x) {
+      bnd[t] = (AT)reinterpret_cast<const VT*>(a.x_s)[t];
+      bnd[kThreads + t] = (AT)reinterpret_cast<const VT*>(a.x_max)[t];
+      bnd[2 * kThreads + t] = (AT)reinterpret_cast<const VT*>(a.x_min)[t];
+    }
+    if (t < a.n_u) {
+      bnd[3 * kThreads + t] = (AT)reinterpret_cast<const VT*>(a.u_max)[t];
+      bnd[4 * kThreads + t] = (AT)reinterpret_cast<const VT*>(a.u_min)[t];
+    }
+    __syncthreads();
+    unsigned char* stage = smem_raw + iter_smem_bytes<MT>(0, a.n_x, a.n_u, a.n_v) +
+                           (size_t)warp * prox_stage_bytes<VT>(a.n_x, a.n_u);
+    for (int m = blockIdx.x * kWarps + warp; m < a.n; m += gridDim.x * kWarps) {
+      k.warp_prox_staged(m, bnd, stage);
+      __syncwarp();  // the lanes' reads of the staging are done before the next node's copies
+    }
+  } else {
+    for (int m = blockIdx.x * kWarps + warp; m < a.n; m += gridDim.x * kWarps)
+      k.warp_prox(m, do_prox, do_bwd && (!do_prox || k.linear()));
+  }
   k.reduce_out(do_prox);
 }
 
@@ -1390,6 +1544,7 @@ __global__ void __launch_bounds__(kThreads, 4) prox_node(const __grid_constant__
 template <typename VT>
 __global__ void __launch_bounds__(kThreads) scan_kernel(const __grid_constant__ IterArgs a, int which, int nu,
                                                         int mode) {
+  grid_dep_sync();
   __shared__ int flag[2];
   if (early_exit(a, nu, mode, flag, false)) return;
   const int e = threadIdx.x;
@@ -1472,6 +1627,7 @@ __global__ void __launch_bounds__(kThreads) scan_kernel(const __grid_constant__ 
 // dh: delta = Lambda_n r_n / (2 p_n), h_n = [Bbar; L]_n delta.
 template <typename VT, typename MT, bool DH>
 __global__ void __launch_bounds__(kThreads, 1) node_mv(const __grid_constant__ IterArgs a, int S, int nu, int mode) {
+  grid_dep_sync();
   using AT = typename Acc<MT>::T;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   Smem<MT> sm = carve<MT>(smem_raw, S, a.n_x, a.n_u, a.n_v, DH);
@@ -1757,6 +1913,7 @@ __device__ void multi_t(const MT* A, int R, int C, int ld, const AT* x, int xs, 
 
 template <typename VT, typename MT, bool DH>
 __global__ void __launch_bounds__(kThreads, 1) node_mv_shared(const __grid_constant__ IterArgs a, int nu, int mode) {
+  grid_dep_sync();
   using AT = typename Acc<MT>::T;
   constexpr int V = Vec<MT>::V;
   extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -1926,6 +2083,7 @@ __device__ __forceinline__ int tc_off(int r, int k, int sbo) {
 
 template <typename VT>
 __global__ void __launch_bounds__(128, 1) node_mv_tc(const __grid_constant__ IterArgs a, int tn, int nu, int mode) {
+  grid_dep_sync();
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   __shared__ int flag[2];
   if (early_exit(a, nu, mode, flag, false)) return;
@@ -2088,6 +2246,8 @@ LaunchCfg config_t(const IterArgs& a, int num_sms, int S_max, int schedule) {
     if (ch.stages < 1) c.stages = 0;
   }
   c.smem_prox = iter_smem_bytes<MT>(0, a.n_x, a.n_u, a.n_v);  // barriers + vectors, no pack slot
+  c.smem_pstage = c.smem_prox + (size_t)kWarps * prox_stage_bytes<VT>(a.n_x, a.n_u);
+  if (c.smem_pstage + 5 * kThreads * sizeof(double) + 1024 > (size_t)optin) c.stages = 0;
   c.grid_prox = (a.n + kWarps - 1) / kWarps;  // one warp per node
   if (c.grid_prox > 8 * num_sms) c.grid_prox = 8 * num_sms;
   c.grid_scan = a.n_chains < 4 * num_sms ? a.n_chains : 4 * num_sms;
@@ -2129,6 +2289,23 @@ LaunchCfg config_t(const IterArgs& a, int num_sms, int S_max, int schedule) {
   return c;
 }
 
+// Launch with programmatic dependent launch allowed (dep): the kernel may be scheduled
+// while the stream's previous kernel drains; it calls grid_dep_sync before any access.
+template <typename... KArgs, typename... Args>
+void launch_dep(void (*kern)(KArgs...), int grid, int block, size_t smem, cudaStream_t s, bool dep, Args... args) {
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = dim3((unsigned)grid);
+  cfg.blockDim = dim3((unsigned)block);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = dep ? 1 : 0;
+  cudaLaunchKernelEx(&cfg, kern, args...);
+}
+
 template <typename VT, typename MT>
 int launch_t(const IterArgs& a, const LaunchCfg& c, int nu, int mode, cudaStream_t s) {
   // once per process and instantiation; thread-safe (solves may run on several threads).
@@ -2153,64 +2330,65 @@ int launch_t(const IterArgs& a, const LaunchCfg& c, int nu, int mode, cudaStream
   }();
   (void)attr_set;
   int ev = 0;
+  const bool dep = c.events == nullptr;  // stage events between the kernels would cut the overlap anyway
   auto mark = [&]() {
     if (c.events) cudaEventRecord(c.events[ev++], s);
   };
   mark();
   if (c.schedule == SCHED_CHAIN) {
-    apg_iter<VT, MT><<<c.grid, c.block, c.smem, s>>>(a, c.stages, nu, mode);
+    launch_dep(apg_iter<VT, MT>, c.grid, c.block, c.smem, s, dep, a, c.stages, nu, mode);
     mark();
     return check_launch("apg_iter");
   }
   if ((mode & MODE_PROX) && nu >= 1) {
-    fwd_scan<VT, MT><<<c.grid_fwd, c.block, c.smem_fwd, s>>>(a, nu, mode);
+    launch_dep(fwd_scan<VT, MT>, c.grid_fwd, c.block, c.smem_fwd, s, dep, a, nu, mode);
     mark();
   }
-  prox_node<VT, MT><<<c.grid_prox, c.block, c.smem_prox, s>>>(a, nu, mode);
+  launch_dep(prox_node<VT, MT>, c.grid_prox, c.block, c.smem_pstage, s, dep, a, nu, mode);
   mark();
   if ((mode & MODE_BWD) && c.schedule == SCHED_HYBRID) {
     // s, [Bbar; L]'[s; psi] and r along the chains and up the top nodes, r of every node out
-    apg_iter<VT, MT><<<c.grid_chain, c.block, c.smem_chain, s>>>(a, c.stages_chain, nu,
+    launch_dep(apg_iter<VT, MT>, c.grid_chain, c.block, c.smem_chain, s, dep, a, c.stages_chain, nu,
                                                                  (mode & ~MODE_PROX) | MODE_GT | MODE_WREADY);
     mark();
     if constexpr (std::is_same<MT, __nv_bfloat16>::value) {
       if (c.tc && (mode & MODE_DELTA)) {
-        node_mv_tc<VT><<<c.grid_tc, 128, c.smem_tc, s>>>(a, c.tn, nu, mode);
+        launch_dep(node_mv_tc<VT>, c.grid_tc, 128, c.smem_tc, s, dep, a, c.tn, nu, mode);
       } else if (c.multi_dh) {
-        node_mv_shared<VT, MT, true><<<c.grid_multi, c.block, c.smem_mdh, s>>>(a, nu, mode);
+        launch_dep(node_mv_shared<VT, MT, true>, c.grid_multi, c.block, c.smem_mdh, s, dep, a, nu, mode);
       } else {
-        node_mv<VT, MT, true><<<c.grid_mv, c.block, c.smem_dh, s>>>(a, c.s_dh, nu, mode);
+        launch_dep(node_mv<VT, MT, true>, c.grid_mv, c.block, c.smem_dh, s, dep, a, c.s_dh, nu, mode);
       }
     } else {
       if (c.multi_dh)
-        node_mv_shared<VT, MT, true><<<c.grid_multi, c.block, c.smem_mdh, s>>>(a, nu, mode);
+        launch_dep(node_mv_shared<VT, MT, true>, c.grid_multi, c.block, c.smem_mdh, s, dep, a, nu, mode);
       else
-        node_mv<VT, MT, true><<<c.grid_mv, c.block, c.smem_dh, s>>>(a, c.s_dh, nu, mode);
+        launch_dep(node_mv<VT, MT, true>, c.grid_mv, c.block, c.smem_dh, s, dep, a, c.s_dh, nu, mode);
     }
     mark();
   } else if (mode & MODE_BWD) {
-    scan_kernel<VT><<<c.grid_scan, c.block, 0, s>>>(a, 0, nu, mode);
+    launch_dep(scan_kernel<VT>, c.grid_scan, c.block, 0, s, dep, a, 0, nu, mode);
     mark();
     if (c.multi_gt)
-      node_mv_shared<VT, MT, false><<<c.grid_multi, c.block, c.smem_mgt, s>>>(a, nu, mode);
+      launch_dep(node_mv_shared<VT, MT, false>, c.grid_multi, c.block, c.smem_mgt, s, dep, a, nu, mode);
     else
-      node_mv<VT, MT, false><<<c.grid_mv, c.block, c.smem_gt, s>>>(a, c.s_gt, nu, mode);
+      launch_dep(node_mv<VT, MT, false>, c.grid_mv, c.block, c.smem_gt, s, dep, a, c.s_gt, nu, mode);
     mark();
-    scan_kernel<VT><<<c.grid_scan, c.block, 0, s>>>(a, 1, nu, mode);
+    launch_dep(scan_kernel<VT>, c.grid_scan, c.block, 0, s, dep, a, 1, nu, mode);
     mark();
     if constexpr (std::is_same<MT, __nv_bfloat16>::value) {
       if (c.tc && (mode & MODE_DELTA)) {
-        node_mv_tc<VT><<<c.grid_tc, 128, c.smem_tc, s>>>(a, c.tn, nu, mode);
+        launch_dep(node_mv_tc<VT>, c.grid_tc, 128, c.smem_tc, s, dep, a, c.tn, nu, mode);
       } else if (c.multi_dh) {
-        node_mv_shared<VT, MT, true><<<c.grid_multi, c.block, c.smem_mdh, s>>>(a, nu, mode);
+        launch_dep(node_mv_shared<VT, MT, true>, c.grid_multi, c.block, c.smem_mdh, s, dep, a, nu, mode);
       } else {
-        node_mv<VT, MT, true><<<c.grid_mv, c.block, c.smem_dh, s>>>(a, c.s_dh, nu, mode);
+        launch_dep(node_mv<VT, MT, true>, c.grid_mv, c.block, c.smem_dh, s, dep, a, c.s_dh, nu, mode);
       }
     } else {
       if (c.multi_dh)
-        node_mv_shared<VT, MT, true><<<c.grid_multi, c.block, c.smem_mdh, s>>>(a, nu, mode);
+        launch_dep(node_mv_shared<VT, MT, true>, c.grid_multi, c.block, c.smem_mdh, s, dep, a, nu, mode);
       else
-        node_mv<VT, MT, true><<<c.grid_mv, c.block, c.smem_dh, s>>>(a, c.s_dh, nu, mode);
+        launch_dep(node_mv<VT, MT, true>, c.grid_mv, c.block, c.smem_dh, s, dep, a, c.s_dh, nu, mode);
     }
     mark();
   }

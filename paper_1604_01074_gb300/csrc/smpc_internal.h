@@ -159,6 +159,7 @@ struct LaunchCfg {
   int grid_prox = 1, grid_scan = 1, grid_mv = 1, grid_fwd = 1;
   size_t smem_prox = 0, smem_gt = 0, smem_dh = 0;
   size_t smem_fwd = 0;   // forward sweep: staged node vectors
+  size_t smem_pstage = 0;  // prox: smem_prox plus the per-warp staging of the node data
   int s_gt = 0, s_dh = 0;   // pack slots of the two mat-vec launches (0: does not fit)
   bool multi_gt = false, multi_dh = false;  // shared pack: several nodes per pass over it
   bool tc = false;          // bfloat16 shared pack: Lambda / [Bbar; L] of delta launches on tensor cores
