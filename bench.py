@@ -525,8 +525,17 @@ def profile_solve(args):
     P = make_problem(args.config, seed=0)
     S = Solver(P, prec, device, args.schedule, shared_packs=int(args.shared_packs))
     stream = torch.cuda.current_stream(device)
-    S.solve(S.device_inputs(step_inputs(P, 0)), args.profile_solve, 0.0, stream)
+    inp = S.device_inputs(step_inputs(P, 0))
+    # a warm-up solve, then the profiled one inside a profiler range (ncu --profile-from-start off
+    # captures only its launches, not the factor's power iteration or schedule tuning)
+    S.solve(inp, 20, 0.0, stream)
+    S.finish()
+    torch.cuda.synchronize()
+    torch.cuda.profiler.start()
+    S.solve(inp, args.profile_solve, 0.0, stream)
     info = S.finish()
+    torch.cuda.synchronize()
+    torch.cuda.profiler.stop()
     S.close()
     print(json.dumps({"profile_solve": args.profile_solve, "precision": args.precision, "info": info}))
 
@@ -809,7 +818,8 @@ def main():
     ap.add_argument("--batched-baseline", type=int, default=4)
     ap.add_argument("--shared-packs", action="store_true", help="--profile-solve: one shared pack per factor")
     ap.add_argument("--profile-solve", type=int, default=0,
-                    help="factor + one solve of this many iterations (tol 0) and exit: the case ncu captures")
+                    help="factor, a warm-up solve, then one solve of this many iterations (tol 0) inside a "
+                         "CUDA profiler range, and exit: the case ncu captures (--profile-from-start off)")
     args = ap.parse_args()
     if args.oracle_sample:
         oracle_sample(args.config, args.oracle_sample)
