@@ -107,7 +107,9 @@ def test_closed_loop_steps_warm_start_in_order():
     exactly as consecutive smpc_solve calls on a twin factor do."""
     import paper_1604_01074_gb300 as smpc
     P = synth.random_instance(35, horizon=6, max_children=3)
-    twin, served = H.Gpu(P, precision=1), H.Gpu(P, precision=1)
+    # one pinned schedule for both: the autotuner could pick different (equally valid)
+    # schedules for the two factors, whose float32 results differ in rounding
+    twin, served = H.Gpu(P, precision=1, schedule=2), H.Gpu(P, precision=1, schedule=2)
     server = smpc.smpc_server_create(10 * smpc.smpc_factor_device_bytes(served.fac), 2)
     try:
         rng = np.random.default_rng(5)
