@@ -146,6 +146,11 @@ __device__ __forceinline__ double warp_max(double v) {
   for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
   return v;
 }
+__device__ __forceinline__ float warp_max(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
 
 // ------------------------------------------------------------------ dual state
 // Late in a solve the dual iterates move by lambda (H z - t) per iteration, far
@@ -467,7 +472,10 @@ struct Kern {
   int S, nu, mode;
   int nd;  // dual block 2 n_x + n_u
   bool abort_ = false;
-  double rmax = 0, hzmax = 0, tmax = 0, pnrm = 0, pdot = 0;
+  // residual maxima in the arithmetic type (a maximum rounds nothing; float64 arithmetic
+  // is slow on this GPU), power-iteration sums in float64
+  AT rmax = 0, hzmax = 0, tmax = 0;
+  double pnrm = 0, pdot = 0;
 
   __device__ Kern(const IterArgs& args, Smem<MT>& s, int S_, int nu_, int mode_)
       : a(args), sm(s), S(S_), nu(nu_), mode(mode_), nd(2 * args.n_x + args.n_u) {}
@@ -863,9 +871,9 @@ struct Kern {
       }
       __syncthreads();
     }
-    rmax = fmax(rmax, (double)rm);
-    hzmax = fmax(hzmax, (double)hm);
-    tmax = fmax(tmax, (double)tm);
+    rmax = fmax(rmax, rm);
+    hzmax = fmax(hzmax, hm);
+    tmax = fmax(tmax, tm);
   }
 
   // w^nu of the segment's nodes without a prox (first iteration, power iteration).
@@ -1000,9 +1008,9 @@ struct Kern {
             if (!isfinite(st_val(ypn))) a.flags[1] = SMPC_EDIVERGED;
           }
         }
-        rmax = fmax(rmax, (double)rm);
-        hzmax = fmax(hzmax, (double)hm);
-        tmax = fmax(tmax, (double)tm);
+        rmax = fmax(rmax, rm);
+        hzmax = fmax(hzmax, hm);
+        tmax = fmax(tmax, tm);
       }
     }
     if (do_w) {  // w^nu without a prox (first iteration, power iteration)
@@ -1128,9 +1136,9 @@ struct Kern {
         if (!isfinite(st_val(ypn))) a.flags[1] = SMPC_EDIVERGED;
       }
     }
-    rmax = fmax(rmax, (double)rm);
-    hzmax = fmax(hzmax, (double)hm);
-    tmax = fmax(tmax, (double)tm);
+    rmax = fmax(rmax, rm);
+    hzmax = fmax(hzmax, hm);
+    tmax = fmax(tmax, tm);
   }
 
   // ---------------------------------------------------------- backward sweep
@@ -1319,24 +1327,25 @@ struct Kern {
     const int tid = threadIdx.x;
     const int lane = tid & 31, warp = tid >> 5;
     if (do_prox && !linear()) {
-      const double r = warp_max(rmax), hz = warp_max(hzmax), tt = warp_max(tmax);
+      const AT r = warp_max(rmax), hz = warp_max(hzmax), tt = warp_max(tmax);
+      AT* r3 = reinterpret_cast<AT*>(sm.res3);  // 3 kWarps entries fit in its 3 kWarps doubles
       if (lane == 0) {
-        sm.res3[warp] = r;
-        sm.res3[kWarps + warp] = hz;
-        sm.res3[2 * kWarps + warp] = tt;
+        r3[warp] = r;
+        r3[kWarps + warp] = hz;
+        r3[2 * kWarps + warp] = tt;
       }
       __syncthreads();
       if (tid == 0) {
-        double R = 0, HZ = 0, TT = 0;
+        AT R = 0, HZ = 0, TT = 0;
         for (int w = 0; w < kWarps; ++w) {
-          R = fmax(R, sm.res3[w]);
-          HZ = fmax(HZ, sm.res3[kWarps + w]);
-          TT = fmax(TT, sm.res3[2 * kWarps + w]);
+          R = fmax(R, r3[w]);
+          HZ = fmax(HZ, r3[kWarps + w]);
+          TT = fmax(TT, r3[2 * kWarps + w]);
         }
         unsigned long long* slot = a.res + 3ll * (nu - 1);
-        atomic_max_nonneg(slot + 0, R);
-        atomic_max_nonneg(slot + 1, HZ);
-        atomic_max_nonneg(slot + 2, TT);
+        atomic_max_nonneg(slot + 0, (double)R);
+        atomic_max_nonneg(slot + 1, (double)HZ);
+        atomic_max_nonneg(slot + 2, (double)TT);
       }
     } else if (do_prox && linear()) {
       const double nr = warp_sum(pnrm), dt = warp_sum(pdot);
