@@ -254,6 +254,7 @@ class Solver:
 
         import paper_1604_01074_gb300 as smpc
         self.smpc, self.torch, self.P = smpc, torch, P
+        self.use_graph = 0  # smpc_solve_opts.use_graph for this solver's solves
         t, net = P["tree"], P["net"]
         self.n, self.n_x, self.n_u = len(t["parent"]), net["n_x"], net["n_u"]
         self.tree = smpc.smpc_tree_create(t["parent"], t["prob"])
@@ -286,7 +287,7 @@ class Solver:
         dp = ctypes.POINTER(ctypes.c_double)
         cast = lambda a: None if a is None else ctypes.cast(ctypes.c_void_p(a), dp)  # noqa: E731
         D = smpc.smpc_step_data(cast(p), cast(q), cast(dhat), cast(eps), cast(alpha2))
-        O = smpc.smpc_solve_opts(int(max_iters), float(tol), 0, 64, int(sync))
+        O = smpc.smpc_solve_opts(int(max_iters), float(tol), 0, 64, int(sync), 0, 0, int(self.use_graph))
         R = smpc.smpc_result(self.u.data_ptr(), self.x.data_ptr(), None,
                              None if u0 is None else u0.ctypes.data_as(dp), None, -1, 0.0, 0.0, 0)
         smpc._check(smpc.lib().smpc_solve(self.fac, ctypes.byref(D), ctypes.byref(O), ctypes.byref(R),
@@ -331,6 +332,7 @@ def run_ours(args, rank, world, local_rank):
     prec = {"fp64": 0, "fp32": 1, "bf16": 2}[args.precision]
     P = make_problem(args.config, seed=0)
     S = Solver(P, prec, device, args.schedule)
+    S.use_graph = 0 if args.no_graph else 1  # the warm-up solves capture the chunks, the timed ones replay them
     stream = torch.cuda.current_stream(device)
     n_steps = args.steps + args.warmup
     inputs = [step_inputs(P, k) for k in range(n_steps)]
@@ -428,7 +430,9 @@ def run_ours(args, rank, world, local_rank):
                    "rho_rel", "tol": args.tol, "max_iters": args.max_iters, "precision": args.precision,
                    "packs": "per node", "schedule": {1: "chain", 2: "node-parallel", 3: "hybrid"}[S.schedule],
                    "schedule_tuning_ms": S.tuned_ms,
-                   "l2": "256 MB buffer written between timed solves (L2 flushed)", "parallelism": f"replicas x{world}"},
+                   "l2": "256 MB buffer written between timed solves (L2 flushed)", "parallelism": f"replicas x{world}",
+                   "launch": "plain launches" if args.no_graph else
+                   "64-iteration chunks as CUDA graphs (smpc_solve use_graph; captured by the warm-up solves)"},
         "iterations_mean": float(np.mean(iters)), "apg_iters_per_s": float(np.sum(iters)) / local_s * world,
         "p50_ms": float(np.percentile(times, 50)), "p99_ms": float(np.percentile(times, 99)),
         "roofline": roof, "clocks": clocks, "gpu_launches": launches,
@@ -801,6 +805,7 @@ def main():
     ap.add_argument("--schedule", type=int, choices=[0, 1, 2, 3], default=0,
                     help="iteration schedule: 0 = the factor times both and keeps the faster")
     ap.add_argument("--max-iters", type=int, default=100000)
+    ap.add_argument("--no-graph", action="store_true", help="plain launches instead of CUDA-graph chunks")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-other-precisions", dest="other_legs", action="store_false")
     ap.add_argument("--oracle-sample", type=int, default=0)

@@ -147,6 +147,13 @@ typedef struct smpc_solve_opts {
    * with float32 matrices. */
   int32_t polish_iters;
   int32_t anchor_every;
+  /* 1: enqueue each chunk of check_every iterations as a CUDA graph, captured the
+   * first time the factor runs that chunk with these max_iters, tol, polish_iters and
+   * anchor_every, and replayed by later solves of the factor with the same settings
+   * (the closed loop of Alg. 2 solves every step with the same ones).  A graph that
+   * cannot be captured turns graphs off for the factor (plain launches, same results).
+   * 0: plain launches.  smpc_solve only; smpc_solve_noalloc ignores it. */
+  int32_t use_graph;
 } smpc_solve_opts;
 
 /* Outputs.  Device pointers may be NULL (not copied).  Host outputs are filled

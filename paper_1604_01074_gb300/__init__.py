@@ -47,7 +47,7 @@ class smpc_step_data(ctypes.Structure):
 class smpc_solve_opts(ctypes.Structure):
     _fields_ = [("max_iters", ctypes.c_int32), ("tol", ctypes.c_double), ("warm_start", ctypes.c_int32),
                 ("check_every", ctypes.c_int32), ("sync", ctypes.c_int32), ("polish_iters", ctypes.c_int32),
-                ("anchor_every", ctypes.c_int32)]
+                ("anchor_every", ctypes.c_int32), ("use_graph", ctypes.c_int32)]
 
 
 class smpc_result(ctypes.Structure):
@@ -209,9 +209,11 @@ def smpc_factor_steps(fac, n, n_u):
 
 def smpc_solve(fac, p, q, dhat, alpha2, eps=None, max_iters=500, tol=0.0, warm_start=0, check_every=0, sync=1,
                u=None, x=None, y=None, u0_host=None, history_host=None, stream=None, polish_iters=0,
-               anchor_every=0, _entry="smpc_solve"):
+               anchor_every=0, use_graph=0, _entry="smpc_solve"):
     """u, x, y: optional torch device tensors (or raw device pointers) receiving the outputs.
-    u0_host / history_host: optional numpy float64 arrays filled when sync=1."""
+    u0_host / history_host: optional numpy float64 arrays filled when sync=1.  use_graph=1
+    enqueues each chunk of iterations as a CUDA graph, captured once per chunk and
+    settings and replayed by later solves of the factor."""
     k = _Keep()
 
     def arg(a):  # host array, or an int device address of float64 data
@@ -221,7 +223,7 @@ def smpc_solve(fac, p, q, dhat, alpha2, eps=None, max_iters=500, tol=0.0, warm_s
 
     D = smpc_step_data(arg(p), arg(q), arg(dhat), arg(eps), arg(alpha2))
     O = smpc_solve_opts(int(max_iters), float(tol), int(warm_start), int(check_every), int(sync), int(polish_iters),
-                        int(anchor_every))
+                        int(anchor_every), int(use_graph))
 
     def dptr(t):
         if t is None:

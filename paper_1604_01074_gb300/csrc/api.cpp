@@ -375,6 +375,7 @@ int ensure_capacity(smpc_factor_t* f, int iters) {
   double* cvec = nullptr;
   TRY(f->alloc(&res, sizeof(unsigned long long) * 3 * (size_t)(cap + 2)));
   TRY(f->alloc(&cvec, sizeof(double) * (size_t)(cap + 2)));
+  f->drop_graphs();  // they hold the old buffers' addresses
   f->res = res;
   f->cvec = cvec;
   f->cap = cap;
@@ -582,6 +583,48 @@ int copy_final_y(smpc_factor_t* f, void* dst) {
   IterArgs a = make_args(f);
   TRY(launch_copy_final_y(f->prec, a, 0, dst, nullptr));
   CK(cudaStreamSynchronize(nullptr));
+  return SMPC_OK;
+}
+
+// The iteration kernels' launch of iteration nu of a solve (the tail launch adds the
+// last prox without a backward sweep).
+int chunk_mode(int nu) { return MODE_BWD | MODE_CHECK | (nu > 0 ? MODE_PROX : 0); }
+
+// Iterations [from, to) as one CUDA graph: captured from the planned launches on the
+// factor's capture stream the first time this key is seen, then launched on s.  A
+// capture or instantiation that fails turns graphs off for the factor and launches
+// the chunk directly (the same kernels with the same arguments).
+int launch_chunk_graph(smpc_factor_t* f, IterPlan& plan, int from, int to, const std::array<long long, 6>& key,
+                       cudaStream_t s) {
+  auto it = f->graphs.find(key);
+  if (it == f->graphs.end()) {
+    bool ok = true;
+    if (!f->capture_stream && cudaStreamCreateWithFlags(&f->capture_stream, cudaStreamNonBlocking) != cudaSuccess)
+      ok = false;
+    cudaGraph_t g = nullptr;
+    const int k0 = plan.kernels;
+    if (ok) ok = cudaStreamBeginCapture(f->capture_stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+    if (ok) {
+      int rc = SMPC_OK;
+      for (int nu = from; nu < to && rc == SMPC_OK; ++nu) rc = launch_planned(plan, nu, chunk_mode(nu), f->capture_stream);
+      const cudaError_t e = cudaStreamEndCapture(f->capture_stream, &g);
+      ok = rc == SMPC_OK && e == cudaSuccess && g != nullptr;
+    }
+    const int kernels = plan.kernels - k0;
+    plan.kernels = k0;
+    cudaGraphExec_t x = nullptr;
+    if (ok) ok = cudaGraphInstantiate(&x, g, 0) == cudaSuccess;
+    if (g) cudaGraphDestroy(g);
+    cudaGetLastError();  // a refused capture leaves its error behind
+    if (!ok) {
+      f->graphs_off = true;
+      for (int nu = from; nu < to; ++nu) TRY(launch_planned(plan, nu, chunk_mode(nu), s));
+      return SMPC_OK;
+    }
+    it = f->graphs.emplace(key, smpc_factor_t::ChunkGraph{x, kernels}).first;
+  }
+  CK(cudaGraphLaunch(it->second.exec, s));
+  plan.kernels += it->second.kernels;
   return SMPC_OK;
 }
 
@@ -1062,11 +1105,16 @@ int smpc_solve(smpc_factor_t* f, const smpc_step_data* data, const smpc_solve_op
   const int chunk = opts->check_every > 0 ? opts->check_every : 128;
   int launched = 0, chunks = 0;
   bool stop = false;
+  const bool graphs = opts->use_graph != 0 && !f->profile;
+  long long tol_bits = 0;
+  std::memcpy(&tol_bits, &opts->tol, sizeof tol_bits);
   while (launched < iters && !stop) {
     const int upto = std::min(iters, launched + chunk);
-    for (int nu = launched; nu < upto; ++nu) {
-      int mode = MODE_BWD | MODE_CHECK | (nu > 0 ? MODE_PROX : 0);
-      TRY(launch_planned(plan, nu, mode, s));
+    if (graphs && !f->graphs_off) {
+      TRY(launch_chunk_graph(f, plan, launched, upto, {launched, upto, iters, tol_bits, opts->polish_iters,
+                                                       opts->anchor_every}, s));
+    } else {
+      for (int nu = launched; nu < upto; ++nu) TRY(launch_planned(plan, nu, chunk_mode(nu), s));
     }
     launched = upto;
     const int slot = chunks & 1;

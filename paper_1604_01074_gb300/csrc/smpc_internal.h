@@ -2,8 +2,10 @@
 // the device code (kernels.cu).  Not part of the public ABI.
 #pragma once
 
+#include <array>
 #include <cstddef>
 #include <cstdint>
+#include <map>
 #include <string>
 #include <vector>
 
@@ -297,6 +299,19 @@ struct smpc_factor_t {
   float tuned_ms[4] = {0, 0, 0, 0};  // per schedule: ms per iteration measured when the factor chose
   smpc::Profile* profile = nullptr;  // set while smpc_profile_solve runs
   bool solved_once = false;
+  // captured iteration chunks (use_graph): key {first iteration, end, max_iters, tol bits,
+  // polish_iters, anchor_every} -> executable graph and its kernel count
+  struct ChunkGraph {
+    cudaGraphExec_t exec = nullptr;
+    int kernels = 0;
+  };
+  std::map<std::array<long long, 6>, ChunkGraph> graphs;
+  cudaStream_t capture_stream = nullptr;  // graphs are captured here, launched on the solve's stream
+  bool graphs_off = false;                // a capture failed: plain launches from then on
+  void drop_graphs() {
+    for (auto& kv : graphs) cudaGraphExecDestroy(kv.second.exec);
+    graphs.clear();
+  }
 
   template <typename T>
   int alloc(T** p, size_t bytes) {
@@ -314,6 +329,8 @@ struct smpc_factor_t {
     return SMPC_OK;
   }
   ~smpc_factor_t() {
+    drop_graphs();
+    if (capture_stream) cudaStreamDestroy(capture_stream);
     for (void* p : allocs) cudaFree(p);
     if (flags_host) cudaFreeHost(flags_host);
     for (auto& v : ev)

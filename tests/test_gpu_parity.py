@@ -337,3 +337,30 @@ def test_bf16_shared_tensor_core_solve_full_size():
     assert info["iterations"] <= 1.02 * ref_iters, info["iterations"]
     u64, x64, _ = res[0][1]
     assert H.relerr(u, u64) <= 1e-3 and H.relerr(x, x64) <= 1e-3, (H.relerr(u, u64), H.relerr(x, x64))
+
+
+@pytest.mark.parametrize("precision", [1, 2])
+def test_graph_chunks_match_plain_launches(precision):
+    """use_graph: chunks captured as CUDA graphs (on the first solve) and replayed (on the
+    next) give bit-identical iterates, iteration counts and launch counts to plain launches."""
+    import torch
+    P = synth.random_instance(36, horizon=8, max_children=3)
+    g = H.Gpu(P, precision=precision, schedule=2)
+    try:
+        def run(use_graph):
+            u0 = np.zeros(g.n_u)
+            info = g.smpc.smpc_solve(g.fac, P["p"], P["q"], P["dhat"], P["alpha2"], eps=P["eps"], max_iters=700,
+                                     tol=1e-4, check_every=64, sync=1, u=g.u, x=g.x, y=g.y, u0_host=u0,
+                                     use_graph=use_graph)
+            return info, u0, [t.clone() for t in (g.u, g.x, g.y)]
+        ref = run(0)
+        for rep in range(2):  # capture, then replay
+            got = run(1)
+            assert got[0]["iterations"] == ref[0]["iterations"]
+            assert got[0]["launches"] == ref[0]["launches"]
+            assert got[0]["rho_rel"] == ref[0]["rho_rel"]
+            assert np.array_equal(got[1], ref[1])
+            for a, b in zip(got[2], ref[2]):
+                assert bool(torch.equal(a, b))
+    finally:
+        g.close()
