@@ -12,7 +12,7 @@ import pytest
 
 import synth
 from oracle import (Tree, apg, cost_update, dense_dual_hessian, factor, jacobi_steps,
-                    lipschitz_dense, prox_box, prox_dist, solve_step, theta_sequence)
+                    lipschitz_dense, prox_box, prox_dist, prox_g, solve_step, theta_sequence)
 from tests import dense_reference as dr
 
 
@@ -337,6 +337,56 @@ def test_jacobi_lipschitz_bounds_step():
 
 
 # ---------------------------------------------------------------- the pins notice planted mistakes
+# ---------------------------------------------------------------- dual rate (Sec. IV-A)
+def dual_value(P, y, mu_s):
+    """D(y) = min_z f(z) + <y, H z> - g*(y), with z(y) from the dense KKT solve and the
+    conjugates of the three blocks of g: <y, x_s> on y <= 0 with ||y|| <= mu_S (safety
+    distance to {x >= x_s}), the support function of [x_min, x_max] with ||y|| <= gamma_d,
+    and the support function of [u_min, u_max] (input box).  Also returns how far y is
+    from the domain of g* (0 inside)."""
+    cost, tree = P["cost"], P["tree"]
+    ys, yz, yp = y
+    x, u = dr.kkt_solve(P, y)
+    Q, c, _, _ = dr.quadratic_data(P)
+    z = np.concatenate([x.ravel(), u.ravel()])
+    f = 0.5 * z @ Q @ z + c @ z + tree["prob"][0] * P["q"] @ cost["W_u"] @ P["q"]
+    lin = np.sum(ys * x) + np.sum(yz * x) + np.sum(yp * u)
+    gs = np.sum(ys * cost["x_s"])
+    gz = np.sum(np.maximum(yz * cost["x_min"], yz * cost["x_max"]))
+    gp = np.sum(np.maximum(yp * cost["u_min"], yp * cost["u_max"]))
+    out = max(ys.max(), (np.linalg.norm(ys, axis=1) / mu_s).max() - 1.0,
+              (np.linalg.norm(yz, axis=1) / cost["gamma_d"]).max() - 1.0, 0.0)
+    return f + lin - gs - gz - gp, out
+
+
+def _dual_rate_setup(P):
+    tree, fac, cu = build(P)
+    M = dense_dual_hessian(fac, tree)
+    L = np.linalg.eigvalsh(0.5 * (M + M.T)).max()
+    return tree, fac, cu, L, tree.prob * P["cost"]["W_x"]
+
+
+@pytest.mark.parametrize("mk", INSTANCES[:2])
+def test_apg_dual_rate_and_zero_duality_gap(mk):
+    """With the scalar step 1/L_D the iteration is the accelerated proximal gradient method
+    on the dual: D* - D(y^nu) <= 2 L_D ||y^0 - y*||^2 / (nu + 1)^2.  Every iterate lies in
+    the domain of g*, and at the solution the dual value meets the primal objective."""
+    P = mk()
+    tree, fac, cu, L, mu_s = _dual_rate_setup(P)
+    R = apg(fac, tree, cu, P["cost"], P["p"], 1.0 / L, 20000)
+    d_star, out = dual_value(P, R.y, mu_s)
+    assert out < 1e-12
+    primal = dr.objective(P, R.x, R.u, mu_s)
+    assert abs(primal - d_star) <= 1e-4 * (1 + abs(d_star))       # strong duality
+    r2 = sum(np.sum(a ** 2) for a in R.y)                          # y^0 = 0
+    for nu in (5, 20, 80, 320, 1280):
+        Rn = apg(fac, tree, cu, P["cost"], P["p"], 1.0 / L, nu)
+        d, out = dual_value(P, Rn.y, mu_s)
+        assert out < 1e-12, nu
+        assert d <= primal + 1e-9 * (1 + abs(primal)), nu          # weak duality
+        assert d_star - d <= 2 * L * r2 / (nu + 1) ** 2, nu
+
+
 def test_pins_catch_planted_mistakes():
     P = synth.random_instance(2)         # branching tree: probabilities below one
     tree, fac, cu = build(P)
@@ -375,6 +425,21 @@ def test_pins_catch_planted_mistakes():
     v = np.array([3.0, -2.0, 0.5]); Pv = np.maximum(v, 1.0); gm = 0.7
     far = v + (Pv - v) / np.linalg.norm(Pv - v)
     assert np.abs(far - brute_prox_dist(v, Pv, gm)).max() > 1e-3
+    # the extrapolation dropped (plain proximal gradient on the dual) breaks the O(1/nu^2) bound
+    Pt = synth.tiny(0)
+    tree_t, fac_t, cu_t, L, mu_t = _dual_rate_setup(Pt)
+    R = apg(fac_t, tree_t, cu_t, Pt["cost"], Pt["p"], 1.0 / L, 20000)
+    d_star = dual_value(Pt, R.y, mu_t)[0]
+    r2 = sum(np.sum(a ** 2) for a in R.y)
+    lam, n = 1.0 / L, tree_t.n
+    y = [np.zeros((n, fac_t.n_x)), np.zeros((n, fac_t.n_x)), np.zeros((n, fac_t.n_u))]
+    nu = 320
+    for _ in range(nu):
+        x, u = solve_step(fac_t, tree_t, cu_t, *y, Pt["p"])
+        t_s, t_z, t_p = prox_g(y[0] / lam + x, y[1] / lam + x, y[2] / lam + u, Pt["cost"], mu_t,
+                               np.full(n, lam), np.full(n, lam))
+        y = [y[0] + lam * (x - t_s), y[1] + lam * (x - t_z), y[2] + lam * (u - t_p)]
+    assert d_star - dual_value(Pt, y, mu_t)[0] > 2 * L * r2 / (nu + 1) ** 2
     # theta with the wrong sign fails the identity
     a = 0.5
     b = 0.5 * (np.sqrt(a ** 4 + 4 * a ** 2) + a ** 2)
