@@ -364,3 +364,26 @@ def test_graph_chunks_match_plain_launches(precision):
                 assert bool(torch.equal(a, b))
     finally:
         g.close()
+
+
+def test_graph_chunks_full_size_bench_configuration():
+    """The launch configuration bench.py times (2081-node tree, float32 per-node packs,
+    schedule by timing, 64-iteration chunks as CUDA graphs) gives bit-identical iterates
+    to plain launches, whose parity with the oracle the other full-size tests check."""
+    import torch
+    P = synth.barcelona(0)
+    g = H.Gpu(P, precision=1)
+    try:
+        def run(use_graph):
+            info = g.smpc.smpc_solve(g.fac, P["p"], P["q"], P["dhat"], P["alpha2"], eps=P["eps"], max_iters=300,
+                                     tol=0.0, check_every=64, sync=1, u=g.u, x=g.x, y=g.y, use_graph=use_graph)
+            return info, [t.clone() for t in (g.u, g.x, g.y)]
+        ref = run(0)
+        for _ in range(2):  # capture, then replay
+            got = run(1)
+            assert got[0]["iterations"] == ref[0]["iterations"] == 300
+            assert got[0]["rho_rel"] == ref[0]["rho_rel"]
+            for a, b in zip(got[1], ref[1]):
+                assert bool(torch.equal(a, b))
+    finally:
+        g.close()
