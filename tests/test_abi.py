@@ -77,3 +77,37 @@ def test_valid_tree_without_device_is_a_cuda_error(lib):
     with pytest.raises(smpc.SmpcError) as ei:
         smpc.smpc_tree_create(np.asarray([-1, 0, 0], np.int32))
     assert ei.value.code == smpc.SMPC_ECUDA
+
+
+def test_binding_structs_match_the_header_layout(tmp_path):
+    """Every ctypes mirror of a struct in include/smpc.h has the C compiler's size and field
+    offsets (a field added, dropped or reordered on one side only fails here)."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    structs = [smpc.smpc_network, smpc.smpc_cost, smpc.smpc_factor_opts, smpc.smpc_step_data,
+               smpc.smpc_solve_opts, smpc.smpc_result, smpc.smpc_tree_info]
+    cname = {"lambda_": "lambda"}  # Python keyword
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "smpc.h"', "int main(void) {"]
+    for s in structs:
+        t = s.__name__
+        lines.append(f'  printf("{t} sizeof %zu\\n", sizeof({t}));')
+        for name, _ in s._fields_:
+            c = cname.get(name, name)
+            lines.append(f'  printf("{t} {name} %zu\\n", offsetof({t}, {c}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-std=c99", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = {}
+    for line in subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.splitlines():
+        t, field, val = line.split()
+        got[(t, field)] = int(val)
+    for s in structs:
+        t = s.__name__
+        assert got[(t, "sizeof")] == ctypes.sizeof(s), t
+        for name, _ in s._fields_:
+            assert got[(t, name)] == getattr(s, name).offset, (t, name)
