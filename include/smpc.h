@@ -152,7 +152,9 @@ typedef struct smpc_solve_opts {
    * anchor_every, and replayed by later solves of the factor with the same settings
    * (the closed loop of Alg. 2 solves every step with the same ones).  A graph that
    * cannot be captured turns graphs off for the factor (plain launches, same results).
-   * 0: plain launches.  smpc_solve only; smpc_solve_noalloc ignores it. */
+   * Each graph is kept until the factor is destroyed (or its iteration buffers grow), so
+   * solves with many different settings accumulate graphs: one per chunk and setting.
+   * 0: plain launches.  smpc_solve only; smpc_solve_static ignores it. */
   int32_t use_graph;
 } smpc_solve_opts;
 
