@@ -6,6 +6,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -321,6 +322,7 @@ IterArgs make_args(const smpc_factor_t* f) {
   a.res = f->res;
   a.counters = f->counters;
   a.flags = f->flags;
+  a.wait_ns = f->wait_ns;
   return a;
 }
 
@@ -805,6 +807,14 @@ int smpc_factor(const smpc_tree* tree, const smpc_network* net, const smpc_cost*
   f->ms = mat_size(f->prec);
   f->W_alpha = cost->W_alpha;
   f->gamma_d = cost->gamma_d;
+  // Diagnostics: SMPC_PIPELINE_WAIT_NS (a positive count of nanoseconds) replaces the 2 s
+  // bound of node_mv's pack-pipeline waits for this factor's solves, so that a test can
+  // make a wait give up (SMPC_ETIMEOUT) without a fault; the waits that let copies in
+  // flight land keep the 2 s bound.
+  if (const char* w = std::getenv("SMPC_PIPELINE_WAIT_NS")) {
+    const unsigned long long v = std::strtoull(w, nullptr, 10);
+    if (v > 0) f->wait_ns = v;
+  }
   const int n = f->n, n_k = f->n_k, nd = f->nd;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&f->num_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
@@ -1053,6 +1063,12 @@ int smpc_solve(smpc_factor_t* f, const smpc_step_data* data, const smpc_solve_op
   const int iters = opts->max_iters;
   TRY(ensure_capacity(f, iters + 1));
   TRY(upload_cvec(f, iters + 1));
+  // the launch plan (and its option checks) before any device work, so that a call
+  // refused for its options leaves the factor's duals as they were
+  IterArgs a = make_args(f);
+  a.tol = opts->tol;
+  IterPlan plan;
+  TRY(plan_iters(f, a, *opts, &plan));
   // step data -> device (Alg. 2 steps 1-2)
   CK(cudaMemcpyAsync(f->d_p, data->p, sizeof(double) * f->R * n_x, cudaMemcpyDefault, s));
   CK(cudaMemcpyAsync(f->d_q, data->q, sizeof(double) * f->R * n_u, cudaMemcpyDefault, s));
@@ -1091,8 +1107,6 @@ int smpc_solve(smpc_factor_t* f, const smpc_step_data* data, const smpc_solve_op
   c.e = f->e;
   c.beta = f->beta;
   TRY(launch_cost_update(f->prec, c, s));
-  IterArgs a = make_args(f);
-  a.tol = opts->tol;
   TRY(launch_init_duals(f->prec, a, (opts->warm_start && f->solved_once) ? 1 : 0, s));
   // arrival counters are reset by the CTAs that consume them; a solve that was cut
   // short by a device error may leave some behind
@@ -1100,8 +1114,6 @@ int smpc_solve(smpc_factor_t* f, const smpc_step_data* data, const smpc_solve_op
   CK(cudaMemsetAsync(f->flags, 0xff, sizeof(int), s));
   CK(cudaMemsetAsync(f->flags + 1, 0, sizeof(int), s));
   CK(cudaMemsetAsync(f->res, 0, sizeof(unsigned long long) * 3 * (size_t)(iters + 2), s));
-  IterPlan plan;
-  TRY(plan_iters(f, a, *opts, &plan));
   const int chunk = opts->check_every > 0 ? opts->check_every : 128;
   int launched = 0, chunks = 0;
   bool stop = false;
@@ -1131,6 +1143,7 @@ int smpc_solve(smpc_factor_t* f, const smpc_step_data* data, const smpc_solve_op
   if (res->u) CK(cudaMemcpyAsync(res->u, f->uout, (size_t)n * n_u * f->vs, cudaMemcpyDefault, s));
   if (res->x) CK(cudaMemcpyAsync(res->x, f->xout, (size_t)n * n_x * f->vs, cudaMemcpyDefault, s));
   f->solved_once = true;
+  f->last_static = false;
   f->last_stream = s;
   f->last_launches = 6 + plan.kernels + 1;  // convert, 3 cost update, init, iterations and tail, final y
   res->launches = f->last_launches;
@@ -1195,6 +1208,10 @@ int smpc_solve_info(smpc_factor_t* f, smpc_result* res) {
   }
   if (!f->solved_once) {
     set_error("no solve to complete");
+    return SMPC_EINVAL;
+  }
+  if (f->last_static) {
+    set_error("the factor's last solve ran through smpc_solve_static, whose host outputs come with opts->sync = 1");
     return SMPC_EINVAL;
   }
   const int n_u = f->n_u;

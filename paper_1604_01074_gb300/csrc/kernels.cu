@@ -115,12 +115,14 @@ __device__ __forceinline__ uint64_t global_ns() {
   asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
   return t;
 }
-// Wait for phase `parity` of barrier b; gives up after kWaitNs and returns false.
-__device__ bool mbar_wait(uint64_t* b, uint32_t parity) {
+// Wait for phase `parity` of barrier b; gives up after limit_ns and returns false.
+// Waits that let copies already in flight land before a CTA leaves always take the
+// long bound kWaitNs.
+__device__ bool mbar_wait(uint64_t* b, uint32_t parity, uint64_t limit_ns = kWaitNs) {
   if (mbar_test(b, parity)) return true;
   const uint64_t t0 = global_ns();
   while (!mbar_test(b, parity)) {
-    if (global_ns() - t0 > kWaitNs) return false;
+    if (global_ns() - t0 > limit_ns) return false;
   }
   return true;
 }
@@ -595,20 +597,33 @@ struct Kern {
       if (!gt()) issue_l(p);
     }
   }
-  // wait for the next K (resp. Lambda) load; returns its slot; sets abort_ on timeout
+  // wait for the next K (resp. Lambda) load; returns its slot; sets abort_ on timeout,
+  // leaving the load counted as in flight so that drain() waits for it
   __device__ int wait_k(Pipe& p) {
     const int slot = p.kuse % S;
     const bool ok = mbar_wait(&sm.barK[slot], (p.kuse / S) & 1);
+    if (__syncthreads_or(!ok)) {
+      fail();
+      return slot;
+    }
     ++p.kuse;
-    if (__syncthreads_or(!ok)) fail();
     return slot;
   }
   __device__ int wait_l(Pipe& p) {
     const int slot = p.luse % S;
     const bool ok = mbar_wait(&sm.barL[slot], (p.luse / S) & 1);
+    if (__syncthreads_or(!ok)) {
+      fail();
+      return slot;
+    }
     ++p.luse;
-    if (__syncthreads_or(!ok)) fail();
     return slot;
+  }
+  // after a timeout: every copy this CTA issued lands (long bound) before it leaves
+  __device__ void drain(Pipe& p) {
+    for (; p.kuse < p.kiss; ++p.kuse) mbar_wait(&sm.barK[p.kuse % S], (p.kuse / S) & 1);
+    for (; p.luse < p.liss; ++p.luse) mbar_wait(&sm.barL[p.luse % S], (p.luse / S) & 1);
+    __syncthreads();
   }
   // let every issued copy land (bounded), forget them, and restart issuing at `next`
   __device__ void flush(Pipe& p, Cursor next) {
@@ -1319,6 +1334,7 @@ struct Kern {
       if (par >= 0 && arrive(par)) process_top(p, par, chain_cursor(ch + gridDim.x));
     }
 
+    if (abort_) drain(p);
     reduce_out(do_prox);
   }
 
@@ -1680,7 +1696,7 @@ __global__ void __launch_bounds__(kThreads, 1) node_mv(const __grid_constant__ I
     } else if (tid < a.n_k) {
       sm.yv[tid] = tid < a.n_x ? (AT)sp[m * a.n_x + tid] : (AT)wb[m * a.n_k + tid];
     }
-    const bool ok = (shared && q > 0) || mbar_wait(&sm.barK[slot], shared ? 0 : (q / S) & 1);
+    const bool ok = (shared && q > 0) || mbar_wait(&sm.barK[slot], shared ? 0 : (q / S) & 1, a.wait_ns);
     if (__syncthreads_or(!ok)) {
       failed_at = q;
       break;

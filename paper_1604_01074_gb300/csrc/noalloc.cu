@@ -149,6 +149,12 @@ extern "C" int smpc_solve_static(smpc_factor_t* f, const smpc_step_data* data, c
     return SMPC_ENOTSUP;
   }
   cudaStream_t s = static_cast<cudaStream_t>(stream);
+  // a stream under capture only records the table kernel: the table is then written
+  // whenever the graph runs, so such a call always records it and leaves the recorded
+  // length unknown
+  cudaStreamCaptureStatus capture = cudaStreamCaptureStatusNone;
+  SCK(cudaStreamIsCapturing(s, &capture));
+  const bool capturing = capture != cudaStreamCaptureStatusNone;
   unsigned char* base = nullptr;
   bool need_theta = false;
   {
@@ -166,60 +172,16 @@ extern "C" int smpc_solve_static(smpc_factor_t* f, const smpc_step_data* data, c
       st.ready = true;
     }
     base = st.base;
-    need_theta = st.theta_len < iters + 3;
-    // the regions behind the table move with the iteration count: only this call's
-    // table length is known to survive it
-    st.theta_len = iters + 3;
+    need_theta = capturing || st.theta_len < iters + 3;
   }
   double* cvec = reinterpret_cast<double*>(base + L.cvec);
   unsigned long long* resv = reinterpret_cast<unsigned long long*>(base + L.res);
   int* counters = reinterpret_cast<int*>(base + L.counters);
   int* flags = reinterpret_cast<int*>(base + L.flags);
-  if (need_theta) {
-    theta_table_kernel<<<1, 1, 0, s>>>(cvec, iters + 3);
-    SCK(cudaGetLastError());
-  }
-  // step data -> the factor's device buffers (no allocation)
-  SCK(cudaMemcpyAsync(f->d_p, data->p, sizeof(double) * f->R * n_x, cudaMemcpyDefault, s));
-  SCK(cudaMemcpyAsync(f->d_q, data->q, sizeof(double) * f->R * n_u, cudaMemcpyDefault, s));
-  if (n_d) SCK(cudaMemcpyAsync(f->d_dhat, data->dhat, sizeof(double) * (size_t)N * n_d, cudaMemcpyDefault, s));
-  if (data->eps && n_d)
-    SCK(cudaMemcpyAsync(f->d_eps, data->eps, sizeof(double) * (size_t)n * n_d, cudaMemcpyDefault, s));
-  SCK(cudaMemcpyAsync(f->d_alpha2, data->alpha2, sizeof(double) * (size_t)N * n_u, cudaMemcpyDefault, s));
-  STRY(launch_convert(f->prec, f->d_p, f->p0, (long long)f->R * n_x, s));
-  CostArgs c;
-  std::memset(&c, 0, sizeof c);
-  c.n = n;
-  c.N = N;
-  c.n_x = n_x;
-  c.n_u = n_u;
-  c.n_d = n_d;
-  c.n_v = f->n_v;
-  c.parent = f->tree->dev.parent;
-  c.stage = f->tree->dev.row;
-  c.tree_of = f->tree->dev.tree_of;
-  c.child_begin = f->tree->dev.child_begin;
-  c.child_count = f->tree->dev.child_count;
-  c.prob = f->tree->dev.prob;
-  c.pbar = f->tree->dev.pbar;
-  c.Pu = f->Pu;
-  c.Pe = f->Pe;
-  c.Rhat = f->Rhat;
-  c.L = f->L;
-  c.alpha1 = f->alpha1;
-  c.W_alpha = f->W_alpha;
-  c.dhat = f->d_dhat;
-  c.eps = f->d_eps;
-  c.alpha2 = f->d_alpha2;
-  c.q = f->d_q;
-  c.uhat64 = f->uhat64;
-  c.abar = f->abar;
-  c.uhat = f->uhat;
-  c.e = f->e;
-  c.beta = f->beta;
-  STRY(launch_cost_update(f->prec, c, s));
 
-  // iteration-kernel arguments: the factor's state, the scratch from the static array
+  // iteration-kernel arguments: the factor's state, the scratch from the static array.
+  // The launch plan (with its option checks) comes before any device work, so that a
+  // call refused for its options leaves the factor's duals as they were.
   const smpc_tree* t = f->tree;
   IterArgs a{};
   std::memset(&a, 0, sizeof a);
@@ -274,17 +236,72 @@ extern "C" int smpc_solve_static(smpc_factor_t* f, const smpc_step_data* data, c
   a.cvec = cvec;
   a.res = resv;
   a.counters = counters;
-  // warm start reads the factor's own record of its last final iterate
-  a.flags = f->flags;
-  STRY(launch_init_duals(f->prec, a, (opts->warm_start && f->solved_once) ? 1 : 0, s));
   a.flags = flags;
+  a.wait_ns = f->wait_ns;
+  IterPlan plan;
+  STRY(plan_iters(f, a, *opts, &plan));
+
+  if (need_theta) {
+    theta_table_kernel<<<1, 1, 0, s>>>(cvec, iters + 3);
+    SCK(cudaGetLastError());
+  }
+  {
+    // the regions behind the table move with the iteration count: only this call's table
+    // length is known to survive it, and only once its table launch has been enqueued
+    std::lock_guard<std::mutex> lock(g_mutex);
+    g_dev[dev].theta_len = capturing ? 0 : iters + 3;
+  }
+  // step data -> the factor's device buffers (no allocation)
+  SCK(cudaMemcpyAsync(f->d_p, data->p, sizeof(double) * f->R * n_x, cudaMemcpyDefault, s));
+  SCK(cudaMemcpyAsync(f->d_q, data->q, sizeof(double) * f->R * n_u, cudaMemcpyDefault, s));
+  if (n_d) SCK(cudaMemcpyAsync(f->d_dhat, data->dhat, sizeof(double) * (size_t)N * n_d, cudaMemcpyDefault, s));
+  if (data->eps && n_d)
+    SCK(cudaMemcpyAsync(f->d_eps, data->eps, sizeof(double) * (size_t)n * n_d, cudaMemcpyDefault, s));
+  SCK(cudaMemcpyAsync(f->d_alpha2, data->alpha2, sizeof(double) * (size_t)N * n_u, cudaMemcpyDefault, s));
+  STRY(launch_convert(f->prec, f->d_p, f->p0, (long long)f->R * n_x, s));
+  CostArgs c;
+  std::memset(&c, 0, sizeof c);
+  c.n = n;
+  c.N = N;
+  c.n_x = n_x;
+  c.n_u = n_u;
+  c.n_d = n_d;
+  c.n_v = f->n_v;
+  c.parent = f->tree->dev.parent;
+  c.stage = f->tree->dev.row;
+  c.tree_of = f->tree->dev.tree_of;
+  c.child_begin = f->tree->dev.child_begin;
+  c.child_count = f->tree->dev.child_count;
+  c.prob = f->tree->dev.prob;
+  c.pbar = f->tree->dev.pbar;
+  c.Pu = f->Pu;
+  c.Pe = f->Pe;
+  c.Rhat = f->Rhat;
+  c.L = f->L;
+  c.alpha1 = f->alpha1;
+  c.W_alpha = f->W_alpha;
+  c.dhat = f->d_dhat;
+  c.eps = f->d_eps;
+  c.alpha2 = f->d_alpha2;
+  c.q = f->d_q;
+  c.uhat64 = f->uhat64;
+  c.abar = f->abar;
+  c.uhat = f->uhat;
+  c.e = f->e;
+  c.beta = f->beta;
+  STRY(launch_cost_update(f->prec, c, s));
+
+  {
+    // warm start reads the factor's own record of its last final iterate
+    IterArgs ai = a;
+    ai.flags = f->flags;
+    STRY(launch_init_duals(f->prec, ai, (opts->warm_start && f->solved_once) ? 1 : 0, s));
+  }
   // what must start at zero (the array keeps the previous call's contents)
   SCK(cudaMemsetAsync(counters, 0, sizeof(int) * (size_t)n, s));
   SCK(cudaMemsetAsync(flags, 0xff, sizeof(int), s));
   SCK(cudaMemsetAsync(flags + 1, 0, sizeof(int), s));
   SCK(cudaMemsetAsync(resv, 0, sizeof(unsigned long long) * 3 * ((size_t)iters + 2), s));
-  IterPlan plan;
-  STRY(plan_iters(f, a, *opts, &plan));
   const int chunk = opts->check_every > 0 ? opts->check_every : 128;
   int launched = 0, chunks = 0;
   bool stop = false;
@@ -309,6 +326,7 @@ extern "C" int smpc_solve_static(smpc_factor_t* f, const smpc_step_data* data, c
   if (res->u) SCK(cudaMemcpyAsync(res->u, f->uout, (size_t)n * n_u * f->vs, cudaMemcpyDefault, s));
   if (res->x) SCK(cudaMemcpyAsync(res->x, f->xout, (size_t)n * n_x * f->vs, cudaMemcpyDefault, s));
   f->solved_once = true;
+  f->last_static = true;
   f->last_stream = s;
   f->last_launches = 6 + plan.kernels + 1 + (need_theta ? 1 : 0);
   res->launches = f->last_launches;

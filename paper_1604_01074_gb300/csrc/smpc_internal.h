@@ -132,6 +132,7 @@ struct IterArgs {
   double tol;
   double* pw;                    // power iteration: [k] ||y_k||^2, [K + k] <y_k, y_{k+1}>
   int pw_len;
+  unsigned long long wait_ns;    // bound of the per-node pack pipeline waits of node_mv
 };
 
 enum KernelMode : int {
@@ -299,6 +300,10 @@ struct smpc_factor_t {
   float tuned_ms[4] = {0, 0, 0, 0};  // per schedule: ms per iteration measured when the factor chose
   smpc::Profile* profile = nullptr;  // set while smpc_profile_solve runs
   bool solved_once = false;
+  unsigned long long wait_ns = 2000000000ull;  // IterArgs::wait_ns (SMPC_PIPELINE_WAIT_NS)
+  // the factor's last solve ran through smpc_solve_static: its residual history and stop
+  // flags live in the static scratch, not in res / flags, so smpc_solve_info refuses it
+  bool last_static = false;
   // captured iteration chunks (use_graph): key {first iteration, end, max_iters, tol bits,
   // polish_iters, anchor_every} -> executable graph and its kernel count
   struct ChunkGraph {
@@ -320,6 +325,7 @@ struct smpc_factor_t {
     void* q = nullptr;
     const cudaError_t e = cudaMalloc(&q, bytes);
     if (e != cudaSuccess) {
+      cudaGetLastError();  // not sticky: clear it so that later launch checks do not see it
       smpc::set_error("cudaMalloc(%zu) failed: %s", bytes, cudaGetErrorString(e));
       return e == cudaErrorMemoryAllocation ? SMPC_ENOMEM : SMPC_ECUDA;
     }

@@ -58,6 +58,21 @@ def oracle_power_lambda(fac, tree, steps_unit, iters=60, seed=0):
     return lam
 
 
+def full_size_steps(P, power_iters=40):
+    """Steps computed on the oracle side without a dense Hessian: the closed-form Jacobi
+    diagonal and lambda = 1 / (1.02 L), L from a power iteration of Algorithm 1."""
+    tree, fac, _ = oracle_build(P)
+    unit = closed_form_steps(fac, tree, 1.0)
+    lam = 1.0 / (1.02 * oracle_power_lambda(fac, tree, unit, iters=power_iters))
+    return closed_form_steps(fac, tree, lam)
+
+
+def coupling_residual(P, u):
+    """max |E u_n + E_d d_n| over the nodes (the demand coupling of eq. demand-control)."""
+    d = P["dhat"][P["tree"]["stage"]] + P["eps"]
+    return float(np.abs(u @ P["net"]["E"].T + d @ P["net"]["Ed"].T).max())
+
+
 def oracle_run(P, steps, iters, y0=None):
     tree, fac, cu = oracle_build(P)
     return oracle.apg(fac, tree, cu, P["cost"], P["p"], steps, iters, y0=y0)
