@@ -1,6 +1,8 @@
 """Benchmark: SMPC solves/s to a 1e-3 relative primal-dual residual on the
 Barcelona-shaped synthetic network (n_x = 63, n_u = 114, n_d = 88, n_e = 17,
-horizon 24, branching [5, 5, 2, 2] -> 100 scenarios, 2081 nodes).
+horizon 24).  Default workload: the large tree, branching [10, 10, 10] ->
+1000 scenarios, 21 111 nodes, float32 per-node packs; the 2081-node tree
+(branching [5, 5, 2, 2], 100 scenarios) runs as a leg.
 
 One step = one SMPC solve: cost update on the device, then APG iterations until
 rho_rel <= 1e-3 (or the cap), cold start y^0 = 0, on one MPC step's synthetic
@@ -11,6 +13,7 @@ inputs (state, forecast, prices differ from step to step).
 Prints one JSON line (rank 0).  Under torchrun every rank solves its own copy of
 the workload (replicas: scaling "weak"); the timed region is bracketed by a
 barrier and a device synchronize on both sides and the max time over ranks is used.
+Without torchrun, --gpus N > 1 starts N ranks itself (torch.distributed.run).
 """
 from __future__ import annotations
 
@@ -20,6 +23,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -29,8 +33,15 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 METRIC = "SMPC solves/sec and ms per solve to 1e-3 primal-dual residual; APG iters/s; p50/p99"
-WORKLOAD = "Barcelona-shaped single tree: n_x=63, n_u=114, n_d=88, n_e=17, N=24, branching [5,5,2,2] -> 100 scenarios, 2081 nodes"
+WORKLOADS = {
+    "large": "Barcelona-shaped large tree: n_x=63, n_u=114, n_d=88, n_e=17, N=24, branching [10,10,10] -> "
+             "1000 scenarios, 21111 nodes",
+    "barcelona": "Barcelona-shaped single tree: n_x=63, n_u=114, n_d=88, n_e=17, N=24, branching [5,5,2,2] -> "
+                 "100 scenarios, 2081 nodes",
+    "tiny": "tiny: 4 tanks, 6 actuators, N=4, branching [2,2,2,1] -> 8 scenarios, 15 nodes",
+}
 PREC_NAMES = {0: "f64", 1: "f32", 2: "bf16"}
+PREC_KEYS = {0: "fp64", 1: "fp32", 2: "bf16"}
 
 
 def peaks():
@@ -41,8 +52,8 @@ def peaks():
     return 6800.0, "fallback"
 
 
-# Measured on a GB300 of this machine with a chain-of-FMA microbenchmark (152 SMs x 8
-# blocks x 256 threads, 8 independent chains per thread): float64 FMA throughput.
+# float64 FMA throughput of the GB300, measured live by smpc_fma_peak (the library's
+# chain-of-FMA diagnostic); this value is used only when that call fails.
 FP64_FMA_TFLOPS = 1.157
 
 
@@ -133,31 +144,75 @@ def stage_bytes(stage, n, n_x, n_u, n_v, prec, shared):
     return None
 
 
+def stage_flops(stage, n, n_x, n_u, n_v):
+    """Flops of one launch of a pack-reading kernel: 2 per matrix entry applied."""
+    n_k = n_x + n_u
+    if stage in ("node_mv_gt", "apg_iter_gt"):
+        return n * 2 * n_k * n_v
+    if stage == "node_mv_dh":
+        return n * 2 * (n_k * n_v + n_v * n_v)
+    return None
+
+
 # --------------------------------------------------------------------- CPU oracle leg
-def oracle_sample(config, iters):
-    """Times the FP64 oracle (as it stands) for `iters` APG iterations; JSON to stdout."""
+def oracle_sample(config, iters, step=0, start_at=0.0):
+    """Times the FP64 oracle (as it stands) for `iters` APG iterations on MPC step
+    `step`'s inputs of the workload; JSON to stdout.  With start_at (a wall-clock time),
+    the timed part waits for it, so that processes started together time together."""
     import oracle
     P = make_problem(config)
+    P.update(step_inputs(P, step))
     tree = oracle.Tree(P["tree"]["parent"], P["tree"]["prob"])
     fac = oracle.factor(P["net"], P["cost"])
     cu = oracle.cost_update(fac, P["cost"], tree, P["alpha2"], P["dhat"], P["eps"], P["q"])
     oracle.apg(fac, tree, cu, P["cost"], P["p"], 1e-9, 2)   # warm caches
+    if start_at > 0:
+        time.sleep(max(0.0, start_at - time.time()))
     t0 = time.perf_counter()
     oracle.apg(fac, tree, cu, P["cost"], P["p"], 1e-9, iters)
     dt = time.perf_counter() - t0
     print(json.dumps({"ms_per_iter": 1e3 * dt / iters, "iters": iters, "seconds": dt}))
 
 
-def run_oracle_sample(config, iters, threads=1):
+def _oracle_cmd(config, iters, step=0, start_at=0.0):
+    return [sys.executable, os.path.abspath(__file__), "--oracle-sample", str(iters), "--config", config,
+            "--oracle-step", str(step), "--oracle-start", repr(start_at)]
+
+
+def _oracle_env(threads=1):
     env = dict(os.environ)
     for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "NUMEXPR_NUM_THREADS"):
         env[k] = str(threads)
     env["CUDA_VISIBLE_DEVICES"] = ""
-    r = subprocess.run([sys.executable, os.path.abspath(__file__), "--oracle-sample", str(iters), "--config", config],
-                       capture_output=True, text=True, env=env, cwd=ROOT, timeout=600)
+    return env
+
+
+def run_oracle_sample(config, iters, threads=1, step=0):
+    t0 = time.perf_counter()
+    r = subprocess.run(_oracle_cmd(config, iters, step), capture_output=True, text=True, env=_oracle_env(threads),
+                       cwd=ROOT, timeout=900)
     if r.returncode != 0:
         raise RuntimeError(r.stderr[-2000:])
-    return json.loads(r.stdout.strip().splitlines()[-1])
+    out = json.loads(r.stdout.strip().splitlines()[-1])
+    out["wall_s"] = time.perf_counter() - t0
+    return out
+
+
+def run_oracle_parallel(config, iters, procs, setup_s):
+    """`procs` single-threaded oracle processes at once, each on its own MPC step's inputs
+    (independent solves, one per host core), timing together from a common start time
+    after their set-up; returns their samples and the wall time."""
+    t0 = time.perf_counter()
+    start_at = time.time() + 2.0 * setup_s + 5.0
+    ps = [subprocess.Popen(_oracle_cmd(config, iters, k, start_at), stdout=subprocess.PIPE, stderr=subprocess.PIPE,
+                           text=True, env=_oracle_env(1), cwd=ROOT) for k in range(procs)]
+    out = []
+    for p_ in ps:
+        o, e = p_.communicate(timeout=900)
+        if p_.returncode != 0:
+            raise RuntimeError(e[-2000:])
+        out.append(json.loads(o.strip().splitlines()[-1]))
+    return out, time.perf_counter() - t0
 
 
 def oracle_iters_to_tol(config):
@@ -169,15 +224,29 @@ def oracle_iters_to_tol(config):
     return None, None
 
 
-def cpu_baseline(config, iters_to_tol, budget_iters=None):
+def cpu_baseline(config, iters_to_tol, seconds=12.0):
+    """The FP64 oracle as it stands, timed on the host cores: one process (one core), and
+    one process per core on independent step inputs (all cores).  Each times a bounded
+    sample of about `seconds` of APG iterations, scaled to the oracle's own iteration
+    count to rho_rel <= 1e-3."""
     probe = run_oracle_sample(config, 3)
-    n = budget_iters or max(5, min(2000, int(15000.0 / max(probe["ms_per_iter"], 1e-3))))
-    s = run_oracle_sample(config, n)
-    ms_solve = s["ms_per_iter"] * iters_to_tol
+    n = max(5, min(2000, int(1000.0 * seconds / max(probe["ms_per_iter"], 1e-3))))
+    one = run_oracle_sample(config, n)
+    cores = os.cpu_count() or 1
+    many, wall = run_oracle_parallel(config, n, cores, probe["wall_s"])
+    # all cores: each process's own iteration rate, summed (they ran at the same time)
+    iters_per_s_all = sum(1000.0 / m["ms_per_iter"] for m in many)
+    ms_solve = one["ms_per_iter"] * iters_to_tol
     return {"value": 1000.0 / ms_solve, "unit": "solves/s", "cores": 1, "kind": "oracle",
-            "sample": f"{n} FP64 APG iterations of the same workload timed ({s['seconds']:.1f} s), "
-                      f"scaled to {iters_to_tol} iterations per solve",
-            "ms_per_iter": s["ms_per_iter"], "iters_per_s": 1000.0 / s["ms_per_iter"]}
+            "sample": f"{n} FP64 APG iterations of the same workload timed ({one['seconds']:.1f} s), "
+                      f"scaled to {iters_to_tol} iterations per solve (the oracle's own count to 1e-3)",
+            "ms_per_iter": one["ms_per_iter"], "iters_per_s": 1000.0 / one["ms_per_iter"],
+            "host_cores": cores,
+            "all_cores": {"value": iters_per_s_all / iters_to_tol, "unit": "solves/s", "cores": cores,
+                          "kind": "oracle", "iters_per_s": iters_per_s_all, "wall_s": wall,
+                          "sample": f"{cores} single-threaded oracle processes at once, one per host core, each "
+                                    f"{n} FP64 APG iterations of its own MPC step's inputs; summed iteration "
+                                    f"rate scaled to {iters_to_tol} iterations per solve"}}
 
 
 # --------------------------------------------------------------------- clocks
@@ -322,9 +391,66 @@ def time_per_iteration(S, inp, stream, lo=100, hi=400, reps=3):
     return (out[hi] - out[lo]) / (hi - lo)
 
 
+SCHED_NAMES = {1: "chain", 2: "node-parallel", 3: "hybrid"}
+
+
+def kernel_roofline(S, P, prec, inp, stream, fp64_peak, iters=200):
+    """Per-kernel device times of a live profiling solve (CUDA events between the launches,
+    smpc_profile_solve) and the roofline of the dominant kernel: algorithmic bytes (or
+    flops) per launch / its mean duration."""
+    t_iter_ms = time_per_iteration(S, inp, stream, *((20, 60) if prec == 0 else (100, 400)))
+    n_v = S.n_u - np.linalg.matrix_rank(P["net"]["E"])
+    nbytes, _, flops = algorithmic_bytes_per_iteration(S.n, S.n_x, S.n_u, n_v, prec)
+    host = {k: v.cpu().numpy() for k, v in inp.items()}
+    stage_ms = S.smpc.smpc_profile_solve(S.fac, host["p"], host["q"], host["dhat"], host["alpha2"], eps=P["eps"],
+                                         iters=iters)
+    names = STAGES[S.schedule]
+    hbm, src = peaks()
+    if S.schedule == 1:
+        kern, k_ms, k_bytes = "apg_iter", stage_ms[0], nbytes
+    else:
+        k = int(np.argmax(stage_ms))
+        kern, k_ms = names[k], stage_ms[k]
+        k_bytes = stage_bytes(kern, S.n, S.n_x, S.n_u, n_v, prec, False)
+    if prec == 0:
+        k_flops = flops if S.schedule == 1 else stage_flops(kern, S.n, S.n_x, S.n_u, n_v)
+        achieved = (k_flops or 0) / (k_ms * 1e-3) / 1e12
+        roof = {"bound": "alu", "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s",
+                "frac": achieved / fp64_peak, "traffic": recorded_traffic("fp64"),
+                "peak_source": "float64 FMA throughput measured live by smpc_fma_peak"}
+    else:
+        achieved = (k_bytes or 0) / (k_ms * 1e-3) / 1e9
+        roof = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+                "traffic": recorded_traffic(f"{PREC_KEYS[prec]}_{kern}_{S.n}"), "peak_source": f"{src} hbm_gbs"}
+    roof.update({"kernel": kern, "us_per_launch": 1000.0 * k_ms, "bytes_per_launch": k_bytes,
+                 "timing": f"CUDA events between the launches of a {iters}-iteration profiling solve",
+                 "stage_us": {n_: 1000.0 * t for n_, t in zip(names, stage_ms)},
+                 "us_per_iteration": 1000.0 * t_iter_ms,
+                 "iteration_bytes": nbytes, "iteration_frac_of_hbm": nbytes / (t_iter_ms * 1e-3) / 1e9 / hbm})
+    return roof
+
+
+def timed_solves(S, dev_in, ks, stream, args, flush):
+    torch = S.torch
+    times, iters, launches = [], [], 0
+    for k in ks:
+        flush.fill_(float(k))
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        S.solve(dev_in[k], args.max_iters, args.tol, stream)
+        e1.record(stream)
+        info = S.finish()
+        times.append(e0.elapsed_time(e1))
+        iters.append(info["iterations"])
+        launches += info["launches"]
+    return times, iters, launches
+
+
 def run_ours(args, rank, world, local_rank):
     import torch
     import torch.distributed as dist
+    import paper_1604_01074_gb300 as smpc
     device = torch.device("cuda", local_rank)
     torch.cuda.set_device(device)
     if world > 1:
@@ -339,85 +465,51 @@ def run_ours(args, rank, world, local_rank):
     dev_in = [S.device_inputs(i) for i in inputs]
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=device)  # 256 MB > L2
 
-    log("factor ready", S.info)
-    # warm-up solves (untimed)
-    for k in range(args.warmup):
+    log("factor ready", S.info, "schedule", S.schedule, S.tuned_ms)
+    for k in range(args.warmup):  # warm-up solves (untimed)
         S.solve(dev_in[k], args.max_iters, args.tol, stream)
         S.finish()
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
-    times, iters, launches = [], [], 0
-    clk = ClockSampler(os.path.join(ROOT, "gpurun_out" if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else "_work",
-                                    f"clocks_rank{rank}.csv"))
+    fd, clk_path = tempfile.mkstemp(prefix="smpc_clocks_", suffix=".csv")
+    os.close(fd)
+    clk = ClockSampler(clk_path)
     with clk:
-        for k in range(args.warmup, n_steps):
-            flush.fill_(float(k))
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            r = S.solve(dev_in[k], args.max_iters, args.tol, stream)
-            e1.record(stream)
-            info = S.finish()
-            times.append(e0.elapsed_time(e1))
-            iters.append(info["iterations"])
-            launches += info["launches"]
+        times, iters, launches = timed_solves(S, dev_in, range(args.warmup, n_steps), stream, args, flush)
         torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
+    clocks = clk.summary()
+    os.unlink(clk_path)
     log("timed solves ms", times, "iterations", iters)
     local_s = sum(times) / 1000.0
     units, secs = aggregate(args.steps, local_s, device if world > 1 else None)
     value = units / secs
     ms_per_step = 1000.0 * local_s / args.steps
-    clocks = clk.summary()
 
-    # kernel roofline: per-kernel device times from CUDA events between the launches of a
-    # live profiling solve of this factor (smpc_profile_solve), right after the timed region
-    t_iter_ms = time_per_iteration(S, dev_in[0], stream, *((20, 60) if prec == 0 else (100, 400)))
-    log("ms per iteration", t_iter_ms)
-    n_v = S.n_u - np.linalg.matrix_rank(P["net"]["E"])
-    nbytes, mat_entries, flops = algorithmic_bytes_per_iteration(S.n, S.n_x, S.n_u, n_v, prec)
-    inp0 = inputs[0]
-    stage_ms = S.smpc.smpc_profile_solve(S.fac, inp0["p"], inp0["q"], inp0["dhat"], inp0["alpha2"], eps=P["eps"],
-                                         iters=200)
-    names = STAGES[S.schedule]
-    log("stage us", dict(zip(names, [1000 * t for t in stage_ms])))
-    hbm, src = peaks()
-    if S.schedule == 1:
-        kern, k_ms, k_bytes = "apg_iter", stage_ms[0], nbytes
-    else:
-        k = int(np.argmax(stage_ms))
-        kern, k_ms = names[k], stage_ms[k]
-        k_bytes = stage_bytes(kern, S.n, S.n_x, S.n_u, n_v, prec, False)
-    if prec == 0 and S.schedule == 1:
-        achieved = flops / (k_ms * 1e-3) / 1e12
-        roof = {"bound": "alu", "achieved": achieved, "peak": FP64_FMA_TFLOPS, "unit": "TFLOP/s",
-                "frac": achieved / FP64_FMA_TFLOPS, "traffic": recorded_traffic("fp64"),
-                "peak_source": "measured FP64 FMA microbenchmark on this pool's GB300"}
-    else:
-        achieved = (k_bytes or 0) / (k_ms * 1e-3) / 1e9
-        roof = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
-                "traffic": recorded_traffic(f"{args.precision}_{kern}"), "peak_source": f"{src} hbm_gbs"}
-    roof.update({"kernel": kern, "us_per_launch": 1000.0 * k_ms, "bytes_per_launch": k_bytes,
-                 "timing": "CUDA events between the launches of a 200-iteration profiling solve",
-                 "stage_us": {n_: 1000.0 * t for n_, t in zip(names, stage_ms)},
-                 "us_per_iteration": 1000.0 * t_iter_ms})
+    try:
+        fp64_peak = smpc.smpc_fma_peak(0)
+    except Exception:  # noqa: BLE001
+        fp64_peak = FP64_FMA_TFLOPS
+    roof = kernel_roofline(S, P, prec, dev_in[0], stream, fp64_peak)
+    log("roofline", roof)
 
-    # end-to-end: host (pinned) inputs, device->host read of u_0 and the residual, wall clock
-    pin_in = [S.pinned_inputs(i) for i in inputs]
+    # end to end through smpc_solve with host (pinned) inputs and the host read of u_0 and
+    # the residual, wall clock; a bounded number of the timed steps' inputs
+    n_e2e = max(1, min(args.steps, args.e2e_steps))
+    pin_in = [S.pinned_inputs(inputs[k]) for k in range(args.warmup, args.warmup + n_e2e)]
     u0 = np.zeros(S.n_u)
-    torch.cuda.synchronize()
     e2e_t = []
-    for k in range(args.warmup, n_steps):
+    for k, pin in enumerate(pin_in):
         flush.fill_(float(k))
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        S.solve(pin_in[k], args.max_iters, args.tol, stream, sync=1, u0=u0)
+        S.solve(pin, args.max_iters, args.tol, stream, sync=1, u0=u0)
         e2e_t.append(time.perf_counter() - t0)
-    e2e_units, e2e_secs = aggregate(args.steps, sum(e2e_t), device if world > 1 else None)
+    e2e_units, e2e_secs = aggregate(n_e2e, sum(e2e_t), device if world > 1 else None)
     log("e2e s", e2e_t)
     h2d = sum(int(np.asarray(v).nbytes) for v in inputs[0].values())
     d2h = 8 * S.n_u + 8 + 24
@@ -426,93 +518,33 @@ def run_ours(args, rank, world, local_rank):
         "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": PREC_NAMES[prec], "data": "synthetic",
-        "config": {"workload": WORKLOAD if args.config == "barcelona" else args.config, "solve": "cold start, tol 1e-3 on "
-                   "rho_rel", "tol": args.tol, "max_iters": args.max_iters, "precision": args.precision,
-                   "packs": "per node", "schedule": {1: "chain", 2: "node-parallel", 3: "hybrid"}[S.schedule],
-                   "schedule_tuning_ms": S.tuned_ms,
-                   "l2": "256 MB buffer written between timed solves (L2 flushed)", "parallelism": f"replicas x{world}",
+        "config": {"workload": WORKLOADS[args.config], "solve": "cold start, tol 1e-3 on rho_rel", "tol": args.tol,
+                   "max_iters": args.max_iters, "precision": args.precision, "packs": "per node",
+                   "schedule": SCHED_NAMES[S.schedule], "schedule_tuning_ms": S.tuned_ms,
+                   "l2": "inputs (packs) larger than L2, and a 256 MB buffer written between timed solves",
+                   "parallelism": f"replicas x{world}",
                    "launch": "plain launches" if args.no_graph else
                    "64-iteration chunks as CUDA graphs (smpc_solve use_graph; captured by the warm-up solves)"},
         "iterations_mean": float(np.mean(iters)), "apg_iters_per_s": float(np.sum(iters)) / local_s * world,
         "p50_ms": float(np.percentile(times, 50)), "p99_ms": float(np.percentile(times, 99)),
         "roofline": roof, "clocks": clocks, "gpu_launches": launches,
-        "e2e": {"value": e2e_units / e2e_secs, "unit": "solves/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "e2e": {"value": e2e_units / e2e_secs, "unit": "solves/s", "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h, "steps": n_e2e,
+                "note": "smpc_solve with pinned host inputs, sync = 1 (u_0 and the residual read back), wall clock"},
+        "fp64_fma_tflops": fp64_peak,
         "tree": S.info,
     }
     log("headline", {k: result[k] for k in ("value", "ms_per_step", "iterations_mean", "p50_ms", "p99_ms")})
     S.close()
     if args.other_legs and rank == 0:
-        # the other precisions on the same workload: iteration cost, roofline, and one
-        # solve of the first step's input to the same tolerance
-        legs = {}
-        sols = {}
-        Sh = Solver(P, prec, device, args.schedule, shared_packs=1)
-        t_sh = time_per_iteration(Sh, dev_in[0], stream, lo=100, hi=400, reps=2)
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        sh_t = []
-        for k in range(args.warmup, n_steps):
-            e0.record(stream)
-            Sh.solve(dev_in[k], args.max_iters, args.tol, stream)
-            e1.record(stream)
-            inf_sh = Sh.finish()
-            sh_t.append(e0.elapsed_time(e1))
-        legs[PREC_NAMES[prec] + "_shared_packs"] = {
-            "solves_per_s": 1000.0 * len(sh_t) / sum(sh_t), "ms_per_solve": float(np.mean(sh_t)),
-            "us_per_iteration": 1000.0 * t_sh, "schedule": {1: "chain", 2: "node-parallel", 3: "hybrid"}[Sh.schedule],
-            "factor_device_bytes": Sh.smpc.smpc_factor_device_bytes(Sh.fac),
-            "note": "one pack per factor: the per-node matrices differ only by 1/(2 p_n), applied to Lambda r"}
-        log("leg shared", legs[PREC_NAMES[prec] + "_shared_packs"])
-        Sh.close()
-        for other in (0, 1, 2):
-            So = Solver(P, other, device)
-            if other == prec:  # the headline precision on the legs' input, for the error statement
-                So.solve(dev_in[0], args.max_iters, args.tol, stream)
-                So.finish()
-                sols[other] = (So.u.double().cpu().numpy(), So.x.double().cpu().numpy())
-                So.close()
-                continue
-            lo, hi = (20, 60) if other == 0 else (100, 400)
-            t_o = time_per_iteration(So, dev_in[0], stream, lo=lo, hi=hi, reps=2)
-            b_o, _, f_o = algorithmic_bytes_per_iteration(So.n, So.n_x, So.n_u, n_v, other)
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            So.solve(dev_in[0], args.max_iters, args.tol, stream)
-            e1.record(stream)
-            inf_o = So.finish()
-            sols[other] = (So.u.double().cpu().numpy(), So.x.double().cpu().numpy())
-            leg = {"us_per_iteration": 1000.0 * t_o, "iterations_run": inf_o["iterations"],
-                   "rho_rel": inf_o["rho_rel"], "reached_tol": inf_o["rho_rel"] <= args.tol,
-                   "ms_for_run": e0.elapsed_time(e1)}
-            if other == 0:
-                leg["roofline"] = {"bound": "alu", "achieved": f_o / (t_o * 1e-3) / 1e12, "peak": FP64_FMA_TFLOPS,
-                                   "unit": "TFLOP/s", "frac": f_o / (t_o * 1e-3) / 1e12 / FP64_FMA_TFLOPS}
-            else:
-                hbm, src = peaks()
-                leg["roofline"] = {"bound": "hbm", "achieved": b_o / (t_o * 1e-3) / 1e9, "peak": hbm, "unit": "GB/s",
-                                   "frac": b_o / (t_o * 1e-3) / 1e9 / hbm}
-            legs[PREC_NAMES[other]] = leg
-            log("leg", PREC_NAMES[other], leg)
-            So.close()
-        # every precision's result against the float64 solve of the same input (which
-        # the parity tests tie to the oracle), relative to 1 + max |.|, and the residual
-        # of the demand coupling E u + E_d d = 0
-        d = P["dhat"][P["tree"]["stage"]] + P["eps"]
-        u64, x64 = sols[0]
-        errs = {}
-        for k, (u, x) in sols.items():
-            errs[PREC_NAMES[k]] = {
-                "u": float(np.abs(u - u64).max() / (1 + np.abs(u64).max())),
-                "x": float(np.abs(x - x64).max() / (1 + np.abs(x64).max())),
-                "coupling": float(np.abs(u @ P["net"]["E"].T + d @ P["net"]["Ed"].T).max())}
-        result["other_precisions"] = legs
-        result["error_vs_fp64_solve"] = errs
+        result["legs"] = run_legs(args, P, prec, dev_in, stream, flush, fp64_peak)
     if rank == 0 and not args.no_cpu_baseline:
         it_ref = int(np.mean(iters))
         stored, _ = oracle_iters_to_tol(args.config)
         try:
             result["cpu_baseline"] = cpu_baseline(args.config, stored or it_ref)
+            if not stored:
+                result["cpu_baseline"]["note"] = "no stored oracle iteration count: scaled by the GPU's count"
             log("cpu baseline", result["cpu_baseline"])
         except Exception as exc:  # noqa: BLE001
             result["cpu_baseline"] = {"error": str(exc)[-300:]}
@@ -520,6 +552,71 @@ def run_ours(args, rank, world, local_rank):
         dist.barrier()
         dist.destroy_process_group()
     return result
+
+
+def run_legs(args, P, prec, dev_in, stream, flush, fp64_peak):
+    """Other precisions and pack layouts on the headline workload (iteration cost and
+    roofline; error against the float64 solve at an equal iteration count), and, for the
+    large tree, the 2081-node tree with float32 per-node packs."""
+    torch = __import__("torch")
+    device = torch.device("cuda", torch.cuda.current_device())
+    legs = {}
+    n_err = args.error_iters
+    sols = {}
+    for other in (0, 1, 2):
+        So = Solver(P, other, device)
+        try:
+            So.solve(dev_in[0], n_err, 0.0, stream)  # fixed count: every precision at the same iterate
+            So.finish()
+            sols[other] = (So.u.double().cpu().numpy(), So.x.double().cpu().numpy())
+            if other != prec:
+                leg = kernel_roofline(So, P, other, dev_in[0], stream, fp64_peak)
+                leg["schedule"] = SCHED_NAMES[So.schedule]
+                legs[PREC_NAMES[other] + "_per_node"] = leg
+                log("leg", PREC_NAMES[other], {k: leg[k] for k in ("us_per_iteration", "kernel", "frac")})
+        finally:
+            So.close()
+    u64, x64 = sols[0]
+    d = P["dhat"][P["tree"]["stage"]] + P["eps"]
+    legs["error_vs_fp64_solve"] = {
+        PREC_NAMES[k]: {"u": float(np.abs(u - u64).max() / (1 + np.abs(u64).max())),
+                        "x": float(np.abs(x - x64).max() / (1 + np.abs(x64).max())),
+                        "coupling": float(np.abs(u @ P["net"]["E"].T + d @ P["net"]["Ed"].T).max())}
+        for k, (u, x) in sols.items()}
+    legs["error_vs_fp64_solve"]["iterations"] = n_err
+    legs["error_vs_fp64_solve"]["note"] = ("relative to 1 + max |.| of the float64 solve at the same iteration count; "
+                                           "the -m gpu tests tie each precision to the FP64 oracle element by element")
+    # shared packs (one pack for all nodes): solves to tol
+    Sh = Solver(P, prec, device, shared_packs=1)
+    try:
+        Sh.use_graph = 1
+        times, iters, _ = timed_solves(Sh, dev_in, range(min(len(dev_in), args.leg_solves)), stream, args, flush)
+        legs[PREC_NAMES[prec] + "_shared_packs"] = {
+            "solves_per_s": 1000.0 * len(times) / sum(times), "ms_per_solve": float(np.mean(times)),
+            "iterations_mean": float(np.mean(iters)), "schedule": SCHED_NAMES[Sh.schedule],
+            "factor_device_bytes": Sh.smpc.smpc_factor_device_bytes(Sh.fac),
+            "note": "one pack per factor: the per-node matrices differ only by 1/(2 p_n), applied to Lambda r"}
+        log("leg shared", legs[PREC_NAMES[prec] + "_shared_packs"])
+    finally:
+        Sh.close()
+    if args.config == "large":
+        Pb = make_problem("barcelona")
+        Sb = Solver(Pb, 1, device)
+        try:
+            Sb.use_graph = 1
+            inb = [Sb.device_inputs(step_inputs(Pb, k)) for k in range(args.leg_solves + 1)]
+            Sb.solve(inb[0], args.max_iters, args.tol, stream)  # warm-up (captures the graphs)
+            Sb.finish()
+            times, iters, _ = timed_solves(Sb, inb, range(1, args.leg_solves + 1), stream, args, flush)
+            leg = {"workload": WORKLOADS["barcelona"], "precision": "fp32", "packs": "per node",
+                   "solves_per_s": 1000.0 * len(times) / sum(times), "ms_per_solve": float(np.mean(times)),
+                   "iterations_mean": float(np.mean(iters)), "schedule": SCHED_NAMES[Sb.schedule]}
+            leg["roofline"] = kernel_roofline(Sb, Pb, 1, inb[0], stream, fp64_peak)
+            legs["barcelona_fp32_per_node"] = leg
+            log("leg barcelona", {k: leg[k] for k in ("solves_per_s", "iterations_mean", "schedule")})
+        finally:
+            Sb.close()
+    return legs
 
 
 def profile_solve(args):
@@ -756,6 +853,11 @@ def run_batched(args):
 
 
 def run_reference(args, rank, world):
+    """The reference arm: the FP64 oracle as it stands, on the host cores, for the same
+    workload and metric.  Each step is a bounded sample of the workload (about 6 s of
+    APG iterations on one MPC step's inputs); ms_per_step is that sample's measured
+    time, and value scales the measured iteration rate to whole solves by the oracle's
+    own iteration count to rho_rel <= 1e-3."""
     if rank != 0:
         return None
     stored, meta = oracle_iters_to_tol(args.config)
@@ -763,22 +865,34 @@ def run_reference(args, rank, world):
     if iters_to_tol is None:
         return {"impl": "reference", "unavailable": "no stored oracle iteration count for this workload"}
     probe = run_oracle_sample(args.config, 3)
-    per = max(3, min(400, int(8000.0 / max(probe["ms_per_iter"], 1e-3))))  # ~8 s of CPU work per step
-    for _ in range(args.warmup):
-        run_oracle_sample(args.config, max(2, per // 10))
-    samples = [run_oracle_sample(args.config, per) for _ in range(args.steps)]
-    ms_iter = statistics.mean(s["ms_per_iter"] for s in samples)
-    ms_solve = ms_iter * iters_to_tol
-    value = 1000.0 / ms_solve
-    sample = f"{per} FP64 APG iterations per step, scaled to {iters_to_tol} iterations per solve (oracle's own count)"
+    per = max(3, min(400, int(6000.0 / max(probe["ms_per_iter"], 1e-3))))
+    for k in range(args.warmup):
+        run_oracle_sample(args.config, max(2, per // 10), step=k)
+    samples = [run_oracle_sample(args.config, per, step=args.warmup + k) for k in range(args.steps)]
+    ms_iter = statistics.mean(s_["ms_per_iter"] for s_ in samples)
+    ms_step = statistics.mean(s_["seconds"] * 1000.0 for s_ in samples)
+    value = 1000.0 / (ms_iter * iters_to_tol)
+    sample = (f"{per} FP64 APG iterations per step ({per / iters_to_tol:.4f} of a solve), iteration rate scaled "
+              f"to {iters_to_tol} iterations per solve (the oracle's own count to 1e-3)")
     return {"impl": "reference", "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_solve, "higher_is_better": True,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD if args.config == "barcelona" else args.config, "tol": args.tol,
-                       "implementation": "FP64 CPU oracle (numpy), single thread"},
-            "apg_iters_per_s": 1000.0 / ms_iter,
-            "cpu_baseline": {"value": value, "unit": "solves/s", "cores": 1, "kind": "oracle", "sample": sample},
+            "config": {"workload": WORKLOADS[args.config], "tol": args.tol,
+                       "implementation": "FP64 CPU oracle (numpy), one host core",
+                       "step": f"a bounded sample: {per} APG iterations of one MPC step's inputs"},
+            "apg_iters_per_s": 1000.0 / ms_iter, "solve_fraction_per_step": per / iters_to_tol,
+            "cpu_baseline": {"value": value, "unit": "solves/s", "cores": 1, "kind": "oracle", "sample": sample,
+                             "host_cores": os.cpu_count()},
             "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def spawn_ranks(n):
+    """--gpus N outside torchrun: run N ranks of this script through torch.distributed.run
+    (one process per GPU, rendezvous on 127.0.0.1) and return its exit code."""
+    cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", f"--nproc-per-node={n}",
+           "--master-addr", "127.0.0.1", "--master-port", str(29500 + os.getpid() % 1000),
+           os.path.abspath(__file__), *sys.argv[1:]]
+    return subprocess.call(cmd, cwd=ROOT)
 
 
 def _jsonable(o):
@@ -800,15 +914,21 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--precision", choices=["fp64", "fp32", "bf16"], default="fp32")
-    ap.add_argument("--config", choices=["barcelona", "tiny", "large"], default="barcelona")
+    ap.add_argument("--config", choices=["barcelona", "tiny", "large"], default="large")
     ap.add_argument("--tol", type=float, default=1e-3)
     ap.add_argument("--schedule", type=int, choices=[0, 1, 2, 3], default=0,
                     help="iteration schedule: 0 = the factor times both and keeps the faster")
     ap.add_argument("--max-iters", type=int, default=100000)
     ap.add_argument("--no-graph", action="store_true", help="plain launches instead of CUDA-graph chunks")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=3, help="solves timed end to end (at most --steps)")
+    ap.add_argument("--error-iters", type=int, default=400,
+                    help="legs: iteration count at which each precision is compared with the float64 solve")
+    ap.add_argument("--leg-solves", type=int, default=3, help="legs: solves timed per leg")
     ap.add_argument("--no-other-precisions", dest="other_legs", action="store_false")
     ap.add_argument("--oracle-sample", type=int, default=0)
+    ap.add_argument("--oracle-step", type=int, default=0)
+    ap.add_argument("--oracle-start", type=float, default=0.0)
     ap.add_argument("--serve", action="store_true", help="closed-loop serving workload (its own JSON line)")
     ap.add_argument("--serve-rate", type=float, default=200.0)
     ap.add_argument("--serve-seconds", type=float, default=20.0)
@@ -827,7 +947,7 @@ def main():
                          "CUDA profiler range, and exit: the case ncu captures (--profile-from-start off)")
     args = ap.parse_args()
     if args.oracle_sample:
-        oracle_sample(args.config, args.oracle_sample)
+        oracle_sample(args.config, args.oracle_sample, args.oracle_step, args.oracle_start)
         return
     if args.profile_solve:
         profile_solve(args)
@@ -838,6 +958,8 @@ def main():
     if args.batched:
         print(json.dumps(run_batched(args), default=_jsonable))
         return
+    if args.gpus > 1 and "WORLD_SIZE" not in os.environ:
+        sys.exit(spawn_ranks(args.gpus))
     rank, world, local_rank = dist_env()
     if args.impl == "reference":
         res = run_reference(args, rank, world)

@@ -61,6 +61,7 @@ typedef enum smpc_precision {
 typedef struct smpc_tree smpc_tree;
 typedef struct smpc_factor_t smpc_factor_t;
 typedef struct smpc_server smpc_server;
+typedef struct smpc_batch smpc_batch;
 
 /* Flow-based network model x+ = A x + B u + G_d d, 0 = E u + E_d d (Sec. II-A,
  * eqs. model and demand-control).  A may be NULL for the identity (tank mass
@@ -249,6 +250,28 @@ int smpc_solve(smpc_factor_t* fac, const smpc_step_data* data, const smpc_solve_
 int smpc_solve_static(smpc_factor_t* fac, const smpc_step_data* data, const smpc_solve_opts* opts,
                       smpc_result* res, void* stream);
 
+/* Batched solves (Sec. IV-B's stage parallelism carried across independent problems):
+ * smpc_batch_create groups `count` factors - single trees or forests (several trees on one
+ * network, see smpc_tree_create), on any mix of networks and precisions - that are then
+ * solved together.  smpc_batch_solve runs the solve of smpc_solve for every factor k with
+ * its own step data data[k] and the shared opts, and writes res[k]: each chunk of
+ * opts->check_every iterations is one launch for the whole batch - with
+ * opts->use_graph = 1 a CUDA graph whose parallel branches are the factors' kernels for
+ * those iterations, captured the first time the batch runs that chunk with these settings
+ * and replayed by later solves; with use_graph = 0 the same kernels on one stream per
+ * factor between a fork and a join on `stream`.  Every factor keeps its own state and
+ * stop: a factor (or a forest's tree) whose residual met tol keeps its iterates and its
+ * kernels return at once; the batch ends when every factor has stopped or at max_iters.
+ * Results per factor, exactly as smpc_solve on that factor alone (including
+ * smpc_solve_trees for forests).  The factors must outlive the batch and a factor may
+ * appear in one batch solve at a time; calls on the same batch must not overlap.
+ * Errors: as smpc_solve (the first failing factor's), SMPC_EINVAL for a NULL or
+ * repeated factor, SMPC_ECUDA, SMPC_ENOMEM. */
+int smpc_batch_create(int32_t count, smpc_factor_t* const* factors, smpc_batch** out);
+int smpc_batch_solve(smpc_batch* batch, const smpc_step_data* data, const smpc_solve_opts* opts, smpc_result* res,
+                     void* stream);
+void smpc_batch_destroy(smpc_batch* batch);
+
 /* Diagnostics; the paper has no counterpart.  Runs one cold-start solve of `iters`
  * iterations (tol 0, legacy default stream) with a CUDA event between consecutive kernels
  * of every full iteration, and writes the mean device time in ms
@@ -260,6 +283,27 @@ int smpc_solve_static(smpc_factor_t* fac, const smpc_step_data* data, const smpc
  * the factor's duals as that solve ends.  Returns n, or minus an smpc_status. */
 int smpc_profile_solve(smpc_factor_t* fac, const smpc_step_data* data, int32_t iters, double* stage_ms,
                        int32_t max_stages);
+
+/* Diagnostics; the paper has no counterpart.  Measures the fused multiply-add
+ * throughput of the current GPU in TFLOP/s (2 flops per FMA) for precision SMPC_FP64
+ * or SMPC_FP32: 8 CTAs of 256 threads per SM, 8 independent FMA chains per thread,
+ * one launch timed with CUDA events after a warm-up launch.  This is the ceiling of a
+ * solve bound by arithmetic rather than memory (float64 packs apply 2 flops per matrix
+ * entry read).  Allocates and frees a small device buffer.
+ * Errors: SMPC_EINVAL (other precision, NULL result), SMPC_ENOMEM, SMPC_ECUDA. */
+int smpc_fma_peak(int32_t precision, double* tflops);
+
+/* Per-tree results of the factor's last smpc_solve (waits for its stream).  In a forest
+ * (smpc_tree_create with R roots) every tree stops at its own first iterate whose
+ * relative residual rho_rel = rho / (1 + max(||H z||_inf, ||t||_inf)) (Sec. IV-E), taken
+ * over that tree's nodes alone, is <= tol: from then on the tree's iterates, outputs and
+ * final dual stay as they were at that iterate while the other trees go on, and the solve
+ * ends when every tree has stopped (or at max_iters).  iterations[r] receives the
+ * iterations tree r ran, rho_rel[r] its relative residual at its last iterate (R entries
+ * each; either pointer may be NULL).  A single tree reports the solve's own figures.
+ * smpc_solve_static keeps one residual for the whole forest and no per-tree record.
+ * Errors: SMPC_EINVAL (no smpc_solve yet, or the last solve was static), SMPC_ECUDA. */
+int smpc_solve_trees(smpc_factor_t* fac, int32_t* iterations, double* rho_rel);
 
 /* Completes an asynchronous solve (opts->sync = 0): waits for the stream of the
  * factor's last solve and fills the host outputs of `res` (iterations, rho,

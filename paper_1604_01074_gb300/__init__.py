@@ -86,6 +86,13 @@ SIGNATURES = {
     "smpc_solve_info": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(smpc_result)]),
     "smpc_solve_static": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(smpc_step_data),
                                          ctypes.POINTER(smpc_solve_opts), ctypes.POINTER(smpc_result), ctypes.c_void_p]),
+    "smpc_fma_peak": (ctypes.c_int, [ctypes.c_int32, _dp]),
+    "smpc_solve_trees": (ctypes.c_int, [ctypes.c_void_p, _ip, _dp]),
+    "smpc_batch_create": (ctypes.c_int, [ctypes.c_int32, ctypes.POINTER(ctypes.c_void_p),
+                                         ctypes.POINTER(ctypes.c_void_p)]),
+    "smpc_batch_solve": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(smpc_step_data),
+                                        ctypes.POINTER(smpc_solve_opts), ctypes.POINTER(smpc_result), ctypes.c_void_p]),
+    "smpc_batch_destroy": (None, [ctypes.c_void_p]),
     "smpc_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "smpc_last_error": (ctypes.c_char_p, []),
     "smpc_version": (ctypes.c_int, []),
@@ -287,12 +294,14 @@ def smpc_server_destroy(server):
 
 
 def smpc_submit(server, fac, p, q, dhat, alpha2, eps=None, max_iters=500, tol=0.0, warm_start=0, check_every=0,
-                polish_iters=0, anchor_every=0):
-    """Queues one solve; returns its ticket.  Step data: numpy float64 arrays."""
+                polish_iters=0, anchor_every=0, use_graph=0):
+    """Queues one solve; returns its ticket.  Step data: numpy float64 arrays.  use_graph=1:
+    the slot runs the solve's iteration chunks as CUDA graphs (captured once per factor,
+    chunk and settings)."""
     k = _Keep()
     D = smpc_step_data(k(p), k(q), k(dhat), k(eps), k(alpha2))
     O = smpc_solve_opts(int(max_iters), float(tol), int(warm_start), int(check_every), 0, int(polish_iters),
-                        int(anchor_every))
+                        int(anchor_every), int(use_graph))
     t = ctypes.c_uint64()
     _check(lib().smpc_submit(server, fac, ctypes.byref(D), ctypes.byref(O), ctypes.byref(t)), "smpc_submit")
     return t.value
@@ -319,6 +328,66 @@ def smpc_solve_info(fac, u0_host=None, history_host=None):
                     None if history_host is None else history_host.ctypes.data_as(_dp), -1, 0.0, 0.0, 0)
     _check(lib().smpc_solve_info(fac, ctypes.byref(R)), "smpc_solve_info")
     return {"iterations": R.iterations, "rho": R.rho, "rho_rel": R.rho_rel, "launches": R.launches}
+
+
+def smpc_batch_create(factors):
+    arr = (ctypes.c_void_p * len(factors))(*[f.value if hasattr(f, "value") else f for f in factors])
+    h = ctypes.c_void_p()
+    _check(lib().smpc_batch_create(len(factors), arr, ctypes.byref(h)), "smpc_batch_create")
+    return h
+
+
+def smpc_batch_destroy(batch):
+    lib().smpc_batch_destroy(batch)
+
+
+def smpc_batch_solve(batch, steps, max_iters=500, tol=0.0, warm_start=0, check_every=0, sync=1, outputs=None,
+                     u0_host=None, stream=None, polish_iters=0, anchor_every=0, use_graph=0):
+    """steps: one dict (p, q, dhat, alpha2, eps) per factor of the batch (numpy float64 or int
+    device addresses).  outputs: optional list of (u, x, y) device tensors per factor;
+    u0_host: optional list of numpy arrays (R * n_u per factor).  Returns one result dict per
+    factor."""
+    k = _Keep()
+
+    def arg(a):
+        if a is None:
+            return None
+        if isinstance(a, int):
+            return ctypes.cast(ctypes.c_void_p(a), _dp)
+        return k(a)
+
+    n = len(steps)
+    D = (smpc_step_data * n)(*[smpc_step_data(arg(d["p"]), arg(d["q"]), arg(d["dhat"]), arg(d.get("eps")),
+                                              arg(d["alpha2"])) for d in steps])
+    O = smpc_solve_opts(int(max_iters), float(tol), int(warm_start), int(check_every), int(sync), int(polish_iters),
+                        int(anchor_every), int(use_graph))
+
+    def dptr(t):
+        return None if t is None else (t if isinstance(t, int) else t.data_ptr())
+
+    R = (smpc_result * n)()
+    for i in range(n):
+        u, x, y = outputs[i] if outputs else (None, None, None)
+        R[i] = smpc_result(dptr(u), dptr(x), dptr(y), None if u0_host is None else u0_host[i].ctypes.data_as(_dp),
+                           None, -1, 0.0, 0.0, 0)
+    s = None if stream is None else (stream if isinstance(stream, int) else stream.cuda_stream)
+    _check(lib().smpc_batch_solve(batch, D, ctypes.byref(O), R, s), "smpc_batch_solve")
+    return [{"iterations": r.iterations, "rho": r.rho, "rho_rel": r.rho_rel, "launches": r.launches} for r in R]
+
+
+def smpc_solve_trees(fac, n_trees):
+    """Per-tree (iterations, rho_rel) of the factor's last smpc_solve: numpy arrays of n_trees."""
+    it = np.zeros(n_trees, dtype=np.int32)
+    rr = np.zeros(n_trees)
+    _check(lib().smpc_solve_trees(fac, it.ctypes.data_as(_ip), rr.ctypes.data_as(_dp)), "smpc_solve_trees")
+    return it, rr
+
+
+def smpc_fma_peak(precision):
+    """Measured FMA throughput of the current GPU in TFLOP/s (SMPC_FP64 or SMPC_FP32)."""
+    t = ctypes.c_double()
+    _check(lib().smpc_fma_peak(int(precision), ctypes.byref(t)), "smpc_fma_peak")
+    return t.value
 
 
 def smpc_status_string(code):

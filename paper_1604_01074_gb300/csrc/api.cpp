@@ -323,6 +323,9 @@ IterArgs make_args(const smpc_factor_t* f) {
   a.counters = f->counters;
   a.flags = f->flags;
   a.wait_ns = f->wait_ns;
+  a.R = f->R;
+  a.res_tree = f->res_tree;  // NULL for a single tree
+  a.tree_done = f->tree_done;
   return a;
 }
 
@@ -375,10 +378,16 @@ int ensure_capacity(smpc_factor_t* f, int iters) {
   int cap = std::max(iters, 1024);
   unsigned long long* res = nullptr;
   double* cvec = nullptr;
+  unsigned long long* res_tree = nullptr;
   TRY(f->alloc(&res, sizeof(unsigned long long) * 3 * (size_t)(cap + 2)));
   TRY(f->alloc(&cvec, sizeof(double) * (size_t)(cap + 2)));
+  if (f->R > 1) {  // forests: a residual per tree and iteration (each tree stops on its own)
+    TRY(f->alloc(&res_tree, sizeof(unsigned long long) * 3 * (size_t)f->R * (size_t)(cap + 2)));
+    CK(cudaMemset(res_tree, 0, sizeof(unsigned long long) * 3 * (size_t)f->R * (size_t)(cap + 2)));
+  }
   f->drop_graphs();  // they hold the old buffers' addresses
   f->res = res;
+  f->res_tree = res_tree;
   f->cvec = cvec;
   f->cap = cap;
   f->cvec_for = -1;
@@ -807,13 +816,14 @@ int smpc_factor(const smpc_tree* tree, const smpc_network* net, const smpc_cost*
   f->ms = mat_size(f->prec);
   f->W_alpha = cost->W_alpha;
   f->gamma_d = cost->gamma_d;
-  // Diagnostics: SMPC_PIPELINE_WAIT_NS (a positive count of nanoseconds) replaces the 2 s
-  // bound of node_mv's pack-pipeline waits for this factor's solves, so that a test can
-  // make a wait give up (SMPC_ETIMEOUT) without a fault; the waits that let copies in
+  // Diagnostics: SMPC_PIPELINE_WAIT_NS (nanoseconds; 0 = one non-blocking test) replaces
+  // the 2 s bound of node_mv's pack-pipeline waits for this factor's solves, so that a test
+  // can make a wait give up (SMPC_ETIMEOUT) without a fault; the waits that let copies in
   // flight land keep the 2 s bound.
   if (const char* w = std::getenv("SMPC_PIPELINE_WAIT_NS")) {
-    const unsigned long long v = std::strtoull(w, nullptr, 10);
-    if (v > 0) f->wait_ns = v;
+    char* end = nullptr;
+    const unsigned long long v = std::strtoull(w, &end, 10);
+    if (end != w) f->wait_ns = v;
   }
   const int n = f->n, n_k = f->n_k, nd = f->nd;
   int dev = 0;
@@ -884,8 +894,9 @@ int smpc_factor(const smpc_tree* tree, const smpc_network* net, const smpc_cost*
       (rc = f->alloc(&f->d_dhat, sizeof(double) * (size_t)f->N * std::max(n_d, 1))) ||
       (rc = f->alloc(&f->d_eps, sizeof(double) * (size_t)n * std::max(n_d, 1))) ||
       (rc = f->alloc(&f->d_alpha2, sizeof(double) * (size_t)f->N * n_u)) || (rc = f->alloc(&f->counters, sizeof(int) * n)) ||
-      (rc = f->alloc(&f->flags, sizeof(int) * 4)))
+      (rc = f->alloc(&f->flags, sizeof(int) * 4)) || (rc = f->alloc(&f->tree_done, sizeof(int) * (size_t)f->R)))
     return fail(rc);
+  if (cudaMemset(f->tree_done, 0xff, sizeof(int) * (size_t)f->R) != cudaSuccess) return fail(SMPC_ECUDA);
   if (cudaMemset(f->d_eps, 0, sizeof(double) * (size_t)n * std::max(n_d, 1)) != cudaSuccess ||
       cudaMemset(f->counters, 0, sizeof(int) * n) != cudaSuccess ||
       cudaMallocHost(reinterpret_cast<void**>(&f->flags_host), sizeof(int) * 4) != cudaSuccess ||
@@ -1037,9 +1048,15 @@ int smpc_factor_steps(const smpc_factor_t* f, double* lambda, double* step_s, do
   return SMPC_OK;
 }
 
-int smpc_solve(smpc_factor_t* f, const smpc_step_data* data, const smpc_solve_opts* opts, smpc_result* res,
-               void* stream) {
-  if (!f || !data || !opts || !res) {
+}  // extern "C"
+
+namespace smpc {
+// Everything a solve does before its iteration chunks (Alg. 2 steps 1-3 up to the APG
+// loop): checks, the launch plan, the step-data upload, the cost update of App. A, the
+// initial duals and the per-solve flags, all enqueued on s.
+int solve_begin(smpc_factor_t* f, const smpc_step_data* data, const smpc_solve_opts* opts, cudaStream_t s,
+                IterPlan* plan_out, IterArgs* args_out) {
+  if (!f || !data || !opts) {
     set_error("NULL argument");
     return SMPC_EINVAL;
   }
@@ -1059,7 +1076,6 @@ int smpc_solve(smpc_factor_t* f, const smpc_step_data* data, const smpc_solve_op
     set_error("step data contains non-finite values");
     return SMPC_EINVAL;
   }
-  cudaStream_t s = static_cast<cudaStream_t>(stream);
   const int iters = opts->max_iters;
   TRY(ensure_capacity(f, iters + 1));
   TRY(upload_cvec(f, iters + 1));
@@ -1067,7 +1083,7 @@ int smpc_solve(smpc_factor_t* f, const smpc_step_data* data, const smpc_solve_op
   // refused for its options leaves the factor's duals as they were
   IterArgs a = make_args(f);
   a.tol = opts->tol;
-  IterPlan plan;
+  IterPlan& plan = *plan_out;
   TRY(plan_iters(f, a, *opts, &plan));
   // step data -> device (Alg. 2 steps 1-2)
   CK(cudaMemcpyAsync(f->d_p, data->p, sizeof(double) * f->R * n_x, cudaMemcpyDefault, s));
@@ -1111,9 +1127,47 @@ int smpc_solve(smpc_factor_t* f, const smpc_step_data* data, const smpc_solve_op
   // arrival counters are reset by the CTAs that consume them; a solve that was cut
   // short by a device error may leave some behind
   CK(cudaMemsetAsync(f->counters, 0, sizeof(int) * (size_t)n, s));
+  CK(cudaMemsetAsync(f->tree_done, 0xff, sizeof(int) * (size_t)f->R, s));  // after init_duals, which reads it
+  if (f->res_tree)
+    CK(cudaMemsetAsync(f->res_tree, 0, sizeof(unsigned long long) * 3 * (size_t)f->R * (size_t)(iters + 2), s));
   CK(cudaMemsetAsync(f->flags, 0xff, sizeof(int), s));
   CK(cudaMemsetAsync(f->flags + 1, 0, sizeof(int), s));
   CK(cudaMemsetAsync(f->res, 0, sizeof(unsigned long long) * 3 * (size_t)(iters + 2), s));
+  *args_out = a;
+  return SMPC_OK;
+}
+
+// After the iteration chunks: the last prox (the tail launch), the final dual and the
+// outputs, enqueued on s; marks the factor's last solve.
+int solve_end(smpc_factor_t* f, IterPlan& plan, const IterArgs& a, int launched, smpc_result* res, cudaStream_t s) {
+  const int n = f->n, n_x = f->n_x, n_u = f->n_u;
+  TRY(launch_planned(plan, launched, MODE_PROX | MODE_CHECK, s));
+  TRY(launch_copy_final_y(f->prec, a, launched, res->y, s));
+  if (res->u) CK(cudaMemcpyAsync(res->u, f->uout, (size_t)n * n_u * f->vs, cudaMemcpyDefault, s));
+  if (res->x) CK(cudaMemcpyAsync(res->x, f->xout, (size_t)n * n_x * f->vs, cudaMemcpyDefault, s));
+  f->solved_once = true;
+  f->last_static = false;
+  f->last_stream = s;
+  f->last_launches = 6 + plan.kernels + 1;  // convert, 3 cost update, init, iterations and tail, final y
+  res->launches = f->last_launches;
+  res->iterations = -1;
+  return SMPC_OK;
+}
+}  // namespace smpc
+
+extern "C" {
+
+int smpc_solve(smpc_factor_t* f, const smpc_step_data* data, const smpc_solve_opts* opts, smpc_result* res,
+               void* stream) {
+  if (!res) {
+    set_error("NULL argument");
+    return SMPC_EINVAL;
+  }
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  IterPlan plan;
+  IterArgs a;
+  TRY(solve_begin(f, data, opts, s, &plan, &a));
+  const int iters = opts->max_iters;
   const int chunk = opts->check_every > 0 ? opts->check_every : 128;
   int launched = 0, chunks = 0;
   bool stop = false;
@@ -1138,19 +1192,12 @@ int smpc_solve(smpc_factor_t* f, const smpc_step_data* data, const smpc_solve_op
     CK(cudaEventRecord(f->ev[slot], s));
     ++chunks;
   }
-  TRY(launch_planned(plan, launched, MODE_PROX | MODE_CHECK, s));
-  TRY(launch_copy_final_y(f->prec, a, launched, res->y, s));
-  if (res->u) CK(cudaMemcpyAsync(res->u, f->uout, (size_t)n * n_u * f->vs, cudaMemcpyDefault, s));
-  if (res->x) CK(cudaMemcpyAsync(res->x, f->xout, (size_t)n * n_x * f->vs, cudaMemcpyDefault, s));
-  f->solved_once = true;
-  f->last_static = false;
-  f->last_stream = s;
-  f->last_launches = 6 + plan.kernels + 1;  // convert, 3 cost update, init, iterations and tail, final y
-  res->launches = f->last_launches;
-  res->iterations = -1;
+  TRY(solve_end(f, plan, a, launched, res, s));
   if (!opts->sync) return SMPC_OK;
   return smpc_solve_info(f, res);
 }
+
+
 
 int smpc_profile_solve(smpc_factor_t* f, const smpc_step_data* data, int32_t iters, double* stage_ms,
                        int32_t max_stages) {
@@ -1199,6 +1246,43 @@ int smpc_profile_solve(smpc_factor_t* f, const smpc_step_data* data, int32_t ite
   const int n = std::min(P.stages, (int)max_stages);
   for (int j = 0; j < n; ++j) stage_ms[j] = ms[j] / P.count;
   return P.stages;
+}
+
+int smpc_solve_trees(smpc_factor_t* f, int32_t* iterations, double* rho_rel) {
+  if (!f || (!iterations && !rho_rel)) {
+    set_error("NULL argument");
+    return SMPC_EINVAL;
+  }
+  if (!f->solved_once) {
+    set_error("no solve to report");
+    return SMPC_EINVAL;
+  }
+  if (f->last_static) {
+    set_error("the factor's last solve ran through smpc_solve_static, which keeps no per-tree record");
+    return SMPC_EINVAL;
+  }
+  CK(cudaStreamSynchronize(f->last_stream));
+  const int R = f->R;
+  int fl[2];
+  CK(cudaMemcpy(fl, f->flags, sizeof fl, cudaMemcpyDeviceToHost));
+  std::vector<int> done(R, -1);
+  CK(cudaMemcpy(done.data(), f->tree_done, sizeof(int) * R, cudaMemcpyDeviceToHost));
+  for (int r = 0; r < R; ++r) {
+    const int it = done[r] >= 0 ? done[r] : fl[0];
+    if (iterations) iterations[r] = it;
+    if (!rho_rel) continue;
+    rho_rel[r] = 0;
+    if (it < 1) continue;
+    unsigned long long q[3];
+    // a forest's own residual per tree; a single tree's is the solve's
+    const unsigned long long* src = f->res_tree ? f->res_tree + 3 * ((size_t)(it - 1) * R + r)
+                                                : f->res + 3 * (size_t)(it - 1);
+    CK(cudaMemcpy(q, src, sizeof q, cudaMemcpyDeviceToHost));
+    double v[3];
+    std::memcpy(v, q, sizeof v);
+    rho_rel[r] = v[0] / (1.0 + std::max(v[1], v[2]));
+  }
+  return SMPC_OK;
 }
 
 int smpc_solve_info(smpc_factor_t* f, smpc_result* res) {

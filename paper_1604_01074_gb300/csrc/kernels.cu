@@ -115,10 +115,22 @@ __device__ __forceinline__ uint64_t global_ns() {
   asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
   return t;
 }
-// Wait for phase `parity` of barrier b; gives up after limit_ns and returns false.
-// Waits that let copies already in flight land before a CTA leaves always take the
-// long bound kWaitNs.
+// Non-blocking test of phase `parity` of barrier b.
+__device__ __forceinline__ bool mbar_test_now(uint64_t* b, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tmbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(b)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Wait for phase `parity` of barrier b; gives up after limit_ns and returns false
+// (limit 0: one non-blocking test).  Waits that let copies already in flight land
+// before a CTA leaves always take the long bound kWaitNs.
 __device__ bool mbar_wait(uint64_t* b, uint32_t parity, uint64_t limit_ns = kWaitNs) {
+  if (limit_ns == 0) return mbar_test_now(b, parity);
   if (mbar_test(b, parity)) return true;
   const uint64_t t0 = global_ns();
   while (!mbar_test(b, parity)) {
@@ -135,6 +147,49 @@ __device__ __forceinline__ T ldcg(const T* p) {
 __device__ __forceinline__ void atomic_max_nonneg(unsigned long long* slot, double v) {
   if (!(v >= 0.0)) v = __longlong_as_double(0x7ff0000000000000ll);  // NaN -> +inf
   atomicMax(slot, static_cast<unsigned long long>(__double_as_longlong(v)));
+}
+
+// Forests with a stop per tree: tree r takes no further forward-sweep or prox writes from
+// launch nu on once it stopped, i.e. when its own relative residual of iteration nu - 2 (or
+// an earlier one) met tol.  Every kernel reaches the same answer: the residual of nu - 2 is
+// final when launch nu starts, and tree_done records earlier stops.
+__device__ __forceinline__ bool tree_stops(const unsigned long long* q, double tol) {
+  const double rho = __longlong_as_double((long long)ldcg(q + 0));
+  const double hz = __longlong_as_double((long long)ldcg(q + 1));
+  const double tt = __longlong_as_double((long long)ldcg(q + 2));
+  return rho / (1.0 + fmax(hz, tt)) <= tol;
+}
+__device__ __forceinline__ bool tree_active(const IterArgs& a, int r, int nu) {
+  if (!a.res_tree) return true;
+  if (ldcg(a.tree_done + r) >= 0) return false;
+  if (!(a.tol > 0) || nu < 2) return true;
+  return !tree_stops(a.res_tree + 3ll * ((long long)(nu - 2) * a.R + r), a.tol);
+}
+// per-tree residual maxima of a CTA, combined in shared memory when the forest is small
+constexpr int kTreeTable = 64;
+__device__ __forceinline__ void tree_res_add(const IterArgs& a, unsigned long long* table, int r, int nu, double rm,
+                                             double hm, double tm) {
+  if (a.R <= kTreeTable) {
+    atomic_max_nonneg(table + 3 * r + 0, rm);
+    atomic_max_nonneg(table + 3 * r + 1, hm);
+    atomic_max_nonneg(table + 3 * r + 2, tm);
+  } else {
+    unsigned long long* q = a.res_tree + 3ll * ((long long)(nu - 1) * a.R + r);
+    atomic_max_nonneg(q + 0, rm);
+    atomic_max_nonneg(q + 1, hm);
+    atomic_max_nonneg(q + 2, tm);
+  }
+}
+__device__ __forceinline__ void tree_table_clear(const IterArgs& a, unsigned long long* table) {
+  if (a.res_tree && a.R <= kTreeTable)
+    for (int q = threadIdx.x; q < 3 * a.R; q += blockDim.x) table[q] = 0;
+}
+// after a block barrier: the CTA's table into the iteration's per-tree residuals
+__device__ __forceinline__ void tree_table_flush(const IterArgs& a, const unsigned long long* table, int nu) {
+  if (!a.res_tree || a.R > kTreeTable) return;
+  unsigned long long* dst = a.res_tree + 3ll * (long long)(nu - 1) * a.R;
+  for (int q = threadIdx.x; q < 3 * a.R; q += blockDim.x)
+    if (table[q]) atomicMax(dst + q, table[q]);
 }
 
 template <typename AT>
@@ -478,6 +533,7 @@ struct Kern {
   // is slow on this GPU), power-iteration sums in float64
   AT rmax = 0, hzmax = 0, tmax = 0;
   double pnrm = 0, pdot = 0;
+  unsigned long long* ttab = nullptr;  // forests with a stop per tree: the CTA's per-tree residuals
 
   __device__ Kern(const IterArgs& args, Smem<MT>& s, int S_, int nu_, int mode_)
       : a(args), sm(s), S(S_), nu(nu_), mode(mode_), nd(2 * args.n_x + args.n_u) {}
@@ -696,6 +752,8 @@ struct Kern {
   // lambda (x - t) however large |w| is.
   static constexpr int kB = 8;
   __device__ void phase_p(int par, const int* nodes, int len) {
+    const int tree = a.tree_of[nodes[0]];
+    if (!tree_active(a, tree, nu)) return;  // a forest's tree that stopped keeps its iterates
     const int e = threadIdx.x, lane = e & 31, warp = e >> 5;
     const bool tank = e < a.n_x, input = !tank && e < a.n_k;
     const int i = e - a.n_x;
@@ -869,7 +927,7 @@ struct Kern {
               rm = fmax(rm, fmax(fabs(es), fabs(ez)));
               hm = fmax(hm, fabs(x));
               tm = fmax(tm, fmax(fabs(x - es), fabs(x - ez)));
-              if (!isfinite(st_val(ysn)) || !isfinite(st_val(yzn))) a.flags[1] = SMPC_EDIVERGED;
+              if (!isfinite(st_val(ysn)) || !isfinite(st_val(yzn)) || !isfinite(x)) a.flags[1] = SMPC_EDIVERGED;
             } else {
               const ST wp = st_extrap(v1[r], v2[r], c);
               const ST ypn = box_lr(st_axpy(wp, l1[r], x - uhi), st_axpy(wp, l1[r], x - ulo));
@@ -879,7 +937,7 @@ struct Kern {
               rm = fmax(rm, fabs(ep));
               hm = fmax(hm, fabs(x));
               tm = fmax(tm, fabs(x - ep));
-              if (!isfinite(st_val(ypn))) a.flags[1] = SMPC_EDIVERGED;
+              if (!isfinite(st_val(ypn)) || !isfinite(x)) a.flags[1] = SMPC_EDIVERGED;
             }
           }
         }
@@ -889,6 +947,10 @@ struct Kern {
     rmax = fmax(rmax, rm);
     hzmax = fmax(hzmax, hm);
     tmax = fmax(tmax, tm);
+    if (ttab && !lin) {
+      const AT r_ = warp_max(rm), h_ = warp_max(hm), t_ = warp_max(tm);
+      if (lane == 0) tree_res_add(a, ttab, tree, nu, (double)r_, (double)h_, (double)t_);
+    }
   }
 
   // w^nu of the segment's nodes without a prox (first iteration, power iteration).
@@ -1006,7 +1068,7 @@ struct Kern {
             rm = fmax(rm, fmax(fabs(es), fabs(ez)));
             hm = fmax(hm, fabs(x));
             tm = fmax(tm, fmax(fabs(x - es), fabs(x - ez)));
-            if (!isfinite(st_val(ysn)) || !isfinite(st_val(yzn))) a.flags[1] = SMPC_EDIVERGED;
+            if (!isfinite(st_val(ysn)) || !isfinite(st_val(yzn)) || !isfinite(x)) a.flags[1] = SMPC_EDIVERGED;
           } else if (e < a.n_k) {
             const int i = e - a.n_x;
             const AT u = U[k];
@@ -1020,7 +1082,7 @@ struct Kern {
             rm = fmax(rm, fabs(ep));
             hm = fmax(hm, fabs(u));
             tm = fmax(tm, fabs(u - ep));
-            if (!isfinite(st_val(ypn))) a.flags[1] = SMPC_EDIVERGED;
+            if (!isfinite(st_val(ypn)) || !isfinite(u)) a.flags[1] = SMPC_EDIVERGED;
           }
         }
         rmax = fmax(rmax, rm);
@@ -1060,7 +1122,7 @@ struct Kern {
   // the launch pays one load latency per node and its code stays small.  stage: this
   // warp's region of prox_stage_bytes; bnd: x_s, x_max, x_min, u_max, u_min in shared
   // memory, kThreads apart.
-  __device__ void warp_prox_staged(int m, const AT* bnd, unsigned char* stage) {
+  __device__ void warp_prox_staged(int m, const AT* bnd, unsigned char* stage, int tree = -1) {
     const int lane = threadIdx.x & 31;
     const int n_x = a.n_x, n_k = a.n_k, n_u = a.n_u;
     ST* Q0 = reinterpret_cast<ST*>(stage);  // y1, y2 of entry e's (first) block: n_k each
@@ -1134,7 +1196,8 @@ struct Kern {
         rm = fmax(rm, fmax(fabs(es), fabs(ez)));
         hm = fmax(hm, fabs(x));
         tm = fmax(tm, fmax(fabs(x - es), fabs(x - ez)));
-        if (!isfinite(st_val(ysn)) || !isfinite(st_val(yzn))) a.flags[1] = SMPC_EDIVERGED;
+        // the prox maps a non-finite v to 0, so the primal iterate is checked as well
+        if (!isfinite(st_val(ysn)) || !isfinite(st_val(yzn)) || !isfinite(x)) a.flags[1] = SMPC_EDIVERGED;
       } else {
         const int i = e - n_x;
         const AT u = (AT)Z[e];
@@ -1148,12 +1211,16 @@ struct Kern {
         rm = fmax(rm, fabs(ep));
         hm = fmax(hm, fabs(u));
         tm = fmax(tm, fabs(u - ep));
-        if (!isfinite(st_val(ypn))) a.flags[1] = SMPC_EDIVERGED;
+        if (!isfinite(st_val(ypn)) || !isfinite(u)) a.flags[1] = SMPC_EDIVERGED;
       }
     }
     rmax = fmax(rmax, rm);
     hzmax = fmax(hzmax, hm);
     tmax = fmax(tmax, tm);
+    if (ttab && tree >= 0) {
+      const AT r_ = warp_max(rm), h_ = warp_max(hm), t_ = warp_max(tm);
+      if (lane == 0) tree_res_add(a, ttab, tree, nu, (double)r_, (double)h_, (double)t_);
+    }
   }
 
   // ---------------------------------------------------------- backward sweep
@@ -1401,7 +1468,7 @@ __device__ bool early_exit(const IterArgs& a, int nu, int mode, int* flag, bool 
         r2 = ldcg(r + 2);
       }
       if (done >= 0 || err != 0) stop = 1;
-      if (test && !stop) {
+      if (test && !stop && !a.res_tree) {
         const double rho = __longlong_as_double((long long)r0);
         const double hz = __longlong_as_double((long long)r1);
         const double tt = __longlong_as_double((long long)r2);
@@ -1414,6 +1481,22 @@ __device__ bool early_exit(const IterArgs& a, int nu, int mode, int* flag, bool 
     *flag = stop;
   }
   __syncthreads();
+  if (*flag == 0 && (mode & MODE_CHECK) && decide && a.res_tree && a.tol > 0 && nu >= 2) {
+    // a stop per tree: block 0 records the trees that stop at this launch; the solve ends
+    // when every tree has stopped (each CTA reaches the same answer)
+    bool all = true;
+    for (int r = threadIdx.x; r < a.R; r += blockDim.x) {
+      const bool was = ldcg(a.tree_done + r) >= 0;
+      const bool now = !was && tree_stops(a.res_tree + 3ll * ((long long)(nu - 2) * a.R + r), a.tol);
+      if (now && blockIdx.x == 0) a.tree_done[r] = nu - 1;
+      all = all && (was || now);
+    }
+    all = __syncthreads_and(all);
+    if (all) {
+      if (blockIdx.x == 0 && threadIdx.x == 0) a.flags[0] = nu - 1;
+      return true;
+    }
+  }
   return *flag != 0;
 }
 
@@ -1422,10 +1505,21 @@ __global__ void __launch_bounds__(kThreads, 1)
     apg_iter(const __grid_constant__ IterArgs a, int S, int nu, int mode) {
   grid_dep_sync();
   extern __shared__ __align__(128) unsigned char smem_raw[];
+  __shared__ unsigned long long ttab[3 * kTreeTable];
   Smem<MT> sm = carve<MT>(smem_raw, S, a.n_x, a.n_u, a.n_v);
   if (early_exit(a, nu, mode, sm.flag + 1, true)) return;
   Kern<VT, MT> k(a, sm, S, nu, mode);
+  const bool tabled = a.res_tree && (mode & MODE_PROX) && nu >= 1 && !(mode & MODE_LINEAR);
+  if (tabled) {
+    tree_table_clear(a, ttab);
+    __syncthreads();
+    k.ttab = ttab;
+  }
   k.run();
+  if (tabled) {
+    __syncthreads();
+    tree_table_flush(a, ttab, nu);
+  }
 }
 
 // ------------------------------------------------------------------ node-parallel schedule
@@ -1475,6 +1569,7 @@ __global__ void __launch_bounds__(kThreads) fwd_scan(const __grid_constant__ Ite
     const int4 d0 = *reinterpret_cast<const int4*>(a.seg + (long long)kSegInts * b);
     const int4 d1 = *reinterpret_cast<const int4*>(a.seg + (long long)kSegInts * b + 4);
     const int pb = d0.y, pl = d0.z, cb = d1.x, len = d1.y;
+    if (!tree_active(a, d0.w, nu)) continue;  // a forest's tree that stopped keeps x and u
     const int L = pl + len;  // the path (root .. par), then the chain
     AT V = 0, U = 0;
     AT X = (act && tank && !lin) ? (AT)reinterpret_cast<const VT*>(a.p0)[(long long)d0.w * a.n_x + e] : (AT)0;
@@ -1530,6 +1625,7 @@ __global__ void __launch_bounds__(kThreads, 3) prox_node(const __grid_constant__
   using AT = typename Acc<MT>::T;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   __shared__ AT bnd[5 * kThreads];  // x_s, x_max, x_min, u_max, u_min
+  __shared__ unsigned long long ttab[3 * kTreeTable];
   Smem<MT> sm = carve<MT>(smem_raw, 0, a.n_x, a.n_u, a.n_v);
   // the forward sweep (when there is one) already took the stop decision
   const bool decide = !((mode & MODE_PROX) && nu >= 1);
@@ -1552,9 +1648,20 @@ __global__ void __launch_bounds__(kThreads, 3) prox_node(const __grid_constant__
     __syncthreads();
     unsigned char* stage = smem_raw + iter_smem_bytes<MT>(0, a.n_x, a.n_u, a.n_v) +
                            (size_t)warp * prox_stage_bytes<VT>(a.n_x, a.n_u);
+    if (a.res_tree) {
+      tree_table_clear(a, ttab);
+      __syncthreads();
+      k.ttab = ttab;
+    }
     for (int m = blockIdx.x * kWarps + warp; m < a.n; m += gridDim.x * kWarps) {
-      k.warp_prox_staged(m, bnd, stage);
+      const int r = a.res_tree ? a.tree_of[m] : -1;
+      if (r >= 0 && !tree_active(a, r, nu)) continue;  // a forest's tree that stopped keeps its iterates
+      k.warp_prox_staged(m, bnd, stage, r);
       __syncwarp();  // the lanes' reads of the staging are done before the next node's copies
+    }
+    if (a.res_tree) {
+      __syncthreads();
+      tree_table_flush(a, ttab, nu);
     }
   } else {
     for (int m = blockIdx.x * kWarps + warp; m < a.n; m += gridDim.x * kWarps)
@@ -1825,23 +1932,38 @@ __global__ void final_y_kernel(IterArgs a, int max_iters, VT* dst) {
   __syncthreads();
   if (blockIdx.x == 0 && threadIdx.x == 0) a.flags[0] = it;
   if (!dst) return;
-  const ST* src = reinterpret_cast<const ST*>((it & 1) ? a.ybuf1 : a.ybuf0);
-  const long long total = (long long)a.n * (2 * a.n_x + a.n_u);
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x)
+  const int nd = 2 * a.n_x + a.n_u;
+  const long long total = (long long)a.n * nd;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x) {
+    int itn = it;  // a forest's tree that stopped early ends at its own iteration count
+    if (a.tree_done) {
+      const int d = a.tree_done[a.tree_of[i / nd]];
+      if (d >= 0) itn = d;
+    }
+    const ST* src = reinterpret_cast<const ST*>((itn & 1) ? a.ybuf1 : a.ybuf0);
     dst[i] = (VT)st_val(src[i]);
+  }
 }
 
 template <typename VT>
 __global__ void init_duals_kernel(IterArgs a, int warm) {
   // cold: y^0 = y^{-1} = 0 ; warm: both = the final dual of the previous solve
   using ST = typename St<VT>::T;
-  const long long total = (long long)a.n * (2 * a.n_x + a.n_u);
-  int it = a.flags[0];
-  const ST* src = reinterpret_cast<const ST*>((it & 1) ? a.ybuf1 : a.ybuf0);
+  const int nd = 2 * a.n_x + a.n_u;
+  const long long total = (long long)a.n * nd;
+  const int it = a.flags[0];
   ST* y0 = reinterpret_cast<ST*>(a.ybuf0);
   ST* y1 = reinterpret_cast<ST*>(a.ybuf1);
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x) {
-    const ST v = warm ? src[i] : st_from<ST>(0.0);
+    ST v = st_from<ST>(0.0);
+    if (warm) {  // each tree of a forest ended at its own iteration count
+      int itn = it;
+      if (a.tree_done) {
+        const int d = a.tree_done[a.tree_of[i / nd]];
+        if (d >= 0) itn = d;
+      }
+      v = ((itn & 1) ? y1 : y0)[i];
+    }
     y0[i] = v;
     y1[i] = v;
   }

@@ -238,6 +238,11 @@ extern "C" int smpc_solve_static(smpc_factor_t* f, const smpc_step_data* data, c
   a.counters = counters;
   a.flags = flags;
   a.wait_ns = f->wait_ns;
+  // one residual for a whole forest here (no stop per tree): the per-tree record is
+  // read by the warm start below, then cleared
+  a.R = f->R;
+  a.res_tree = nullptr;
+  a.tree_done = f->tree_done;
   IterPlan plan;
   STRY(plan_iters(f, a, *opts, &plan));
 
@@ -297,6 +302,7 @@ extern "C" int smpc_solve_static(smpc_factor_t* f, const smpc_step_data* data, c
     ai.flags = f->flags;
     STRY(launch_init_duals(f->prec, ai, (opts->warm_start && f->solved_once) ? 1 : 0, s));
   }
+  SCK(cudaMemsetAsync(f->tree_done, 0xff, sizeof(int) * (size_t)f->R, s));
   // what must start at zero (the array keeps the previous call's contents)
   SCK(cudaMemsetAsync(counters, 0, sizeof(int) * (size_t)n, s));
   SCK(cudaMemsetAsync(flags, 0xff, sizeof(int), s));

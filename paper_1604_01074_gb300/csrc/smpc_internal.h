@@ -133,6 +133,13 @@ struct IterArgs {
   double* pw;                    // power iteration: [k] ||y_k||^2, [K + k] <y_k, y_{k+1}>
   int pw_len;
   unsigned long long wait_ns;    // bound of the per-node pack pipeline waits of node_mv
+  // Forests (R > 1 trees): each tree stops at its own first iterate whose relative residual
+  // meets tol.  res_tree: per iteration and tree, (rho, ||Hz||, ||t||) as float64 bits, or
+  // NULL (one residual for the whole forest); tree_done: per tree, the iterations it ran
+  // once it stopped, -1 while it runs (NULL: none).
+  int R;
+  unsigned long long* res_tree;
+  int* tree_done;
 };
 
 enum KernelMode : int {
@@ -247,6 +254,13 @@ size_t mat_size(int prec);
 }  // namespace smpc
 
 namespace smpc {
+// The parts of smpc_solve around its iteration chunks (api.cpp), shared with the batch
+// solve (batch.cpp): solve_begin checks the call, plans the launches and enqueues the
+// step-data upload, the cost update, the initial duals and the per-solve flags;
+// solve_end enqueues the tail launch, the final dual and the outputs.
+int solve_begin(smpc_factor_t* f, const smpc_step_data* data, const smpc_solve_opts* opts, cudaStream_t s,
+                IterPlan* plan, IterArgs* args);
+int solve_end(smpc_factor_t* f, IterPlan& plan, const IterArgs& a, int launched, smpc_result* res, cudaStream_t s);
 // Validates polish_iters and the kernel configuration; SMPC_ENOTSUP when the network
 // does not fit the shared-memory pipeline.
 int plan_iters(const smpc_factor_t* f, const IterArgs& a, const smpc_solve_opts& opts, IterPlan* plan);
@@ -289,6 +303,8 @@ struct smpc_factor_t {
   int* flags = nullptr;
   int* flags_host = nullptr;  // pinned, 2 x 2 ints
   unsigned long long* res = nullptr;
+  unsigned long long* res_tree = nullptr;  // forests: cap x R x 3 per-tree residuals
+  int* tree_done = nullptr;                // forests: R per-tree iteration counts (-1 running)
   double* cvec = nullptr;
   int cap = 0;                // iterations the res/cvec buffers hold
   int cvec_for = -1;

@@ -1,13 +1,15 @@
 """Error paths of the solve, reached without any GPU fault:
 
 * SMPC_EDIVERGED: steps far above 1 / L make the APG iteration grow geometrically
-  until the duals overflow; device-resident step data holding a NaN (host data is
-  refused before any device work) gives non-finite iterates at once.
+  until the iterates overflow; device-resident step data holding a NaN (host data is
+  refused before any device work) gives non-finite primal iterates at once (the prox
+  maps a non-finite argument to 0, so the primal iterate is checked too).
 * SMPC_ENOMEM: a factor whose per-node packs need more device memory than the GPU
   has (a 2-million-node tree with the 63-tank network in float64: about 430 GB);
   cudaMalloc refuses it and nothing is launched.
-* SMPC_ETIMEOUT: a test-only bound of one nanosecond on node_mv's pack-pipeline waits
-  (SMPC_PIPELINE_WAIT_NS, read when a factor is created) makes the first wait give up;
+* SMPC_ETIMEOUT: a test-only bound of zero on node_mv's pack-pipeline waits (one
+  non-blocking test; SMPC_PIPELINE_WAIT_NS, read when a factor is created) makes a wait
+  whose copy has not landed yet give up;
   the CTA records the error, lets its copies in flight land under the normal 2 s
   bound and returns, and the other kernels of the solve see the error flag and exit.
 After each, the same process solves a fresh factor normally.
@@ -106,7 +108,7 @@ def test_pipeline_wait_that_gives_up_reports_etimeout():
     P = synth.barcelona(0)
     tree, fac, _ = H.oracle_build(P)
     steps = H.closed_form_steps(fac, tree, 1e-6)
-    os.environ["SMPC_PIPELINE_WAIT_NS"] = "1"
+    os.environ["SMPC_PIPELINE_WAIT_NS"] = "0"
     try:
         g = H.Gpu(P, steps=steps, precision=1, schedule=2)
     finally:

@@ -56,15 +56,54 @@ def test_forest_matches_each_tree_alone(schedule, shared):
 
 @pytest.mark.parametrize("precision", [1, 2])
 def test_forest_reduced_precision(precision):
+    """Every member tree of a float32 / bfloat16 forest against the FP64 oracle run on that
+    tree alone: the elementwise bounds of the full-size reduced-precision tests
+    (1e-4 and 2e-3 relative to 1 + the largest entry) and |rho_rel| of each tree within 1e-4."""
     members, F, steps, per = _forest_case(4, 4)
+    iters = 300
     g = H.Gpu(F, steps=steps, precision=precision, shared_packs=1)
     try:
-        info = g.solve(300)
+        g.solve(iters)
+        u, x, y = g.arrays()
+        its, rr = g.smpc.smpc_solve_trees(g.fac, len(members))
     finally:
         g.close()
-    g64 = H.Gpu(F, steps=steps, precision=0, shared_packs=1)
+    bound = {1: 1e-4, 2: 2e-3}[precision]
+    for r, P in enumerate(members):
+        R = H.oracle_run(P, per[r], iters)
+        idx = F["members"][r]
+        e = (H.relerr(u[idx], R.u), H.relerr(x[idx], R.x), H.relerr(y[idx], H.stack_y(R.y)))
+        assert max(e) <= bound, (r, e)
+        assert its[r] == iters
+        assert abs(rr[r] - R.rho_rel[-1]) <= 1e-4, (r, rr[r], R.rho_rel[-1])
+
+
+@pytest.mark.parametrize("schedule", [1, 2, 3])
+@pytest.mark.parametrize("shared", [0, 1])
+def test_forest_stops_each_tree_on_its_own(schedule, shared):
+    """With a tolerance, every tree of a forest stops at its own first iterate whose relative
+    residual (over that tree's nodes, Sec. IV-E) meets it, exactly as the oracle stops on
+    that tree alone; the stopped tree keeps that iterate while the others go on."""
+    members, F, steps, per = _forest_case(7, 5)
+    tol, cap = 2e-4, 4000
+    g = H.Gpu(F, steps=steps, schedule=schedule, shared_packs=shared)
     try:
-        ref = g64.solve(300)
+        info = g.solve(cap, tol=tol, check_every=32)
+        u, x, y = g.arrays()
+        its, rr = g.smpc.smpc_solve_trees(g.fac, len(members))
     finally:
-        g64.close()
-    assert abs(info["rho_rel"] - ref["rho_rel"]) <= 1e-4
+        g.close()
+    counts = []
+    for r, P in enumerate(members):
+        tree, fac, cu = H.oracle_build(P)
+        R = oracle.apg(fac, tree, cu, P["cost"], P["p"], per[r], cap, tol=tol)
+        k = len(R.rho_rel)
+        counts.append(k)
+        assert R.rho_rel[-1] <= tol, r
+        assert its[r] == k, (r, its[r], k)
+        idx = F["members"][r]
+        e = (H.relerr(u[idx], R.u), H.relerr(x[idx], R.x), H.relerr(y[idx], H.stack_y(R.y)))
+        assert max(e) <= FP64_TOL, (r, e)
+        assert abs(rr[r] - R.rho_rel[-1]) <= 1e-9, (r, rr[r], R.rho_rel[-1])
+    assert len(set(counts)) > 1, counts  # the trees stop at different iterations
+    assert info["iterations"] == max(counts)
