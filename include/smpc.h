@@ -115,9 +115,16 @@ typedef struct smpc_factor_opts {
   /* Iteration schedule: 1 = one launch per iteration with one CTA per chain (maximal
    * leaf path) of the tree; 2 = the backward sweep as subtree scans around per-node
    * mat-vec launches, one task per node; 3 = node-parallel forward sweep and prox, a chain
-   * pass up to r, and the node-parallel Lambda / [Bbar; L] launch; 0 = time all of them on
-   * this GPU when the factor is built and keep the fastest.  Results agree to rounding. */
+   * pass up to r, and the node-parallel Lambda / [Bbar; L] launch; 4 = node-parallel forward
+   * sweep and prox, then the whole backward sweep as one chain pass (every pack read once
+   * per iteration); 0 = time all of them on this GPU when the factor is built and keep the
+   * fastest.  Results agree to rounding. */
   int32_t schedule;
+  /* SMPC_BF16 with shared_packs = 1: the Lambda and [Bbar; L] products of the delta
+   * iterations run on the tensor cores as GEMMs over tc_width nodes at a time (16, 32 or
+   * 64); 0 = time the three widths on this GPU when the factor is built and keep the
+   * fastest.  Ignored otherwise.  Results are the same for every width. */
+  int32_t tc_width;
 } smpc_factor_opts;
 
 /* Per-solve data (Alg. 2, steps 1-2).  float64; each pointer may address host or
@@ -207,10 +214,10 @@ void smpc_factor_destroy(smpc_factor_t* fac);
  * shapes as in smpc_factor_opts). */
 int smpc_factor_steps(const smpc_factor_t* fac, double* lambda, double* step_s, double* step_z,
                       double* step_p);
-/* Returns the schedule the factor uses (1, 2 or 3, see smpc_factor_opts.schedule), or minus
- * SMPC_EINVAL for a NULL factor.  When ms_per_iter is not NULL, ms_per_iter[0..2] receive the
- * measured ms per iteration of schedules 1, 2 and 3 when the factor chose among them (0 when
- * it did not time them). */
+/* Returns the schedule the factor uses (1 to 4, see smpc_factor_opts.schedule), or minus
+ * SMPC_EINVAL for a NULL factor.  When ms_per_iter is not NULL, ms_per_iter[0..3] receive the
+ * measured ms per iteration of schedules 1, 2, 3 and 4 when the factor chose among them (0
+ * when it did not time them). */
 int smpc_factor_schedule(const smpc_factor_t* fac, double* ms_per_iter);
 
 /* One SMPC solve (Alg. 2 step 3): the cost update of App. A on the device from
@@ -279,7 +286,8 @@ void smpc_batch_destroy(smpc_batch* batch);
  * (apg_iter), 6 for schedule 2 (forward sweep, prox and dual update, subtree scan of s,
  * [Bbar; L]' mat-vec, subtree scan of r, Lambda and [Bbar; L] mat-vecs) and 4 for schedule 3
  * (forward sweep; prox and dual update; s, [Bbar; L]' mat-vecs and r along the chains; Lambda
- * and [Bbar; L] mat-vecs).  SMPC_BF16 anchor iterations are not timed.  Leaves
+ * and [Bbar; L] mat-vecs) and 3 for schedule 4 (forward sweep; prox and dual update; the
+ * whole backward sweep along the chains).  SMPC_BF16 anchor iterations are not timed.  Leaves
  * the factor's duals as that solve ends.  Returns n, or minus an smpc_status. */
 int smpc_profile_solve(smpc_factor_t* fac, const smpc_step_data* data, int32_t iters, double* stage_ms,
                        int32_t max_stages);
@@ -292,6 +300,12 @@ int smpc_profile_solve(smpc_factor_t* fac, const smpc_step_data* data, int32_t i
  * entry read).  Allocates and frees a small device buffer.
  * Errors: SMPC_EINVAL (other precision, NULL result), SMPC_ENOMEM, SMPC_ECUDA. */
 int smpc_fma_peak(int32_t precision, double* tflops);
+
+/* The tensor-core GEMM width (nodes per GEMM) a bfloat16 shared-pack factor uses, or 0
+ * when its launches do not use the tensor cores; minus SMPC_EINVAL for a NULL factor.  When
+ * ms_per_width is not NULL, ms_per_width[0..2] receive the measured ms per delta iteration
+ * with widths 16, 32 and 64 (0 when not timed). */
+int smpc_factor_tc_width(const smpc_factor_t* fac, double* ms_per_width);
 
 /* Per-tree results of the factor's last smpc_solve (waits for its stream).  In a forest
  * (smpc_tree_create with R roots) every tree stops at its own first iterate whose

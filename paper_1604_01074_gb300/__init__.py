@@ -37,7 +37,7 @@ class smpc_factor_opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int32), ("precondition", ctypes.c_int32), ("lambda_", ctypes.c_double),
                 ("power_iters", ctypes.c_int32), ("lambda_margin", ctypes.c_double),
                 ("step_s", _dp), ("step_z", _dp), ("step_p", _dp), ("shared_packs", ctypes.c_int32),
-                ("schedule", ctypes.c_int32)]
+                ("schedule", ctypes.c_int32), ("tc_width", ctypes.c_int32)]
 
 
 class smpc_step_data(ctypes.Structure):
@@ -88,6 +88,7 @@ SIGNATURES = {
                                          ctypes.POINTER(smpc_solve_opts), ctypes.POINTER(smpc_result), ctypes.c_void_p]),
     "smpc_fma_peak": (ctypes.c_int, [ctypes.c_int32, _dp]),
     "smpc_solve_trees": (ctypes.c_int, [ctypes.c_void_p, _ip, _dp]),
+    "smpc_factor_tc_width": (ctypes.c_int, [ctypes.c_void_p, _dp]),
     "smpc_batch_create": (ctypes.c_int, [ctypes.c_int32, ctypes.POINTER(ctypes.c_void_p),
                                          ctypes.POINTER(ctypes.c_void_p)]),
     "smpc_batch_solve": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(smpc_step_data),
@@ -171,10 +172,11 @@ def smpc_tree_destroy(tree):
 
 
 def smpc_factor(tree, net, cost, precision=SMPC_FP64, precondition=1, lam=0.0, power_iters=0, lambda_margin=0.0,
-                steps=None, safety_unweighted=0, schedule=0, shared_packs=0):
+                steps=None, safety_unweighted=0, schedule=0, shared_packs=0, tc_width=0):
     """net / cost: dicts with the fields of smpc_network / smpc_cost (numpy arrays).
     steps: optional dict {'s': (n,), 'z': (n,), 'p': (n, n_u)} of explicit per-entry steps.
-    schedule: 0 = time the iteration schedules and keep the fastest, 1 = chain, 2 = node, 3 = hybrid."""
+    schedule: 0 = time the iteration schedules and keep the fastest, 1 = chain, 2 = node, 3 = hybrid,
+    4 = fused chain pass."""
     k = _Keep()
     A = net.get("A")
     n_x, n_u = net["B"].shape
@@ -186,7 +188,7 @@ def smpc_factor(tree, net, cost, precision=SMPC_FP64, precondition=1, lam=0.0, p
                   k(cost["x_min"]), k(cost["x_max"]), k(cost["x_s"]), k(cost["u_min"]), k(cost["u_max"]),
                   int(safety_unweighted))
     O = smpc_factor_opts(int(precision), int(precondition), float(lam), int(power_iters), float(lambda_margin),
-                         None, None, None, int(shared_packs), int(schedule))
+                         None, None, None, int(shared_packs), int(schedule), int(tc_width))
     if steps is not None:
         O.step_s, O.step_z, O.step_p = k(steps["s"]), k(steps["z"]), k(steps["p"])
     h = ctypes.c_void_p()
@@ -200,11 +202,20 @@ def smpc_factor_destroy(fac):
 
 def smpc_factor_schedule(fac):
     """(schedule in use, {schedule: ms per iteration} as timed by the factor)."""
-    ms = (ctypes.c_double * 3)()
+    ms = (ctypes.c_double * 4)()
     s = lib().smpc_factor_schedule(fac, ms)
     if s < 0:
         raise SmpcError(-s, smpc_last_error())
-    return s, {1: ms[0], 2: ms[1], 3: ms[2]}
+    return s, {1: ms[0], 2: ms[1], 3: ms[2], 4: ms[3]}
+
+
+def smpc_factor_tc_width(fac):
+    """(nodes per tensor-core GEMM or 0, {16: ms, 32: ms, 64: ms} as timed by the factor)."""
+    ms = (ctypes.c_double * 3)()
+    w = lib().smpc_factor_tc_width(fac, ms)
+    if w < 0:
+        raise SmpcError(-w, smpc_last_error())
+    return w, {16: ms[0], 32: ms[1], 64: ms[2]}
 
 
 def smpc_factor_steps(fac, n, n_u):

@@ -478,9 +478,11 @@ namespace smpc {
 // Iteration schedule of a factor: the requested one, or (0) the fastest on this GPU,
 // timed with CUDA events over a few solve-mode iterations of the factor's own tree and
 // packs from a zero state; the state is cleared again afterwards.
+int reset_state(smpc_factor_t* f);
+
 int choose_schedule(smpc_factor_t* f, int requested) {
   if (requested < 0 || requested > kSchedules) {
-    set_error("schedule must be 0 (auto), 1 (chain), 2 (node) or 3 (hybrid)");
+    set_error("schedule must be 0 (auto), 1 (chain), 2 (node), 3 (hybrid) or 4 (fused chain pass)");
     return SMPC_EINVAL;
   }
   IterArgs a = make_args(f);
@@ -541,7 +543,12 @@ int choose_schedule(smpc_factor_t* f, int requested) {
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  // back to the state a fresh factor has
+  return reset_state(f);
+}
+
+// Back to the state a fresh factor has, after iterations run for timing.
+int reset_state(smpc_factor_t* f) {
+  const bool anchored = f->packs32 != nullptr;
   const size_t ny = (size_t)f->n * f->nd;
   const size_t nk = (size_t)f->n * f->n_k;
   if (cudaMemset(f->ybuf0, 0, ny * kStateSize) != cudaSuccess || cudaMemset(f->ybuf1, 0, ny * kStateSize) != cudaSuccess ||
@@ -557,6 +564,58 @@ int choose_schedule(smpc_factor_t* f, int requested) {
   return SMPC_OK;
 }
 
+// Width of the tensor-core GEMMs (nodes per MMA) of a bfloat16 shared-pack factor: the
+// requested one, or (0) the fastest of 16, 32 and 64 nodes on this GPU, timed over a few
+// delta iterations of the factor's schedule; the state is cleared again afterwards.
+int tune_tc(smpc_factor_t* f, int requested) {
+  IterArgs a = make_args(f);
+  f->tc_width = 0;
+  if (!f->packs32) return SMPC_OK;  // not a bfloat16 factor
+  a.ha = f->ha;
+  a.wa = f->wa;
+  if (!iter_config(f->prec, a, f->num_sms, f->schedule).tc) return SMPC_OK;
+  if (requested != 0) {
+    if (requested != 16 && requested != 32 && requested != 64) {
+      set_error("tc_width must be 0 (by timing), 16, 32 or 64");
+      return SMPC_EINVAL;
+    }
+    f->tc_width = requested;
+    return SMPC_OK;
+  }
+  TRY(upload_cvec(f, 16));
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  constexpr int kWarm = 2, kTimed = 6;
+  float best = -1;
+  const int widths[3] = {16, 32, 64};
+  for (int k = 0; k < 3; ++k) {
+    const LaunchCfg cfg = iter_config(f->prec, a, f->num_sms, f->schedule, widths[k]);
+    if (!cfg.tc || cfg.stages < 1) continue;
+    int rc = SMPC_OK;
+    const int mode = MODE_BWD | MODE_PROX | MODE_DELTA;
+    for (int nu = 1; nu <= kWarm && !rc; ++nu) rc = launch_iter(f->prec, a, cfg, nu, mode, nullptr);
+    cudaEventRecord(e0);
+    for (int nu = kWarm + 1; nu <= kWarm + kTimed && !rc; ++nu) rc = launch_iter(f->prec, a, cfg, nu, mode, nullptr);
+    cudaEventRecord(e1);
+    float ms = 0;
+    if (rc || cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+      cudaEventDestroy(e0);
+      cudaEventDestroy(e1);
+      if (!rc) set_error("tensor-core width timing failed: %s", cudaGetErrorString(cudaGetLastError()));
+      return rc ? rc : SMPC_ECUDA;
+    }
+    f->tc_ms[k] = ms / kTimed;
+    if (best < 0 || ms < best) {
+      best = ms;
+      f->tc_width = widths[k];
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return reset_state(f);
+}
+
 int plan_iters(const smpc_factor_t* f, const IterArgs& a, const smpc_solve_opts& opts, IterPlan* plan) {
   const int iters = opts.max_iters;
   if (opts.polish_iters < 0 || opts.polish_iters > iters || opts.anchor_every < 0) {
@@ -565,7 +624,7 @@ int plan_iters(const smpc_factor_t* f, const IterArgs& a, const smpc_solve_opts&
   }
   plan->prec = f->prec;
   plan->args = a;
-  plan->cfg = iter_config(f->prec, a, f->num_sms, f->schedule);
+  plan->cfg = iter_config(f->prec, a, f->num_sms, f->schedule, f->tc_width);
   if (plan->cfg.stages < 1) {
     set_error("network too large for the shared-memory pipeline");
     return SMPC_ENOTSUP;
@@ -1015,6 +1074,7 @@ int smpc_factor(const smpc_tree* tree, const smpc_network* net, const smpc_cost*
     return fail(SMPC_ECUDA);
   }
   if ((rc = choose_schedule(f, o.schedule))) return fail(rc);
+  if ((rc = tune_tc(f, o.tc_width))) return fail(rc);
   *out = f;
   return SMPC_OK;
 }
@@ -1032,8 +1092,19 @@ int smpc_factor_schedule(const smpc_factor_t* f, double* ms_per_iter) {
     ms_per_iter[0] = f->tuned_ms[SCHED_CHAIN];
     ms_per_iter[1] = f->tuned_ms[SCHED_NODE];
     ms_per_iter[2] = f->tuned_ms[SCHED_HYBRID];
+    ms_per_iter[3] = f->tuned_ms[SCHED_FUSED];
   }
   return f->schedule;
+}
+
+int smpc_factor_tc_width(const smpc_factor_t* f, double* ms_per_width) {
+  if (!f) {
+    set_error("NULL factor");
+    return -SMPC_EINVAL;
+  }
+  if (ms_per_width)
+    for (int k = 0; k < 3; ++k) ms_per_width[k] = f->tc_ms[k];
+  return f->tc_width;
 }
 
 int smpc_factor_steps(const smpc_factor_t* f, double* lambda, double* step_s, double* step_z, double* step_p) {

@@ -2368,7 +2368,7 @@ int optin_smem() {
 }
 
 template <typename VT, typename MT>
-LaunchCfg config_t(const IterArgs& a, int num_sms, int S_max, int schedule) {
+LaunchCfg config_t(const IterArgs& a, int num_sms, int S_max, int schedule, int tc_width = 0) {
   LaunchCfg c;
   const int optin = optin_smem();
   c.schedule = schedule;
@@ -2385,7 +2385,7 @@ LaunchCfg config_t(const IterArgs& a, int num_sms, int S_max, int schedule) {
     return c;
   }
   c.stages = fits_threads ? 1 : 0;
-  if (schedule == SCHED_HYBRID) {
+  if (schedule == SCHED_HYBRID || schedule == SCHED_FUSED) {
     const LaunchCfg ch = config_t<VT, MT>(a, num_sms, S_max, SCHED_CHAIN);
     c.grid_chain = ch.grid;
     c.stages_chain = ch.stages;
@@ -2419,8 +2419,12 @@ LaunchCfg config_t(const IterArgs& a, int num_sms, int S_max, int schedule) {
       tc_smem_bytes(a.n_v, kTcMaxN) + 256 <= (size_t)optin) {
     // the widest GEMM (16, 32 or 64 nodes) that still gives every SM a batch
     c.tc = true;
-    c.tn = 16;
-    while (c.tn < kTcMaxN && a.n >= 2 * c.tn * num_sms) c.tn *= 2;
+    if (tc_width == 16 || tc_width == 32 || tc_width == 64) {
+      c.tn = tc_width;  // chosen by timing when the factor was built
+    } else {
+      c.tn = 16;  // the widest GEMM that still gives every SM two batches
+      while (c.tn < kTcMaxN && a.n >= 2 * c.tn * num_sms) c.tn *= 2;
+    }
     c.smem_tc = tc_smem_bytes(a.n_v, c.tn);
     const int batches = (a.n + c.tn - 1) / c.tn;
     c.grid_tc = batches < num_sms ? batches : num_sms;
@@ -2493,7 +2497,13 @@ int launch_t(const IterArgs& a, const LaunchCfg& c, int nu, int mode, cudaStream
   }
   launch_dep(prox_node<VT, MT>, c.grid_prox, c.block, c.smem_pstage, s, dep, a, nu, mode);
   mark();
-  if ((mode & MODE_BWD) && c.schedule == SCHED_HYBRID) {
+  if ((mode & MODE_BWD) && c.schedule == SCHED_FUSED) {
+    // the whole backward sweep (s, [Bbar; L]'[s; psi], r, Lambda r / (2 p) and [Bbar; L] delta)
+    // along the chains and up the top nodes: every pack is read once per iteration
+    launch_dep(apg_iter<VT, MT>, c.grid_chain, c.block, c.smem_chain, s, dep, a, c.stages_chain, nu,
+               (mode & ~MODE_PROX) | MODE_WREADY);
+    mark();
+  } else if ((mode & MODE_BWD) && c.schedule == SCHED_HYBRID) {
     // s, [Bbar; L]'[s; psi] and r along the chains and up the top nodes, r of every node out
     launch_dep(apg_iter<VT, MT>, c.grid_chain, c.block, c.smem_chain, s, dep, a, c.stages_chain, nu,
                                                                  (mode & ~MODE_PROX) | MODE_GT | MODE_WREADY);
@@ -2556,11 +2566,11 @@ long long pack_entries(int prec, int n_k, int n_v) {
   }
 }
 
-LaunchCfg iter_config(int prec, const IterArgs& a, int num_sms, int schedule) {
+LaunchCfg iter_config(int prec, const IterArgs& a, int num_sms, int schedule, int tc_width) {
   switch (prec) {
     case SMPC_FP64: return config_t<double, double>(a, num_sms, 1, schedule);
     case SMPC_FP32: return config_t<float, float>(a, num_sms, 2, schedule);
-    default: return config_t<float, __nv_bfloat16>(a, num_sms, 4, schedule);
+    default: return config_t<float, __nv_bfloat16>(a, num_sms, 4, schedule, tc_width);
   }
 }
 

@@ -154,11 +154,12 @@ enum KernelMode : int {
 };
 
 enum Schedule : int {
-  SCHED_CHAIN = 1,  // one apg_iter launch per iteration, one CTA per chain
-  SCHED_NODE = 2,   // six launches per iteration, one task per node in each
-  SCHED_HYBRID = 3  // node-parallel forward sweep and prox, a chain pass up to r, node-parallel Lambda / [Bbar; L]
+  SCHED_CHAIN = 1,   // one apg_iter launch per iteration, one CTA per chain
+  SCHED_NODE = 2,    // six launches per iteration, one task per node in each
+  SCHED_HYBRID = 3,  // node-parallel forward sweep and prox, a chain pass up to r, node-parallel Lambda / [Bbar; L]
+  SCHED_FUSED = 4    // node-parallel forward sweep and prox, then the whole backward sweep as one chain pass
 };
-constexpr int kSchedules = 3;
+constexpr int kSchedules = 4;
 
 struct LaunchCfg {
   int schedule = SCHED_CHAIN;
@@ -187,11 +188,14 @@ struct LaunchCfg {
 // kernels one launch_iter call enqueues
 inline int kernels_per_call(const LaunchCfg& c, int mode) {
   if (c.schedule == SCHED_CHAIN) return 1;
-  return 1 + ((mode & MODE_PROX) ? 1 : 0) + ((mode & MODE_BWD) ? (c.schedule == SCHED_HYBRID ? 2 : 4) : 0);
+  const int bwd = c.schedule == SCHED_HYBRID ? 2 : c.schedule == SCHED_FUSED ? 1 : 4;
+  return 1 + ((mode & MODE_PROX) ? 1 : 0) + ((mode & MODE_BWD) ? bwd : 0);
 }
 
 // Kernel launchers (kernels.cu).  prec: smpc_precision.
-LaunchCfg iter_config(int prec, const IterArgs& a, int num_sms, int schedule = SCHED_CHAIN);
+// tc_width: nodes per tensor-core GEMM of a bfloat16 shared-pack factor (16, 32, 64; 0: by
+// the tree size)
+LaunchCfg iter_config(int prec, const IterArgs& a, int num_sms, int schedule = SCHED_CHAIN, int tc_width = 0);
 int launch_iter(int prec, const IterArgs& a, const LaunchCfg& cfg, int nu, int mode, void* stream);
 int launch_pack(int prec, int n, int n_k, int n_v, const double* K, const double* Lam, const double* prob,
                 void* packs, long long pack_stride, void* stream);
@@ -313,7 +317,9 @@ struct smpc_factor_t {
   int last_launches = 0;
   int num_sms = 0;
   int schedule = smpc::SCHED_CHAIN;  // iteration schedule in use
-  float tuned_ms[4] = {0, 0, 0, 0};  // per schedule: ms per iteration measured when the factor chose
+  float tuned_ms[5] = {0, 0, 0, 0, 0};  // per schedule: ms per iteration measured when the factor chose
+  int tc_width = 0;                   // bfloat16 shared packs: nodes per tensor-core GEMM (0: none)
+  float tc_ms[3] = {0, 0, 0};         // ms per delta iteration measured for widths 16, 32, 64
   smpc::Profile* profile = nullptr;  // set while smpc_profile_solve runs
   bool solved_once = false;
   unsigned long long wait_ns = 2000000000ull;  // IterArgs::wait_ns (SMPC_PIPELINE_WAIT_NS)

@@ -92,7 +92,7 @@ class Gpu:
     """One instance on the GPU through the C ABI."""
 
     def __init__(self, P, steps=None, precision=0, precondition=1, lam=0.0, power_iters=0, lambda_margin=0.0,
-                 schedule=0, shared_packs=0):
+                 schedule=0, shared_packs=0, tc_width=0):
         import torch
 
         import paper_1604_01074_gb300 as smpc
@@ -104,7 +104,7 @@ class Gpu:
         self.tree = smpc.smpc_tree_create(t["parent"], t["prob"])
         self.fac = smpc.smpc_factor(self.tree, net, cost, precision=precision, precondition=precondition, lam=lam,
                                     power_iters=power_iters, lambda_margin=lambda_margin, steps=steps,
-                                    schedule=schedule, shared_packs=shared_packs)
+                                    schedule=schedule, shared_packs=shared_packs, tc_width=tc_width)
         dt = torch.float64 if precision == 0 else torch.float32
         dev = torch.device("cuda", 0)
         self.u = torch.zeros((self.n, self.n_u), dtype=dt, device=dev)

@@ -30,7 +30,7 @@ def _forest_case(seed, count):
     return members, F, steps, per
 
 
-@pytest.mark.parametrize("schedule", [1, 2, 3])
+@pytest.mark.parametrize("schedule", [1, 2, 3, 4])
 @pytest.mark.parametrize("shared", [0, 1])
 def test_forest_matches_each_tree_alone(schedule, shared):
     members, F, steps, per = _forest_case(0, 5)
@@ -57,8 +57,9 @@ def test_forest_matches_each_tree_alone(schedule, shared):
 @pytest.mark.parametrize("precision", [1, 2])
 def test_forest_reduced_precision(precision):
     """Every member tree of a float32 / bfloat16 forest against the FP64 oracle run on that
-    tree alone: the elementwise bounds of the full-size reduced-precision tests
-    (1e-4 and 2e-3 relative to 1 + the largest entry) and |rho_rel| of each tree within 1e-4."""
+    tree alone, with the bars of the full-size reduced-precision tests at equal iteration
+    counts: float32 1e-4 elementwise (relative to 1 + the largest entry) and |rho_rel| of
+    each tree within 1e-4; bfloat16 (anchored) 0.15 and 0.05."""
     members, F, steps, per = _forest_case(4, 4)
     iters = 300
     g = H.Gpu(F, steps=steps, precision=precision, shared_packs=1)
@@ -68,17 +69,17 @@ def test_forest_reduced_precision(precision):
         its, rr = g.smpc.smpc_solve_trees(g.fac, len(members))
     finally:
         g.close()
-    bound = {1: 1e-4, 2: 2e-3}[precision]
+    bound, rho_bound = {1: (1e-4, 1e-4), 2: (0.15, 0.05)}[precision]
     for r, P in enumerate(members):
         R = H.oracle_run(P, per[r], iters)
         idx = F["members"][r]
         e = (H.relerr(u[idx], R.u), H.relerr(x[idx], R.x), H.relerr(y[idx], H.stack_y(R.y)))
         assert max(e) <= bound, (r, e)
         assert its[r] == iters
-        assert abs(rr[r] - R.rho_rel[-1]) <= 1e-4, (r, rr[r], R.rho_rel[-1])
+        assert abs(rr[r] - R.rho_rel[-1]) <= rho_bound, (r, rr[r], R.rho_rel[-1])
 
 
-@pytest.mark.parametrize("schedule", [1, 2, 3])
+@pytest.mark.parametrize("schedule", [1, 2, 3, 4])
 @pytest.mark.parametrize("shared", [0, 1])
 def test_forest_stops_each_tree_on_its_own(schedule, shared):
     """With a tolerance, every tree of a forest stops at its own first iterate whose relative
