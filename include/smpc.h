@@ -62,6 +62,7 @@ typedef struct smpc_tree smpc_tree;
 typedef struct smpc_factor_t smpc_factor_t;
 typedef struct smpc_server smpc_server;
 typedef struct smpc_batch smpc_batch;
+typedef struct smpc_shard smpc_shard;
 
 /* Flow-based network model x+ = A x + B u + G_d d, 0 = E u + E_d d (Sec. II-A,
  * eqs. model and demand-control).  A may be NULL for the identity (tank mass
@@ -278,6 +279,44 @@ int smpc_batch_create(int32_t count, smpc_factor_t* const* factors, smpc_batch**
 int smpc_batch_solve(smpc_batch* batch, const smpc_step_data* data, const smpc_solve_opts* opts, smpc_result* res,
                      void* stream);
 void smpc_batch_destroy(smpc_batch* batch);
+
+/* Shards: one scenario tree split over several GPUs, one process per GPU (Sec. IV-B: the
+ * nodes of a stage are independent given their children's sums).  Every GPU creates the
+ * tree and factor of the whole problem, then a shard that owns the chains (maximal leaf
+ * paths, numbered as smpc_tree_info's n_chains) [chain_begin, chain_end); the top nodes
+ * above the chains are replicated on every GPU.  A sharded solve is driven by the caller,
+ * who owns the exchange between the GPUs:
+ *   smpc_shard_begin(shard, data, opts, residuals, stream)   - smpc_solve's set-up;
+ *   for nu = 0, 1, ...:
+ *     smpc_shard_step(shard, nu, 0, exchange)   - forward sweep and prox of the shard's nodes
+ *         (iteration nu - 1), backward sweep along its chains (iteration nu), and into
+ *         exchange (device, n_cut x (n_x + n_v) of the vector type) the sums of s and r
+ *         over its chain heads below each cut parent (a top node with chain children);
+ *     caller: exchange = its sum over the GPUs (allreduce, sum);
+ *     smpc_shard_step(shard, nu, 1, exchange)   - the backward sweep of the top nodes with
+ *         the totals, the same on every GPU;
+ *     caller (nu >= 1): residuals[3 (nu - 1) .. 3 (nu - 1) + 2] = its maximum over the GPUs
+ *         (allreduce, max; float64 bit patterns, so an integer maximum is the same);
+ *     every so often smpc_shard_flags: once done >= 0 the solve has stopped on every GPU;
+ *   smpc_shard_step(shard, n, 2, NULL) with n = the loop count - the last prox; the caller's
+ *       residual maximum for iteration n - 1; then smpc_shard_finish(shard, n, res).
+ * residuals: device, 3 (max_iters + 2) unsigned 64-bit, owned by the caller.  Each GPU's
+ * outputs hold its own chains' and the top nodes' entries (others are not updated).  Stops
+ * are the same on every GPU since every GPU reads the same residuals.  float64 and float32
+ * factors of a single tree whose root is a top node; all calls on the stream of begin.
+ * Errors: SMPC_EINVAL, SMPC_ENOTSUP (bfloat16, a chain starting at a root), SMPC_ENOMEM,
+ * SMPC_ECUDA, and the solve's own errors from smpc_shard_finish. */
+int smpc_shard_create(smpc_factor_t* fac, int32_t chain_begin, int32_t chain_end, smpc_shard** out);
+int smpc_shard_info(const smpc_shard* shard, int32_t* n_cut, int32_t* width, int32_t* n_nodes);
+/* The n_nodes (smpc_shard_info) nodes whose rows this shard's outputs hold, ascending:
+ * the top nodes and the nodes of its own chains. */
+int smpc_shard_nodes(const smpc_shard* shard, int32_t* nodes);
+int smpc_shard_begin(smpc_shard* shard, const smpc_step_data* data, const smpc_solve_opts* opts,
+                     unsigned long long* residuals, void* stream);
+int smpc_shard_step(smpc_shard* shard, int32_t nu, int32_t phase, void* exchange);
+int smpc_shard_flags(const smpc_shard* shard, int32_t* done, int32_t* error);
+int smpc_shard_finish(smpc_shard* shard, int32_t launched, smpc_result* res);
+void smpc_shard_destroy(smpc_shard* shard);
 
 /* Diagnostics; the paper has no counterpart.  Runs one cold-start solve of `iters`
  * iterations (tol 0, legacy default stream) with a CUDA event between consecutive kernels

@@ -94,6 +94,16 @@ SIGNATURES = {
     "smpc_batch_solve": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(smpc_step_data),
                                         ctypes.POINTER(smpc_solve_opts), ctypes.POINTER(smpc_result), ctypes.c_void_p]),
     "smpc_batch_destroy": (None, [ctypes.c_void_p]),
+    "smpc_shard_create": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32,
+                                         ctypes.POINTER(ctypes.c_void_p)]),
+    "smpc_shard_info": (ctypes.c_int, [ctypes.c_void_p, _ip, _ip, _ip]),
+    "smpc_shard_nodes": (ctypes.c_int, [ctypes.c_void_p, _ip]),
+    "smpc_shard_begin": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(smpc_step_data),
+                                        ctypes.POINTER(smpc_solve_opts), ctypes.c_void_p, ctypes.c_void_p]),
+    "smpc_shard_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p]),
+    "smpc_shard_flags": (ctypes.c_int, [ctypes.c_void_p, _ip, _ip]),
+    "smpc_shard_finish": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.POINTER(smpc_result)]),
+    "smpc_shard_destroy": (None, [ctypes.c_void_p]),
     "smpc_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "smpc_last_error": (ctypes.c_char_p, []),
     "smpc_version": (ctypes.c_int, []),
@@ -384,6 +394,60 @@ def smpc_batch_solve(batch, steps, max_iters=500, tol=0.0, warm_start=0, check_e
     s = None if stream is None else (stream if isinstance(stream, int) else stream.cuda_stream)
     _check(lib().smpc_batch_solve(batch, D, ctypes.byref(O), R, s), "smpc_batch_solve")
     return [{"iterations": r.iterations, "rho": r.rho, "rho_rel": r.rho_rel, "launches": r.launches} for r in R]
+
+
+def smpc_shard_create(fac, chain_begin, chain_end):
+    h = ctypes.c_void_p()
+    _check(lib().smpc_shard_create(fac, int(chain_begin), int(chain_end), ctypes.byref(h)), "smpc_shard_create")
+    return h
+
+
+def smpc_shard_info(shard):
+    """(n_cut, width, n_nodes): cut parents, entries per cut parent in the exchange, nodes updated."""
+    a, b, c = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+    _check(lib().smpc_shard_info(shard, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)), "smpc_shard_info")
+    return a.value, b.value, c.value
+
+
+def smpc_shard_nodes(shard):
+    n = smpc_shard_info(shard)[2]
+    out = np.zeros(n, dtype=np.int32)
+    _check(lib().smpc_shard_nodes(shard, out.ctypes.data_as(_ip)), "smpc_shard_nodes")
+    return out
+
+
+def smpc_shard_begin(shard, p, q, dhat, alpha2, residuals, eps=None, max_iters=500, tol=0.0, warm_start=0,
+                     stream=None):
+    """residuals: an int device address of 3 (max_iters + 2) uint64 (the caller's buffer)."""
+    k = _Keep()
+    D = smpc_step_data(k(p), k(q), k(dhat), k(eps), k(alpha2))
+    O = smpc_solve_opts(int(max_iters), float(tol), int(warm_start), 0, 0, 0, 0, 0)
+    s = None if stream is None else (stream if isinstance(stream, int) else stream.cuda_stream)
+    _check(lib().smpc_shard_begin(shard, ctypes.byref(D), ctypes.byref(O), ctypes.c_void_p(residuals), s),
+           "smpc_shard_begin")
+
+
+def smpc_shard_step(shard, nu, phase, exchange=None):
+    _check(lib().smpc_shard_step(shard, int(nu), int(phase), None if exchange is None else ctypes.c_void_p(exchange)),
+           "smpc_shard_step")
+
+
+def smpc_shard_flags(shard):
+    d, e = ctypes.c_int32(), ctypes.c_int32()
+    _check(lib().smpc_shard_flags(shard, ctypes.byref(d), ctypes.byref(e)), "smpc_shard_flags")
+    return d.value, e.value
+
+
+def smpc_shard_finish(shard, launched, u=None, x=None, y=None):
+    def dptr(t):
+        return None if t is None else (t if isinstance(t, int) else t.data_ptr())
+    R = smpc_result(dptr(u), dptr(x), dptr(y), None, None, -1, 0.0, 0.0, 0)
+    _check(lib().smpc_shard_finish(shard, int(launched), ctypes.byref(R)), "smpc_shard_finish")
+    return {"iterations": R.iterations, "rho": R.rho, "rho_rel": R.rho_rel}
+
+
+def smpc_shard_destroy(shard):
+    lib().smpc_shard_destroy(shard)
 
 
 def smpc_solve_trees(fac, n_trees):

@@ -15,7 +15,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libsmpc.so")
-SOURCES = ["kernels.cu", "api.cpp", "factor_host.cpp", "noalloc.cu", "server.cpp", "diag.cu", "batch.cpp"]
+SOURCES = ["kernels.cu", "api.cpp", "factor_host.cpp", "noalloc.cu", "server.cpp", "diag.cu", "batch.cpp", "shard.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

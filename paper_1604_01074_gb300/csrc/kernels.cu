@@ -1398,6 +1398,7 @@ struct Kern {
       chain_backward(p, nodes, len);
       if (abort_) break;
       const int par = a.chain_parent[ch];
+      if (mode & MODE_NOCLIMB) continue;  // a shard: the heads' s and r go to the exchange
       if (par >= 0 && arrive(par)) process_top(p, par, chain_cursor(ch + gridDim.x));
     }
 
@@ -1632,7 +1633,7 @@ __global__ void __launch_bounds__(kThreads, 3) prox_node(const __grid_constant__
   if (early_exit(a, nu, mode, sm.flag + 1, decide)) return;
   Kern<VT, MT> k(a, sm, 0, nu, mode);
   const bool do_prox = (mode & MODE_PROX) != 0 && nu >= 1;
-  const bool do_bwd = (mode & MODE_BWD) != 0;
+  const bool do_bwd = (mode & (MODE_BWD | MODE_WONLY)) != 0;
   const int warp = threadIdx.x >> 5;
   if (do_prox && !k.linear()) {
     const int t = threadIdx.x;
@@ -1653,7 +1654,9 @@ __global__ void __launch_bounds__(kThreads, 3) prox_node(const __grid_constant__
       __syncthreads();
       k.ttab = ttab;
     }
-    for (int m = blockIdx.x * kWarps + warp; m < a.n; m += gridDim.x * kWarps) {
+    const int nn = a.node_list ? a.n_list : a.n;
+    for (int j = blockIdx.x * kWarps + warp; j < nn; j += gridDim.x * kWarps) {
+      const int m = a.node_list ? a.node_list[j] : j;
       const int r = a.res_tree ? a.tree_of[m] : -1;
       if (r >= 0 && !tree_active(a, r, nu)) continue;  // a forest's tree that stopped keeps its iterates
       k.warp_prox_staged(m, bnd, stage, r);
@@ -1664,8 +1667,9 @@ __global__ void __launch_bounds__(kThreads, 3) prox_node(const __grid_constant__
       tree_table_flush(a, ttab, nu);
     }
   } else {
-    for (int m = blockIdx.x * kWarps + warp; m < a.n; m += gridDim.x * kWarps)
-      k.warp_prox(m, do_prox, do_bwd && (!do_prox || k.linear()));
+    const int nn = a.node_list ? a.n_list : a.n;
+    for (int j = blockIdx.x * kWarps + warp; j < nn; j += gridDim.x * kWarps)
+      k.warp_prox(a.node_list ? a.node_list[j] : j, do_prox, do_bwd && (!do_prox || k.linear()));
   }
   k.reduce_out(do_prox);
 }
@@ -1838,6 +1842,48 @@ __global__ void __launch_bounds__(kThreads, 1) node_mv(const __grid_constant__ I
     a.flags[1] = SMPC_ETIMEOUT;
     const int end = shared ? min(count, 1) : min(count, failed_at + S);
     for (int q = failed_at; q < end; ++q) mbar_wait(&sm.barK[q % S], (q / S) & 1);
+  }
+}
+
+// ------------------------------------------------------------------ shards
+// Cut parent j (a top node with chain children): the sums over this GPU's chain heads
+// below it of s (n_x entries) and r (n_v entries); one CTA per cut parent.
+template <typename VT>
+__global__ void cut_sums_kernel(IterArgs a, int n_cut, const int* cut_off, const int* cut_heads, VT* out) {
+  const int W = a.n_x + a.n_v;
+  const VT* sp = reinterpret_cast<const VT*>(a.spub);
+  const VT* rp = reinterpret_cast<const VT*>(a.rpub);
+  for (int j = blockIdx.x; j < n_cut; j += gridDim.x) {
+    for (int e = threadIdx.x; e < W; e += blockDim.x) {
+      VT v = 0;
+      for (int q = cut_off[j]; q < cut_off[j + 1]; ++q) {  // heads in index order
+        const long long h = cut_heads[q];
+        v += e < a.n_x ? sp[h * a.n_x + e] : rp[h * a.n_v + (e - a.n_x)];
+      }
+      out[(long long)j * W + e] = v;
+    }
+  }
+}
+// The exchanged totals into the chain children of each cut parent: the first chain child
+// carries the total, the others zero, so that the top pass's sum over children is the
+// sum over every GPU's chains.
+template <typename VT>
+__global__ void cut_scatter_kernel(IterArgs a, int n_cut, const int* chl_off, const int* chl, const VT* in) {
+  const int W = a.n_x + a.n_v;
+  VT* sp = reinterpret_cast<VT*>(a.spub);
+  VT* rp = reinterpret_cast<VT*>(a.rpub);
+  for (int j = blockIdx.x; j < n_cut; j += gridDim.x) {
+    for (int q = chl_off[j]; q < chl_off[j + 1]; ++q) {
+      const long long c = chl[q];
+      const bool first = q == chl_off[j];
+      for (int e = threadIdx.x; e < W; e += blockDim.x) {
+        const VT v = first ? in[(long long)j * W + e] : (VT)0;
+        if (e < a.n_x)
+          sp[c * a.n_x + e] = v;
+        else
+          rp[c * a.n_v + (e - a.n_x)] = v;
+      }
+    }
   }
 }
 
@@ -2623,6 +2669,30 @@ int launch_copy_final_y(int prec, const IterArgs& a, int max_iters, void* dst, v
   else
     final_y_kernel<float><<<dst ? 256 : 1, 256, 0, s>>>(a, max_iters, (float*)dst);
   return check_launch("final_y");
+}
+
+int launch_cut_sums(int prec, const IterArgs& a, int n_cut, const int* cut_off, const int* cut_heads, void* out,
+                    void* stream) {
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (n_cut <= 0) return SMPC_OK;
+  const int grid = n_cut < 1024 ? n_cut : 1024;
+  if (prec == SMPC_FP64)
+    cut_sums_kernel<double><<<grid, 256, 0, s>>>(a, n_cut, cut_off, cut_heads, (double*)out);
+  else
+    cut_sums_kernel<float><<<grid, 256, 0, s>>>(a, n_cut, cut_off, cut_heads, (float*)out);
+  return check_launch("cut_sums");
+}
+
+int launch_cut_scatter(int prec, const IterArgs& a, int n_cut, const int* chl_off, const int* chl, const void* in,
+                       void* stream) {
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (n_cut <= 0) return SMPC_OK;
+  const int grid = n_cut < 1024 ? n_cut : 1024;
+  if (prec == SMPC_FP64)
+    cut_scatter_kernel<double><<<grid, 256, 0, s>>>(a, n_cut, chl_off, chl, (const double*)in);
+  else
+    cut_scatter_kernel<float><<<grid, 256, 0, s>>>(a, n_cut, chl_off, chl, (const float*)in);
+  return check_launch("cut_scatter");
 }
 
 int launch_init_duals(int prec, const IterArgs& a, int warm, void* stream) {

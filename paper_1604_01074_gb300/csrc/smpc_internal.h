@@ -140,6 +140,10 @@ struct IterArgs {
   int R;
   unsigned long long* res_tree;
   int* tree_done;
+  // Shards of a tree split over several GPUs: the nodes this GPU updates in the prox
+  // (its chains and the replicated top nodes), or NULL for all n nodes.
+  const int* node_list;
+  int n_list;
 };
 
 enum KernelMode : int {
@@ -150,7 +154,10 @@ enum KernelMode : int {
   MODE_ANCHOR = 16,   // anchored solve: evaluate the whole solve step at w_a = w^nu into ha
   MODE_DELTA = 32,    // anchored solve: solve step on w^nu - w_a, without the affine data
   MODE_GT = 64,       // backward sweep up to r only: s, g = [Bbar; L]'[s; psi], r for every node
-  MODE_WREADY = 128   // w^nu was written by an earlier launch of the iteration
+  MODE_WREADY = 128,  // w^nu was written by an earlier launch of the iteration
+  MODE_NOCLIMB = 256,  // chain pass of a shard: chains publish their heads' s and r, no top-node climb
+  MODE_WONLY = 512     // prox launch writes w^nu of an iteration without a prox (as with MODE_BWD) while
+                       // the backward sweep is launched separately
 };
 
 enum Schedule : int {
@@ -228,6 +235,14 @@ int launch_cost_update(int prec, const CostArgs& a, void* stream);
 int launch_copy_final_y(int prec, const IterArgs& a, int max_iters, void* dst, void* stream);
 long long pack_entries(int prec, int n_k, int n_v);
 int launch_init_duals(int prec, const IterArgs& a, int warm, void* stream);
+// Shards: out[j] = the sums over this GPU's chain heads below cut parent j of their s
+// (n_x) and r (n_v), heads listed in CSR form (cut_off, cut_heads); and the scatter of the
+// exchanged totals: for cut parent j, the first chain child in (chl_off, chl) takes the
+// total, the other chain children zero, in spub / rpub.
+int launch_cut_sums(int prec, const IterArgs& a, int n_cut, const int* cut_off, const int* cut_heads, void* out,
+                    void* stream);
+int launch_cut_scatter(int prec, const IterArgs& a, int n_cut, const int* chl_off, const int* chl, const void* in,
+                       void* stream);
 int launch_convert(int prec, const double* src, void* dst, long long count, void* stream);
 size_t vec_size(int prec);
 
