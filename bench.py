@@ -724,7 +724,7 @@ def _serve_window(smpc, server, sess, rate, seconds, drain, args, rng):
             req = _session_request(s_["P"], s_["k"], s_["x"], s_["q"])
             tk = smpc.smpc_submit(server, s_["fac"], req["p"], req["q"], req["dhat"], req["alpha2"], eps=s_["P"]["eps"],
                                   max_iters=args.serve_max_iters, tol=args.tol, warm_start=int(s_["k"] > 0),
-                                  check_every=64, use_graph=1)
+                                  check_every=64)
             s_["pending"].append((tk, time.perf_counter(), s_["k"]))
             s_["k"] += 1
             offered += 1
@@ -770,6 +770,7 @@ def run_serve(args):
         sess.append({"P": P, "tree": tree, "fac": fac, "prec": prec, "x": P["p"].copy(), "q": P["q"].copy(),
                      "k": 0, "pending": [], "rng": np.random.default_rng(100 + i)})
     total_bytes = sum(smpc.smpc_factor_device_bytes(s_["fac"]) for s_ in sess)
+    log("serve: factors ready,", total_bytes / 1e9, "GB")
     budget = int(args.serve_budget_gb * 1e9)
     server = smpc.smpc_server_create(budget, args.serve_slots)
     rng = np.random.default_rng(0)
@@ -777,10 +778,11 @@ def run_serve(args):
     for s_ in sess:
         req = _session_request(s_["P"], 0, s_["x"], s_["q"])
         tk = smpc.smpc_submit(server, s_["fac"], req["p"], req["q"], req["dhat"], req["alpha2"], eps=s_["P"]["eps"],
-                              max_iters=args.serve_max_iters, tol=args.tol, check_every=64, use_graph=1)
+                              max_iters=args.serve_max_iters, tol=args.tol, check_every=64)
         s_["pending"].append((tk, time.perf_counter(), 0))
         s_["k"] = 1
     t_cold = time.perf_counter()
+    n_cold = 0
     while any(s_["pending"] for s_ in sess):
         for s_ in sess:
             if s_["pending"]:
@@ -791,6 +793,9 @@ def run_serve(args):
                     s_["pending"].pop(0)
                     s_["x"] = _plant_step(s_["P"], s_["x"], u0, k, s_["rng"])
                     s_["q"] = u0
+                    n_cold += 1
+                    if n_cold % 16 == 0:
+                        log("serve: cold steps", n_cold, "of", len(sess), "after", time.perf_counter() - t_cold, "s")
         time.sleep(0.001)
     log("serve: cold steps done in", time.perf_counter() - t_cold, "s")
     windows = []
@@ -811,7 +816,7 @@ def run_serve(args):
         "config": {"workload": SERVE_WORKLOAD, "slots": args.serve_slots, "hbm_budget_bytes": budget,
                    "factor_bytes_total": total_bytes, "precision": "fp32 and bf16 shared packs, alternating by session",
                    "max_iters": args.serve_max_iters, "tol": args.tol, "warm_start": "each session's previous step",
-                   "launch": "64-iteration chunks as CUDA graphs per factor", "rates": args.serve_rates,
+                   "launch": "plain launches, 64-iteration chunks between stop checks", "rates": args.serve_rates,
                    "window_s": args.serve_seconds}}
     # baseline: the plain per-request FP64 solve (one pack per node), one at a time, on a
     # sample of sessions continuing their closed loops (warm-started steps, same tol)

@@ -1523,6 +1523,363 @@ __global__ void __launch_bounds__(kThreads, 1)
   }
 }
 
+// ------------------------------------------------------------------ fused backward pass (schedule 4)
+// The whole backward sweep of Algorithm 1 in one launch with every pack read once: one CTA
+// of kBT threads per chain (and the top nodes by last arrival, as in apg_iter), each chain
+// node's pack [Bbar; L | Lambda / (2 p_n)] streamed through S shared-memory slots with
+// cp.async.bulk while the previous nodes are processed.  Per node, three mat-vecs from
+// shared memory: g = [Bbar; L]' [s; psi], r = r_below + beta + g, delta = Lambda r, and
+// h = [Bbar; L] delta.  512 threads per CTA (one CTA per SM) halve each mat-vec's serial
+// work against apg_iter's 256, which keeps the node time below the pack's HBM time.
+constexpr int kBT = 512;
+
+template <typename MT>
+__host__ __device__ inline int bwd_slices(int n_v) {
+  const int G = row_stride<MT>(n_v) / (16 / (int)sizeof(MT));
+  const int P = kBT / G;
+  return P > 20 ? 20 : P;
+}
+
+template <typename MT>
+__host__ __device__ inline size_t bwd_smem_bytes(int S, int n_x, int n_u, int n_v) {
+  using AT = typename Acc<MT>::T;
+  const int n_k = n_x + n_u, ld = row_stride<MT>(n_v);
+  size_t m = (size_t)S * (kpad<MT>(n_k, n_v) + lpad<MT>(n_v)) * sizeof(MT);
+  m = round_up(m, 16) + 4 * sizeof(uint64_t);
+  m = round_up(m, 16);
+  m += ((size_t)3 * ld + round_up(n_k, 4) + (size_t)bwd_slices<MT>(n_v) * ld) * sizeof(AT);
+  m = round_up(m, 16) + 16 * sizeof(int);
+  return round_up(m, 128);
+}
+
+template <typename VT, typename MT>
+struct Bwd {
+  using AT = typename Acc<MT>::T;
+  const IterArgs& a;
+  int S, nu, mode, ld;
+  unsigned char* base;
+  size_t kbytes, lbytes;
+  uint64_t* bar;  // one per slot: the node's [Bbar; L] and Lambda copies
+  AT *dv, *rv, *gv, *yv, *part;
+  int* flag;
+  uint32_t iss = 0, use = 0;  // loads issued / consumed (the same in every thread)
+  Cursor cur;                 // next chain node to load
+  int cnode = -1;             // thread 0: its node id
+  bool abort_ = false;
+
+  __device__ Bwd(const IterArgs& args, unsigned char* smem, int S_, int nu_, int mode_)
+      : a(args), S(S_), nu(nu_), mode(mode_), base(smem) {
+    ld = row_stride<MT>(a.n_v);
+    kbytes = kpad<MT>(a.n_k, a.n_v) * sizeof(MT);
+    lbytes = lpad<MT>(a.n_v) * sizeof(MT);
+    size_t off = round_up((size_t)S * (kbytes + lbytes), 16);
+    bar = reinterpret_cast<uint64_t*>(base + off);
+    off = round_up(off + 4 * sizeof(uint64_t), 16);
+    AT* v = reinterpret_cast<AT*>(base + off);
+    dv = v;
+    v += ld;
+    rv = v;
+    v += ld;
+    gv = v;
+    v += ld;
+    yv = v;
+    v += round_up(a.n_k, 4);
+    part = v;
+    v += bwd_slices<MT>(a.n_v) * ld;
+    off = round_up(reinterpret_cast<unsigned char*>(v) - base, 16);
+    flag = reinterpret_cast<int*>(base + off);
+  }
+  __device__ MT* K(int s) const { return reinterpret_cast<MT*>(base + (size_t)s * (kbytes + lbytes)); }
+  __device__ MT* Lm(int s) const { return reinterpret_cast<MT*>(base + (size_t)s * (kbytes + lbytes) + kbytes); }
+  __device__ const MT* pack(int n) const {
+    return reinterpret_cast<const MT*>(a.packs) + (long long)n * a.pack_stride;
+  }
+  __device__ const VT* cv(const void* p) const { return reinterpret_cast<const VT*>(p); }
+  __device__ VT* mv(void* p) const { return reinterpret_cast<VT*>(p); }
+  __device__ bool no_affine() const { return (mode & (MODE_LINEAR | MODE_DELTA)) != 0; }
+
+  // ---------------------------------------------------------- pipeline
+  __device__ Cursor chain_cursor(int chain) const {
+    Cursor c;
+    c.chain = chain < a.n_chains ? chain : -1;
+    c.k = c.chain >= 0 ? a.chain_off[c.chain + 1] - a.chain_off[c.chain] - 1 : 0;
+    return c;
+  }
+  __device__ void advance(Cursor& c) const {
+    if (c.chain < 0) return;
+    if (--c.k < 0) c = chain_cursor(c.chain + gridDim.x);
+  }
+  __device__ int node_of(const Cursor& c) const { return a.chain_node[a.chain_off[c.chain] + c.k]; }
+  __device__ void copy_node(uint32_t seq, int n) {  // thread 0
+    const int slot = seq % S;
+    fence_proxy_async();
+    mbar_expect_tx(&bar[slot], (uint32_t)(kbytes + lbytes));
+    const unsigned char* src = reinterpret_cast<const unsigned char*>(pack(n));
+    bulk_g2s(K(slot), src, (uint32_t)kbytes, &bar[slot]);
+    bulk_g2s(Lm(slot), src + kpad<MT>(a.n_k, a.n_v) * sizeof(MT), (uint32_t)lbytes, &bar[slot]);
+  }
+  __device__ void set_cursor(Cursor c) {
+    cur = c;
+    if (threadIdx.x == 0) cnode = c.chain >= 0 ? node_of(c) : -1;
+  }
+  __device__ void issue() {
+    if (cur.chain < 0) return;
+    if (threadIdx.x == 0) copy_node(iss, cnode);
+    ++iss;
+    advance(cur);
+    if (threadIdx.x == 0 && cur.chain >= 0) cnode = node_of(cur);
+  }
+  __device__ void prime() {
+    for (int q = 0; q < S; ++q) issue();
+  }
+  __device__ void fail() {
+    if (threadIdx.x == 0) a.flags[1] = SMPC_ETIMEOUT;
+    abort_ = true;
+  }
+  // the next load's slot; on timeout the load stays counted as in flight for drain()
+  __device__ int wait() {
+    const int slot = use % S;
+    const bool ok = mbar_wait(&bar[slot], (use / S) & 1);
+    if (__syncthreads_or(!ok)) {
+      fail();
+      return slot;
+    }
+    ++use;
+    return slot;
+  }
+  __device__ void drain() {
+    for (; use < iss; ++use) mbar_wait(&bar[use % S], (use / S) & 1);
+    __syncthreads();
+  }
+  // let every issued load land (bounded) and restart issuing at `next`
+  __device__ void flush(Cursor next) {
+    bool ok = true;
+    for (; use < iss; ++use) ok &= mbar_wait(&bar[use % S], (use / S) & 1);
+    set_cursor(next);
+    if (__syncthreads_or(!ok)) fail();
+  }
+
+  // ---------------------------------------------------------- mat-vecs from shared memory
+  // out[j] = sum_i A[i ld + j] x[i], j < C (A' x): thread (g, p) accumulates columns
+  // g V .. g V + V - 1 over the p-th row slice; slices are added in a fixed order.
+  __device__ void mtv_t(const MT* A, int R, int C, const AT* x, AT* out) {
+    constexpr int V = Vec<MT>::V;
+    const int t = threadIdx.x;
+    const int G = ld / V;
+    const int P = bwd_slices<MT>(a.n_v);
+    const int rc = (R + P - 1) / P;
+    if (t < P * G) {
+      const int g = t % G, p = t / G;
+      const int i0 = p * rc, i1 = min(R, i0 + rc);
+      AT acc[V];
+#pragma unroll
+      for (int k = 0; k < V; ++k) acc[k] = 0;
+      const MT* col = A + g * V;
+#pragma unroll 4
+      for (int i = i0; i < i1; ++i) {
+        AT av[V];
+        ld16(col + (long long)i * ld, av);
+        const AT xi = x[i];
+#pragma unroll
+        for (int k = 0; k < V; ++k) acc[k] += av[k] * xi;
+      }
+      AT* dst = part + p * ld + g * V;
+#pragma unroll
+      for (int k = 0; k < V; ++k) dst[k] = acc[k];
+    }
+    __syncthreads();
+    for (int j = t; j < C; j += kBT) {
+      AT v[20];
+#pragma unroll
+      for (int p = 0; p < 20; ++p) v[p] = p < P ? part[p * ld + j] : (AT)0;
+      AT s0 = 0, s1 = 0;
+#pragma unroll
+      for (int p = 0; p < 20; p += 2) {  // fixed order: deterministic
+        s0 += v[p];
+        s1 += v[p + 1];
+      }
+      out[j] = s0 + s1;
+    }
+    __syncthreads();
+  }
+  // h of node m = A dv (R = n_k rows): two threads per row, each half of the columns,
+  // combined by a shuffle; written to global memory (anchor launches: to h_a, h = 0).
+  __device__ void mtv_n_out(const MT* A, int m) {
+    constexpr int V = Vec<MT>::V;
+    const int G = ld / V, Gh = (G + 1) / 2;
+    const int t = threadIdx.x, i = t >> 1, half = t & 1;
+    AT acc0 = 0, acc1 = 0;
+    if (i < a.n_k) {
+      const MT* row = A + (long long)i * ld;
+      const int g1 = min(G, (half + 1) * Gh);
+#pragma unroll 4
+      for (int g = half * Gh; g < g1; ++g) {
+        AT av[V], xv[V];
+        ld16(row + g * V, av);
+        ldx(dv + g * V, xv);
+#pragma unroll
+        for (int k = 0; k < V; k += 2) {
+          acc0 += av[k] * xv[k];
+          acc1 += av[k + 1] * xv[k + 1];
+        }
+      }
+    }
+    AT v = acc0 + acc1;
+    v += __shfl_xor_sync(0xffffffffu, v, 1);
+    if (i < a.n_k && half == 0) {
+      const long long q = (long long)m * a.n_k + i;
+      if (mode & MODE_ANCHOR) {  // h_a = h(w_a); the part on w - w_a starts at zero
+        mv(a.ha)[q] = (VT)v;
+        mv(a.h)[q] = (VT)0;
+      } else {
+        mv(a.h)[q] = (VT)v;
+      }
+    }
+    __syncthreads();
+  }
+
+  // ---------------------------------------------------------- one node's backward step
+  // yv holds [s; psi]; thread j < n_v holds r_j (children and beta) in rreg.
+  __device__ void node(int m, AT& rreg, bool refill) {
+    const int t = threadIdx.x;
+    const int slot = wait();
+    if (abort_) return;
+    mtv_t(K(slot), a.n_k, a.n_v, yv, gv);
+    if (t < a.n_v) {
+      rreg += gv[t];
+      rv[t] = rreg;
+    }
+    __syncthreads();
+    mtv_t(Lm(slot), a.n_v, a.n_v, rv, dv);  // Lambda is symmetric
+    if (a.pscale) {  // shared pack: delta = (Lambda r) / (2 p_n)
+      if (t < a.n_v) dv[t] *= (AT)cv(a.pscale)[m];
+      __syncthreads();
+    }
+    mtv_n_out(K(slot), m);
+    if (refill) issue();
+  }
+
+  __device__ void chain(const int* nodes, int len) {
+    const int e = threadIdx.x;
+    AT sreg = 0, rreg = 0;
+    const bool lin = no_affine();
+    const VT* wb = cv(a.wbuf);
+    int m = nodes[len - 1];
+    AT wcur = e < a.n_k ? (AT)wb[(long long)m * a.n_k + e] : (AT)0;
+    AT bcur = (e < a.n_v && !lin) ? (AT)cv(a.beta)[(long long)m * a.n_v + e] : (AT)0;
+    for (int k = len - 1; k >= 0; --k) {
+      m = nodes[k];
+      AT wnext = 0, bnext = 0;
+      if (k > 0) {  // the next node's vectors into registers while this node runs
+        const int mn = nodes[k - 1];
+        if (e < a.n_k) wnext = (AT)wb[(long long)mn * a.n_k + e];
+        if (e < a.n_v && !lin) bnext = (AT)cv(a.beta)[(long long)mn * a.n_v + e];
+      }
+      if (e < a.n_x) {
+        sreg += wcur;
+        yv[e] = sreg;
+      } else if (e < a.n_k) {
+        yv[e] = wcur;
+      }
+      rreg += bcur;
+      node(m, rreg, true);
+      if (abort_) return;
+      wcur = wnext;
+      bcur = bnext;
+    }
+    const int head = nodes[0];
+    if (e < a.n_x) mv(a.spub)[(long long)head * a.n_x + e] = (VT)sreg;
+    if (e < a.n_v) mv(a.rpub)[(long long)head * a.n_v + e] = (VT)rreg;
+  }
+
+  // arrival at top node t (its children and its own ready w count); true for the last one
+  __device__ bool arrive(int t) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      fence_acq_rel_gpu();
+      const int old = atomicAdd(&a.counters[t], 1);
+      const int last = (old == a.top_expect[t] - 1);
+      if (last) {
+        a.counters[t] = 0;
+        fence_acq_rel_gpu();
+      }
+      flag[0] = last;
+    }
+    __syncthreads();
+    return flag[0] != 0;
+  }
+
+  // top node t (this CTA arrived last), then up while it stays last
+  __device__ void process_top(int t, Cursor next) {
+    flush(next);
+    if (abort_) return;
+    const int e = threadIdx.x;
+    const bool lin = no_affine();
+    while (t >= 0) {
+      if (threadIdx.x == 0) copy_node(iss, t);
+      ++iss;
+      const int cb = a.child_begin[t], cc = a.child_count[t];
+      AT sreg = 0, rreg = 0;
+      if (e < a.n_k) {
+        AT v = (AT)ldcg(cv(a.wbuf) + (long long)t * a.n_k + e);
+        if (e < a.n_x) {
+          for (int c = cb; c < cb + cc; ++c) v += (AT)ldcg(cv(a.spub) + (long long)c * a.n_x + e);
+          sreg = v;
+        }
+        yv[e] = v;
+      }
+      if (e < a.n_v) {
+        rreg = lin ? (AT)0 : (AT)cv(a.beta)[(long long)t * a.n_v + e];
+        for (int c = cb; c < cb + cc; ++c) rreg += (AT)ldcg(cv(a.rpub) + (long long)c * a.n_v + e);
+      }
+      node(t, rreg, false);
+      if (abort_) return;
+      if (e < a.n_x) mv(a.spub)[(long long)t * a.n_x + e] = (VT)sreg;
+      if (e < a.n_v) mv(a.rpub)[(long long)t * a.n_v + e] = (VT)rreg;
+      t = a.parent[t];
+      if (t < 0 || !arrive(t)) break;
+    }
+    prime();
+  }
+
+  __device__ void run() {
+    const int tid = threadIdx.x;
+    for (int j = a.n_v + tid; j < ld; j += kBT) dv[j] = 0;
+    if (tid == 0) {
+      for (int q = 0; q < S; ++q) mbar_init(&bar[q], 1);
+      fence_barrier_init();
+      fence_proxy_async();
+    }
+    __syncthreads();
+    set_cursor(chain_cursor(blockIdx.x));
+    prime();
+    for (int ti = blockIdx.x; ti < a.n_top && !abort_; ti += gridDim.x) {
+      const int t = a.top_nodes[ti];
+      if (arrive(t)) process_top(t, chain_cursor(blockIdx.x));
+    }
+    for (int ch = blockIdx.x; ch < a.n_chains && !abort_; ch += gridDim.x) {
+      const int cb = a.chain_off[ch], len = a.chain_off[ch + 1] - cb;
+      chain(a.chain_node + cb, len);
+      if (abort_) break;
+      if (mode & MODE_NOCLIMB) continue;
+      const int par = a.chain_parent[ch];
+      if (par >= 0 && arrive(par)) process_top(par, chain_cursor(ch + gridDim.x));
+    }
+    if (abort_) drain();
+  }
+};
+
+template <typename VT, typename MT>
+__global__ void __launch_bounds__(kBT, 1)
+    chain_bwd(const __grid_constant__ IterArgs a, int S, int nu, int mode) {
+  grid_dep_sync();
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  __shared__ int flag[2];
+  if (early_exit(a, nu, mode, flag, false)) return;
+  Bwd<VT, MT> k(a, smem_raw, S, nu, mode);
+  k.run();
+}
+
 // ------------------------------------------------------------------ node-parallel schedule
 // The backward sweep is linear in (w, beta).  With s = subtree sums of xi,
 // g_n = [Bbar; L]_n' [s_n; psi_n] and r = subtree sums of beta + g, the mat-vecs of
@@ -2431,12 +2788,21 @@ LaunchCfg config_t(const IterArgs& a, int num_sms, int S_max, int schedule, int 
     return c;
   }
   c.stages = fits_threads ? 1 : 0;
-  if (schedule == SCHED_HYBRID || schedule == SCHED_FUSED) {
+  if (schedule == SCHED_HYBRID) {
     const LaunchCfg ch = config_t<VT, MT>(a, num_sms, S_max, SCHED_CHAIN);
     c.grid_chain = ch.grid;
     c.stages_chain = ch.stages;
     c.smem_chain = ch.smem;
     if (ch.stages < 1) c.stages = 0;
+  }
+  if (schedule == SCHED_FUSED) {  // chain_bwd: kBT threads, as many pack slots as fit
+    int S = S_max;
+    while (S > 1 && bwd_smem_bytes<MT>(S, a.n_x, a.n_u, a.n_v) + 256 > (size_t)optin) --S;
+    c.stages_chain = S;
+    c.smem_chain = bwd_smem_bytes<MT>(S, a.n_x, a.n_u, a.n_v);
+    c.grid_chain = a.n_chains < num_sms ? a.n_chains : num_sms;
+    if (c.grid_chain < 1) c.grid_chain = 1;
+    if (c.smem_chain + 256 > (size_t)optin || 2 * a.n_k > kBT || a.n_v > kBT) c.stages = 0;
   }
   c.smem_prox = iter_smem_bytes<MT>(0, a.n_x, a.n_u, a.n_v);  // barriers + vectors, no pack slot
   c.smem_pstage = c.smem_prox + (size_t)kWarps * prox_stage_bytes<VT>(a.n_x, a.n_u);
@@ -2515,6 +2881,7 @@ int launch_t(const IterArgs& a, const LaunchCfg& c, int nu, int mode, cudaStream
         cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - (int)at.sharedSizeBytes);
     };
     allow(apg_iter<VT, MT>);
+    allow(chain_bwd<VT, MT>);
     allow(node_mv<VT, MT, false>);
     allow(node_mv<VT, MT, true>);
     allow(prox_node<VT, MT>);
@@ -2546,7 +2913,7 @@ int launch_t(const IterArgs& a, const LaunchCfg& c, int nu, int mode, cudaStream
   if ((mode & MODE_BWD) && c.schedule == SCHED_FUSED) {
     // the whole backward sweep (s, [Bbar; L]'[s; psi], r, Lambda r / (2 p) and [Bbar; L] delta)
     // along the chains and up the top nodes: every pack is read once per iteration
-    launch_dep(apg_iter<VT, MT>, c.grid_chain, c.block, c.smem_chain, s, dep, a, c.stages_chain, nu,
+    launch_dep(chain_bwd<VT, MT>, c.grid_chain, kBT, c.smem_chain, s, dep, a, c.stages_chain, nu,
                (mode & ~MODE_PROX) | MODE_WREADY);
     mark();
   } else if ((mode & MODE_BWD) && c.schedule == SCHED_HYBRID) {
