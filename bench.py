@@ -794,8 +794,10 @@ def run_serve(args):
                     s_["x"] = _plant_step(s_["P"], s_["x"], u0, k, s_["rng"])
                     s_["q"] = u0
                     n_cold += 1
-                    if n_cold % 16 == 0:
-                        log("serve: cold steps", n_cold, "of", len(sess), "after", time.perf_counter() - t_cold, "s")
+                    log("serve: cold step", n_cold, "of", len(sess), "session", sess.index(s_), "nodes",
+                        len(s_["P"]["tree"]["parent"]), "prec", s_["prec"], "iterations", r["iterations"],
+                        "rho_rel", round(r["rho_rel"], 6), "run_ms", round(r["run_ms"], 1), "at",
+                        round(time.perf_counter() - t_cold, 2))
         time.sleep(0.001)
     log("serve: cold steps done in", time.perf_counter() - t_cold, "s")
     windows = []
