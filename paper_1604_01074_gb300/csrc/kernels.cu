@@ -1161,12 +1161,15 @@ struct Kern {
     const AT is = (AT)cv(a.inv_s)[m], iz = (AT)cv(a.inv_z)[m];
     const ST zero = st_from<ST>(0.0);
     cp_async_wait_all();
-    // block norms ||lambda r|| of the two distance blocks
+    // block norms ||lambda r|| of the two distance blocks; the extrapolations w of a tank's
+    // two blocks replace y^{it-1} in the staging (nothing else reads it) for the next pass
     AT ps = 0, pz = 0;
 #pragma unroll 1
     for (int e = lane; e < n_x; e += 32) {
       const AT x = (AT)Z[e];
       const ST ws = st_extrap(Q0[e], Q1[e], c), wz = st_extrap(Q2[e], Q3[e], c);
+      Q1[e] = ws;
+      Q3[e] = wz;
       const ST qs = st_axpy(ws, ls, x - bnd[e]);
       const AT rs = st_neg(qs) ? (AT)st_val(qs) : (AT)0;
       const AT rz = (AT)st_val(box_lr(st_axpy(wz, lz, x - bnd[kThreads + e]), st_axpy(wz, lz, x - bnd[2 * kThreads + e])));
@@ -1184,7 +1187,7 @@ struct Kern {
       if (e < n_x) {
         const AT x = (AT)Z[e];
         const ST v1 = Q0[e], w1 = Q2[e];
-        const ST ws = st_extrap(v1, Q1[e], c), wz = st_extrap(w1, Q3[e], c);
+        const ST ws = Q1[e], wz = Q3[e];  // written by the first pass (same lane)
         const ST qs = st_axpy(ws, ls, x - bnd[e]);
         const ST ysn = st_scale(st_neg(qs) ? qs : zero, ks);
         const ST yzn = st_scale(box_lr(st_axpy(wz, lz, x - bnd[kThreads + e]), st_axpy(wz, lz, x - bnd[2 * kThreads + e])), kz);

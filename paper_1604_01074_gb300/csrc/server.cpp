@@ -37,6 +37,7 @@ struct Request {
   std::vector<double> p, q, dhat, eps, alpha2;
   bool has_eps = false;
   smpc_solve_opts opts{};
+  size_t admitted_bytes = 0;  // the factor's footprint counted at admission (a solve may grow it)
   // results
   bool done = false;
   int status = SMPC_OK;
@@ -92,7 +93,8 @@ Request* smpc_server::pick_locked() {
     if (in_flight_bytes + r->f->device_bytes > budget) continue;
     queue.erase(it);
     held.insert(r->f);
-    in_flight_bytes += r->f->device_bytes;
+    r->admitted_bytes = r->f->device_bytes;
+    in_flight_bytes += r->admitted_bytes;
     return r;
   }
   return nullptr;
@@ -152,7 +154,9 @@ void smpc_server::worker(int slot) {
     r->rho_rel = res.rho_rel;
     r->launches = res.launches;
     r->done = true;
-    in_flight_bytes -= r->f->device_bytes;  // the factor stays held until the ticket is polled
+    // exactly what admission added: the solve may have grown the factor's iteration buffers
+    // (the factor stays held until the ticket is polled)
+    in_flight_bytes -= r->admitted_bytes;
     cv.notify_all();
   }
   lk.unlock();

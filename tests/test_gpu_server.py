@@ -145,3 +145,27 @@ def test_closed_loop_steps_warm_start_in_order():
         smpc.smpc_server_destroy(server)
         twin.close()
         served.close()
+
+
+def test_admission_after_solves_that_grow_their_factors():
+    """A solve with more iterations than any earlier one on its factor grows the factor's
+    iteration buffers; admission must release exactly what it counted, so that later
+    requests keep being admitted (a budget room for two factors, many rounds)."""
+    import paper_1604_01074_gb300 as smpc
+    insts = _instances()[:3]
+    gs = [(P, H.Gpu(P, precision=prec)) for _, P, prec in insts]
+    try:
+        sizes = sorted(smpc.smpc_factor_device_bytes(g.fac) for _, g in gs)
+        server = smpc.smpc_server_create(sizes[-1] + sizes[-2] + (1 << 20), 2)
+        try:
+            for rnd in range(4):
+                iters = 1500 + 2000 * rnd  # every round beyond the factors' buffers so far
+                ts = [smpc.smpc_submit(server, g.fac, P["p"], P["q"], P["dhat"], P["alpha2"], eps=P["eps"],
+                                       max_iters=iters) for P, g in gs]
+                res = [_wait(smpc, server, t, timeout=60.0) for t in ts]
+                assert all(r["iterations"] == iters for r in res), rnd
+        finally:
+            smpc.smpc_server_destroy(server)
+    finally:
+        for _, g in gs:
+            g.close()
