@@ -76,6 +76,11 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
       "l"(src), "r"(bytes), "r"(smem_u32(b))
       : "memory");
 }
+// Bulk prefetch of [src, src + bytes) into L2 (a hint: no completion to wait for); src
+// 16-byte aligned, bytes a multiple of 16.
+__device__ __forceinline__ void bulk_prefetch_l2(const void* src, uint32_t bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
+}
 // One 4- or 8-byte element copied into shared memory by cp.async: the copies of a
 // thread are issued back to back without holding registers and complete at
 // cp_async_wait_all, after which the issuing thread sees them (others after a barrier).
@@ -1568,6 +1573,12 @@ struct Bwd {
   uint32_t iss = 0, use = 0;  // loads issued / consumed (the same in every thread)
   Cursor cur;                 // next chain node to load
   int cnode = -1;             // thread 0: its node id
+  // L2 prefetch: the packs of the kPre chain nodes after the last one copied are requested
+  // into L2 ahead of their shared-memory copies, so that more of each SM's stream is in
+  // flight than its pack slots hold
+  static constexpr int kPre = 2;
+  Cursor pcur;                // next chain node to prefetch
+  uint32_t pfs = 0;           // nodes prefetched (counted like iss)
   bool abort_ = false;
 
   __device__ Bwd(const IterArgs& args, unsigned char* smem, int S_, int nu_, int mode_)
@@ -1623,7 +1634,16 @@ struct Bwd {
   }
   __device__ void set_cursor(Cursor c) {
     cur = c;
+    pcur = c;
+    pfs = iss;
     if (threadIdx.x == 0) cnode = c.chain >= 0 ? node_of(c) : -1;
+  }
+  __device__ void prefetch_ahead() {
+    while (pcur.chain >= 0 && pfs < iss + kPre) {
+      if (pfs >= iss && threadIdx.x == 0) bulk_prefetch_l2(pack(node_of(pcur)), (uint32_t)(kbytes + lbytes));
+      ++pfs;
+      advance(pcur);
+    }
   }
   __device__ void issue() {
     if (cur.chain < 0) return;
@@ -1631,6 +1651,7 @@ struct Bwd {
     ++iss;
     advance(cur);
     if (threadIdx.x == 0 && cur.chain >= 0) cnode = node_of(cur);
+    prefetch_ahead();
   }
   __device__ void prime() {
     for (int q = 0; q < S; ++q) issue();
@@ -2151,6 +2172,10 @@ __global__ void __launch_bounds__(kThreads, 1) node_mv(const __grid_constant__ I
     const unsigned char* src = reinterpret_cast<const unsigned char*>(packs + (long long)m * a.pack_stride);
     bulk_g2s(sm.K(slot), src, kb, &sm.barK[slot]);
     if (DH) bulk_g2s(sm.Lm(slot), src + kp * sizeof(MT), lb, &sm.barK[slot]);
+    // the pack whose copy follows this one into the same slot, requested into L2 now, so
+    // that more of the stream is in flight than the slots hold
+    if (!shared && q + S < count)
+      bulk_prefetch_l2(packs + (long long)(m + S * G) * a.pack_stride, kb + (DH ? lb : 0u));
   };
   if (tid == 0)
     for (int q = 0; q < S && q < count && (!shared || q == 0); ++q) issue(q);
