@@ -1548,6 +1548,8 @@ __host__ __device__ inline int bwd_slices(int n_v) {
   return P > 20 ? 20 : P;
 }
 
+constexpr int kChainIds = 64;  // chain node ids kept in shared memory (longer chains: global)
+
 template <typename MT>
 __host__ __device__ inline size_t bwd_smem_bytes(int S, int n_x, int n_u, int n_v) {
   using AT = typename Acc<MT>::T;
@@ -1556,7 +1558,7 @@ __host__ __device__ inline size_t bwd_smem_bytes(int S, int n_x, int n_u, int n_
   m = round_up(m, 16) + 4 * sizeof(uint64_t);
   m = round_up(m, 16);
   m += ((size_t)3 * ld + round_up(n_k, 4) + (size_t)bwd_slices<MT>(n_v) * ld) * sizeof(AT);
-  m = round_up(m, 16) + 16 * sizeof(int);
+  m = round_up(m, 16) + (16 + kChainIds) * sizeof(int);
   return round_up(m, 128);
 }
 
@@ -1571,14 +1573,13 @@ struct Bwd {
   AT *dv, *rv, *gv, *yv, *part;
   int* flag;
   uint32_t iss = 0, use = 0;  // loads issued / consumed (the same in every thread)
-  Cursor cur;                 // next chain node to load
-  int cnode = -1;             // thread 0: its node id
-  // L2 prefetch: the packs of the kPre chain nodes after the last one copied are requested
-  // into L2 ahead of their shared-memory copies, so that more of each SM's stream is in
-  // flight than its pack slots hold
-  static constexpr int kPre = 2;
-  Cursor pcur;                // next chain node to prefetch
-  uint32_t pfs = 0;           // nodes prefetched (counted like iss)
+  // next chain node to load: chain, position k (counting down) and the chain's first entry
+  // in chain_node, so that a node id is one load whose latency is spent while a node runs
+  struct Cur {
+    int chain, k, off;
+  } cur;
+  int cnode = -1;             // thread 0: the node id at cur
+  int* cids;                  // the current chain's node ids (kChainIds at most), top-down
   bool abort_ = false;
 
   __device__ Bwd(const IterArgs& args, unsigned char* smem, int S_, int nu_, int mode_)
@@ -1602,6 +1603,7 @@ struct Bwd {
     v += bwd_slices<MT>(a.n_v) * ld;
     off = round_up(reinterpret_cast<unsigned char*>(v) - base, 16);
     flag = reinterpret_cast<int*>(base + off);
+    cids = flag + 16;
   }
   __device__ MT* K(int s) const { return reinterpret_cast<MT*>(base + (size_t)s * (kbytes + lbytes)); }
   __device__ MT* Lm(int s) const { return reinterpret_cast<MT*>(base + (size_t)s * (kbytes + lbytes) + kbytes); }
@@ -1613,17 +1615,18 @@ struct Bwd {
   __device__ bool no_affine() const { return (mode & (MODE_LINEAR | MODE_DELTA)) != 0; }
 
   // ---------------------------------------------------------- pipeline
-  __device__ Cursor chain_cursor(int chain) const {
-    Cursor c;
+  __device__ Cur chain_cursor(int chain) const {
+    Cur c;
     c.chain = chain < a.n_chains ? chain : -1;
-    c.k = c.chain >= 0 ? a.chain_off[c.chain + 1] - a.chain_off[c.chain] - 1 : 0;
+    c.off = c.chain >= 0 ? a.chain_off[c.chain] : 0;
+    c.k = c.chain >= 0 ? a.chain_off[c.chain + 1] - c.off - 1 : 0;
     return c;
   }
-  __device__ void advance(Cursor& c) const {
+  __device__ void advance(Cur& c) const {
     if (c.chain < 0) return;
     if (--c.k < 0) c = chain_cursor(c.chain + gridDim.x);
   }
-  __device__ int node_of(const Cursor& c) const { return a.chain_node[a.chain_off[c.chain] + c.k]; }
+  __device__ int node_of(const Cur& c) const { return a.chain_node[c.off + c.k]; }
   __device__ void copy_node(uint32_t seq, int n) {  // thread 0
     const int slot = seq % S;
     fence_proxy_async();
@@ -1632,26 +1635,16 @@ struct Bwd {
     bulk_g2s(K(slot), src, (uint32_t)kbytes, &bar[slot]);
     bulk_g2s(Lm(slot), src + kpad<MT>(a.n_k, a.n_v) * sizeof(MT), (uint32_t)lbytes, &bar[slot]);
   }
-  __device__ void set_cursor(Cursor c) {
+  __device__ void set_cursor(Cur c) {
     cur = c;
-    pcur = c;
-    pfs = iss;
     if (threadIdx.x == 0) cnode = c.chain >= 0 ? node_of(c) : -1;
-  }
-  __device__ void prefetch_ahead() {
-    while (pcur.chain >= 0 && pfs < iss + kPre) {
-      if (pfs >= iss && threadIdx.x == 0) bulk_prefetch_l2(pack(node_of(pcur)), (uint32_t)(kbytes + lbytes));
-      ++pfs;
-      advance(pcur);
-    }
   }
   __device__ void issue() {
     if (cur.chain < 0) return;
     if (threadIdx.x == 0) copy_node(iss, cnode);
     ++iss;
     advance(cur);
-    if (threadIdx.x == 0 && cur.chain >= 0) cnode = node_of(cur);
-    prefetch_ahead();
+    if (threadIdx.x == 0 && cur.chain >= 0) cnode = node_of(cur);  // used at the next issue
   }
   __device__ void prime() {
     for (int q = 0; q < S; ++q) issue();
@@ -1676,7 +1669,7 @@ struct Bwd {
     __syncthreads();
   }
   // let every issued load land (bounded) and restart issuing at `next`
-  __device__ void flush(Cursor next) {
+  __device__ void flush(Cur next) {
     bool ok = true;
     for (; use < iss; ++use) ok &= mbar_wait(&bar[use % S], (use / S) & 1);
     set_cursor(next);
@@ -1783,11 +1776,20 @@ struct Bwd {
     if (refill) issue();
   }
 
-  __device__ void chain(const int* nodes, int len) {
+  __device__ void chain(const int* gnodes, int len) {
     const int e = threadIdx.x;
     AT sreg = 0, rreg = 0;
     const bool lin = no_affine();
     const VT* wb = cv(a.wbuf);
+    // the chain's node ids into shared memory: per node only shared-memory reads lead to
+    // the next node's vector loads
+    const int* nodes = gnodes;
+    if (len <= kChainIds) {
+      __syncthreads();  // the previous chain's ids are no longer read
+      for (int q = e; q < len; q += kBT) cids[q] = gnodes[q];
+      __syncthreads();
+      nodes = cids;
+    }
     int m = nodes[len - 1];
     AT wcur = e < a.n_k ? (AT)wb[(long long)m * a.n_k + e] : (AT)0;
     AT bcur = (e < a.n_v && !lin) ? (AT)cv(a.beta)[(long long)m * a.n_v + e] : (AT)0;
@@ -1834,7 +1836,7 @@ struct Bwd {
   }
 
   // top node t (this CTA arrived last), then up while it stays last
-  __device__ void process_top(int t, Cursor next) {
+  __device__ void process_top(int t, Cur next) {
     flush(next);
     if (abort_) return;
     const int e = threadIdx.x;
@@ -2172,10 +2174,6 @@ __global__ void __launch_bounds__(kThreads, 1) node_mv(const __grid_constant__ I
     const unsigned char* src = reinterpret_cast<const unsigned char*>(packs + (long long)m * a.pack_stride);
     bulk_g2s(sm.K(slot), src, kb, &sm.barK[slot]);
     if (DH) bulk_g2s(sm.Lm(slot), src + kp * sizeof(MT), lb, &sm.barK[slot]);
-    // the pack whose copy follows this one into the same slot, requested into L2 now, so
-    // that more of the stream is in flight than the slots hold
-    if (!shared && q + S < count)
-      bulk_prefetch_l2(packs + (long long)(m + S * G) * a.pack_stride, kb + (DH ? lb : 0u));
   };
   if (tid == 0)
     for (int q = 0; q < S && q < count && (!shared || q == 0); ++q) issue(q);
