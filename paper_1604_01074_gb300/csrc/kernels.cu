@@ -1533,19 +1533,13 @@ __global__ void __launch_bounds__(kThreads, 1)
 
 // ------------------------------------------------------------------ fused backward pass (schedule 4)
 // The whole backward sweep of Algorithm 1 in one launch with every pack read once: one CTA
-// of kBT threads per chain (and the top nodes by last arrival, as in apg_iter).  Per node:
-// g = [Bbar; L]' [s; psi], r = r_below + beta + g, delta = Lambda r, h = [Bbar; L] delta.
-// [Bbar; L] (used twice) is streamed through S shared-memory slots with cp.async.bulk;
-// Lambda (used once) goes from global memory straight into registers, each thread loading
-// its own 16-byte pieces of the next node's Lambda while the current node finishes.  Keeping
-// Lambda out of the slots lets one more [Bbar; L] copy be in flight per SM, and 512 threads
-// per CTA (one CTA per SM) halve each mat-vec's serial work against apg_iter's 256.
+// of kBT threads per chain (and the top nodes by last arrival, as in apg_iter), each chain
+// node's pack [Bbar; L | Lambda / (2 p_n)] streamed through S shared-memory slots with
+// cp.async.bulk while the previous nodes are processed.  Per node, three mat-vecs from
+// shared memory: g = [Bbar; L]' [s; psi], r = r_below + beta + g, delta = Lambda r, and
+// h = [Bbar; L] delta.  512 threads per CTA (one CTA per SM) halve each mat-vec's serial
+// work against apg_iter's 256, which keeps the node time below the pack's HBM time.
 constexpr int kBT = 512;
-// Lambda rows per thread (n_v <= lam_rows x slices): float64 rows hold 2 entries per 16 bytes,
-// so a float64 pack has about half the slices and needs more rows per thread
-template <typename MT>
-__host__ __device__ constexpr int lam_rows() { return sizeof(MT) == 8 ? 10 : 8; }
-constexpr int kChainIds = 64;  // chain node ids kept in shared memory (longer chains: global)
 
 template <typename MT>
 __host__ __device__ inline int bwd_slices(int n_v) {
@@ -1554,57 +1548,48 @@ __host__ __device__ inline int bwd_slices(int n_v) {
   return P > 20 ? 20 : P;
 }
 
+constexpr int kChainIds = 64;  // chain node ids kept in shared memory (longer chains: global)
+
 template <typename MT>
 __host__ __device__ inline size_t bwd_smem_bytes(int S, int n_x, int n_u, int n_v) {
   using AT = typename Acc<MT>::T;
   const int n_k = n_x + n_u, ld = row_stride<MT>(n_v);
-  size_t m = (size_t)S * kpad<MT>(n_k, n_v) * sizeof(MT);
-  m = round_up(m, 16) + 8 * sizeof(uint64_t);
+  size_t m = (size_t)S * (kpad<MT>(n_k, n_v) + lpad<MT>(n_v)) * sizeof(MT);
+  m = round_up(m, 16) + 4 * sizeof(uint64_t);
   m = round_up(m, 16);
   m += ((size_t)3 * ld + round_up(n_k, 4) + (size_t)bwd_slices<MT>(n_v) * ld) * sizeof(AT);
   m = round_up(m, 16) + (16 + kChainIds) * sizeof(int);
   return round_up(m, 128);
 }
-template <typename MT>
-__host__ __device__ inline bool bwd_fits(int n_x, int n_u, int n_v) {
-  const int P = bwd_slices<MT>(n_v);
-  return 2 * (n_x + n_u) <= kBT && n_v <= kBT && (n_v + P - 1) / P <= lam_rows<MT>();
-}
 
 template <typename VT, typename MT>
 struct Bwd {
   using AT = typename Acc<MT>::T;
-  static constexpr int V = Vec<MT>::V;
-  static constexpr int kLamRows = lam_rows<MT>();
   const IterArgs& a;
-  int S, nu, mode, ld, P, G, rl;
+  int S, nu, mode, ld;
   unsigned char* base;
-  size_t kbytes;
-  uint64_t* bar;  // one per slot
+  size_t kbytes, lbytes;
+  uint64_t* bar;  // one per slot: the node's [Bbar; L] and Lambda copies
   AT *dv, *rv, *gv, *yv, *part;
   int* flag;
-  int* cids;                  // the current chain's node ids, top-down
-  uint32_t iss = 0, use = 0;  // [Bbar; L] loads issued / consumed (the same in every thread)
+  uint32_t iss = 0, use = 0;  // loads issued / consumed (the same in every thread)
   // next chain node to load: chain, position k (counting down) and the chain's first entry
   // in chain_node, so that a node id is one load whose latency is spent while a node runs
   struct Cur {
     int chain, k, off;
   } cur;
-  int cnode = -1;   // thread 0: the node id at cur
-  uint4 lam[kLamRows];  // this thread's 16-byte pieces of a node's Lambda rows
-  int lam_node = -1;    // the node whose Lambda is in lam
+  int cnode = -1;             // thread 0: the node id at cur
+  int* cids;                  // the current chain's node ids (kChainIds at most), top-down
   bool abort_ = false;
 
   __device__ Bwd(const IterArgs& args, unsigned char* smem, int S_, int nu_, int mode_)
       : a(args), S(S_), nu(nu_), mode(mode_), base(smem) {
     ld = row_stride<MT>(a.n_v);
-    G = ld / V;
-    P = bwd_slices<MT>(a.n_v);
-    rl = (a.n_v + P - 1) / P;
     kbytes = kpad<MT>(a.n_k, a.n_v) * sizeof(MT);
-    size_t off = round_up((size_t)S * kbytes, 16);
+    lbytes = lpad<MT>(a.n_v) * sizeof(MT);
+    size_t off = round_up((size_t)S * (kbytes + lbytes), 16);
     bar = reinterpret_cast<uint64_t*>(base + off);
-    off = round_up(off + 8 * sizeof(uint64_t), 16);
+    off = round_up(off + 4 * sizeof(uint64_t), 16);
     AT* v = reinterpret_cast<AT*>(base + off);
     dv = v;
     v += ld;
@@ -1615,12 +1600,13 @@ struct Bwd {
     yv = v;
     v += round_up(a.n_k, 4);
     part = v;
-    v += P * ld;
+    v += bwd_slices<MT>(a.n_v) * ld;
     off = round_up(reinterpret_cast<unsigned char*>(v) - base, 16);
     flag = reinterpret_cast<int*>(base + off);
     cids = flag + 16;
   }
-  __device__ MT* K(int s) const { return reinterpret_cast<MT*>(base + (size_t)s * kbytes); }
+  __device__ MT* K(int s) const { return reinterpret_cast<MT*>(base + (size_t)s * (kbytes + lbytes)); }
+  __device__ MT* Lm(int s) const { return reinterpret_cast<MT*>(base + (size_t)s * (kbytes + lbytes) + kbytes); }
   __device__ const MT* pack(int n) const {
     return reinterpret_cast<const MT*>(a.packs) + (long long)n * a.pack_stride;
   }
@@ -1628,7 +1614,7 @@ struct Bwd {
   __device__ VT* mv(void* p) const { return reinterpret_cast<VT*>(p); }
   __device__ bool no_affine() const { return (mode & (MODE_LINEAR | MODE_DELTA)) != 0; }
 
-  // ---------------------------------------------------------- [Bbar; L] pipeline
+  // ---------------------------------------------------------- pipeline
   __device__ Cur chain_cursor(int chain) const {
     Cur c;
     c.chain = chain < a.n_chains ? chain : -1;
@@ -1644,8 +1630,10 @@ struct Bwd {
   __device__ void copy_node(uint32_t seq, int n) {  // thread 0
     const int slot = seq % S;
     fence_proxy_async();
-    mbar_expect_tx(&bar[slot], (uint32_t)kbytes);
-    bulk_g2s(K(slot), pack(n), (uint32_t)kbytes, &bar[slot]);
+    mbar_expect_tx(&bar[slot], (uint32_t)(kbytes + lbytes));
+    const unsigned char* src = reinterpret_cast<const unsigned char*>(pack(n));
+    bulk_g2s(K(slot), src, (uint32_t)kbytes, &bar[slot]);
+    bulk_g2s(Lm(slot), src + kpad<MT>(a.n_k, a.n_v) * sizeof(MT), (uint32_t)lbytes, &bar[slot]);
   }
   __device__ void set_cursor(Cur c) {
     cur = c;
@@ -1688,83 +1676,15 @@ struct Bwd {
     if (__syncthreads_or(!ok)) fail();
   }
 
-  // ---------------------------------------------------------- Lambda in registers
-  // Thread (g, p), p < P, g < G, holds columns g V .. g V + V - 1 of Lambda rows p rl .. p rl +
-  // rl - 1: read-only 16-byte loads, coalesced over g; issued early, used a node later.
-  __device__ void load_lam(int m) {
+  // ---------------------------------------------------------- mat-vecs from shared memory
+  // out[j] = sum_i A[i ld + j] x[i], j < C (A' x): thread (g, p) accumulates columns
+  // g V .. g V + V - 1 over the p-th row slice; slices are added in a fixed order.
+  __device__ void mtv_t(const MT* A, int R, int C, const AT* x, AT* out) {
+    constexpr int V = Vec<MT>::V;
     const int t = threadIdx.x;
-    lam_node = m;
-    if (t >= P * G) return;
-    const int g = t % G, p = t / G;
-    const MT* L = pack(m) + kpad<MT>(a.n_k, a.n_v) + g * V;
-#pragma unroll
-    for (int r = 0; r < kLamRows; ++r) {
-      const int i = p * rl + r;
-      if (r < rl && i < a.n_v) lam[r] = __ldg(reinterpret_cast<const uint4*>(L + (long long)i * ld));
-    }
-  }
-  __device__ static void unpack(const uint4& q, float (&o)[4]) {
-    o[0] = __uint_as_float(q.x); o[1] = __uint_as_float(q.y); o[2] = __uint_as_float(q.z); o[3] = __uint_as_float(q.w);
-  }
-  __device__ static void unpack(const uint4& q, double (&o)[2]) {
-    o[0] = __hiloint2double((int)q.y, (int)q.x);
-    o[1] = __hiloint2double((int)q.w, (int)q.z);
-  }
-  __device__ static void unpack(const uint4& q, float (&o)[8]) {  // bfloat16 -> float32: a 16-bit shift
-    o[0] = __uint_as_float(q.x << 16); o[1] = __uint_as_float(q.x & 0xffff0000u);
-    o[2] = __uint_as_float(q.y << 16); o[3] = __uint_as_float(q.y & 0xffff0000u);
-    o[4] = __uint_as_float(q.z << 16); o[5] = __uint_as_float(q.z & 0xffff0000u);
-    o[6] = __uint_as_float(q.w << 16); o[7] = __uint_as_float(q.w & 0xffff0000u);
-  }
-  // the slices' partial sums into out[j], j < C, in a fixed order
-  __device__ void reduce_part(int C, AT* out) {
-    for (int j = threadIdx.x; j < C; j += kBT) {
-      AT v[20];
-#pragma unroll
-      for (int p = 0; p < 20; ++p) v[p] = p < P ? part[p * ld + j] : (AT)0;
-      AT s0 = 0, s1 = 0;
-#pragma unroll
-      for (int p = 0; p < 20; p += 2) {
-        s0 += v[p];
-        s1 += v[p + 1];
-      }
-      out[j] = s0 + s1;
-    }
-    __syncthreads();
-  }
-  // dv = Lambda rv (Lambda is symmetric, so its columns are its rows)
-  __device__ void lam_product() {
-    const int t = threadIdx.x;
-    if (t < P * G) {
-      const int g = t % G, p = t / G;
-      AT acc[V];
-#pragma unroll
-      for (int k = 0; k < V; ++k) acc[k] = 0;
-#pragma unroll
-      for (int r = 0; r < kLamRows; ++r) {
-        const int i = p * rl + r;
-        if (r < rl && i < a.n_v) {
-          AT av[V];
-          unpack(lam[r], av);
-          const AT xi = rv[i];
-#pragma unroll
-          for (int k = 0; k < V; ++k) acc[k] += av[k] * xi;
-        }
-      }
-      AT* dst = part + p * ld + g * V;
-#pragma unroll
-      for (int k = 0; k < V; ++k) dst[k] = acc[k];
-    }
-    __syncthreads();
-    reduce_part(a.n_v, dv);
-  }
-
-  // ---------------------------------------------------------- [Bbar; L] from shared memory
-  // out[j] = sum_i A[i ld + j] x[i], j < n_v (A' x): thread (g, p) accumulates columns
-  // g V .. g V + V - 1 over the p-th row slice; the slices are added in a fixed order.
-  __device__ void kt_product(const MT* A, const AT* x, AT* out) {
-    const int t = threadIdx.x;
-    const int R = a.n_k, rc = (R + P - 1) / P;
+    const int G = ld / V;
+    const int P = bwd_slices<MT>(a.n_v);
+    const int rc = (R + P - 1) / P;
     if (t < P * G) {
       const int g = t % G, p = t / G;
       const int i0 = p * rc, i1 = min(R, i0 + rc);
@@ -1785,12 +1705,25 @@ struct Bwd {
       for (int k = 0; k < V; ++k) dst[k] = acc[k];
     }
     __syncthreads();
-    reduce_part(a.n_v, out);
+    for (int j = t; j < C; j += kBT) {
+      AT v[20];
+#pragma unroll
+      for (int p = 0; p < 20; ++p) v[p] = p < P ? part[p * ld + j] : (AT)0;
+      AT s0 = 0, s1 = 0;
+#pragma unroll
+      for (int p = 0; p < 20; p += 2) {  // fixed order: deterministic
+        s0 += v[p];
+        s1 += v[p + 1];
+      }
+      out[j] = s0 + s1;
+    }
+    __syncthreads();
   }
-  // h of node m = A dv (n_k rows): two threads per row, each half of the columns,
+  // h of node m = A dv (R = n_k rows): two threads per row, each half of the columns,
   // combined by a shuffle; written to global memory (anchor launches: to h_a, h = 0).
-  __device__ void k_product_out(const MT* A, int m) {
-    const int Gh = (G + 1) / 2;
+  __device__ void mtv_n_out(const MT* A, int m) {
+    constexpr int V = Vec<MT>::V;
+    const int G = ld / V, Gh = (G + 1) / 2;
     const int t = threadIdx.x, i = t >> 1, half = t & 1;
     AT acc0 = 0, acc1 = 0;
     if (i < a.n_k) {
@@ -1823,26 +1756,23 @@ struct Bwd {
   }
 
   // ---------------------------------------------------------- one node's backward step
-  // yv holds [s; psi]; thread j < n_v holds r_j (children and beta) in rreg; next: the node
-  // this CTA processes after m (-1: not known), whose Lambda is loaded during this step.
-  __device__ void node(int m, AT& rreg, bool refill, int next) {
+  // yv holds [s; psi]; thread j < n_v holds r_j (children and beta) in rreg.
+  __device__ void node(int m, AT& rreg, bool refill) {
     const int t = threadIdx.x;
-    if (lam_node != m) load_lam(m);
     const int slot = wait();
     if (abort_) return;
-    kt_product(K(slot), yv, gv);
+    mtv_t(K(slot), a.n_k, a.n_v, yv, gv);
     if (t < a.n_v) {
       rreg += gv[t];
       rv[t] = rreg;
     }
     __syncthreads();
-    lam_product();
-    if (next >= 0) load_lam(next);
+    mtv_t(Lm(slot), a.n_v, a.n_v, rv, dv);  // Lambda is symmetric
     if (a.pscale) {  // shared pack: delta = (Lambda r) / (2 p_n)
       if (t < a.n_v) dv[t] *= (AT)cv(a.pscale)[m];
       __syncthreads();
     }
-    k_product_out(K(slot), m);
+    mtv_n_out(K(slot), m);
     if (refill) issue();
   }
 
@@ -1851,9 +1781,11 @@ struct Bwd {
     AT sreg = 0, rreg = 0;
     const bool lin = no_affine();
     const VT* wb = cv(a.wbuf);
+    // the chain's node ids into shared memory: per node only shared-memory reads lead to
+    // the next node's vector loads
     const int* nodes = gnodes;
-    if (len <= kChainIds) {  // per node, only shared-memory reads lead to the next node's loads
-      __syncthreads();
+    if (len <= kChainIds) {
+      __syncthreads();  // the previous chain's ids are no longer read
       for (int q = e; q < len; q += kBT) cids[q] = gnodes[q];
       __syncthreads();
       nodes = cids;
@@ -1863,9 +1795,9 @@ struct Bwd {
     AT bcur = (e < a.n_v && !lin) ? (AT)cv(a.beta)[(long long)m * a.n_v + e] : (AT)0;
     for (int k = len - 1; k >= 0; --k) {
       m = nodes[k];
-      const int mn = k > 0 ? nodes[k - 1] : -1;
       AT wnext = 0, bnext = 0;
-      if (mn >= 0) {  // the next node's vectors into registers while this node runs
+      if (k > 0) {  // the next node's vectors into registers while this node runs
+        const int mn = nodes[k - 1];
         if (e < a.n_k) wnext = (AT)wb[(long long)mn * a.n_k + e];
         if (e < a.n_v && !lin) bnext = (AT)cv(a.beta)[(long long)mn * a.n_v + e];
       }
@@ -1876,7 +1808,7 @@ struct Bwd {
         yv[e] = wcur;
       }
       rreg += bcur;
-      node(m, rreg, true, mn);
+      node(m, rreg, true);
       if (abort_) return;
       wcur = wnext;
       bcur = bnext;
@@ -1926,7 +1858,7 @@ struct Bwd {
         rreg = lin ? (AT)0 : (AT)cv(a.beta)[(long long)t * a.n_v + e];
         for (int c = cb; c < cb + cc; ++c) rreg += (AT)ldcg(cv(a.rpub) + (long long)c * a.n_v + e);
       }
-      node(t, rreg, false, -1);
+      node(t, rreg, false);
       if (abort_) return;
       if (e < a.n_x) mv(a.spub)[(long long)t * a.n_x + e] = (VT)sreg;
       if (e < a.n_v) mv(a.rpub)[(long long)t * a.n_v + e] = (VT)rreg;
@@ -2889,14 +2821,14 @@ LaunchCfg config_t(const IterArgs& a, int num_sms, int S_max, int schedule, int 
     c.smem_chain = ch.smem;
     if (ch.stages < 1) c.stages = 0;
   }
-  if (schedule == SCHED_FUSED) {  // chain_bwd: kBT threads, as many [Bbar; L] slots as fit (<= 8)
-    int S = 8;
+  if (schedule == SCHED_FUSED) {  // chain_bwd: kBT threads, as many pack slots as fit
+    int S = S_max;
     while (S > 1 && bwd_smem_bytes<MT>(S, a.n_x, a.n_u, a.n_v) + 256 > (size_t)optin) --S;
     c.stages_chain = S;
     c.smem_chain = bwd_smem_bytes<MT>(S, a.n_x, a.n_u, a.n_v);
     c.grid_chain = a.n_chains < num_sms ? a.n_chains : num_sms;
     if (c.grid_chain < 1) c.grid_chain = 1;
-    if (c.smem_chain + 256 > (size_t)optin || !bwd_fits<MT>(a.n_x, a.n_u, a.n_v)) c.stages = 0;
+    if (c.smem_chain + 256 > (size_t)optin || 2 * a.n_k > kBT || a.n_v > kBT) c.stages = 0;
   }
   c.smem_prox = iter_smem_bytes<MT>(0, a.n_x, a.n_u, a.n_v);  // barriers + vectors, no pack slot
   c.smem_pstage = c.smem_prox + (size_t)kWarps * prox_stage_bytes<VT>(a.n_x, a.n_u);
