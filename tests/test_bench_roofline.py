@@ -29,6 +29,11 @@ def test_stage_bytes_per_node_match_the_matrix_entries():
     assert bench.stage_bytes("node_mv_dh", N, NX, NU, NV, 1, True) == N * 4 * (NV + NK)
     # kernels without a pack have no byte model
     assert bench.stage_bytes("prox_node", N, NX, NU, NV, 1, False) is None
+    # the fused backward pass reads each pack once: [Bbar; L] and Lambda, w and beta in, h out,
+    # s and r published
+    fused = bench.stage_bytes("apg_iter_bwd", N, NX, NU, NV, 1, False)
+    assert fused == N * 4 * (NK * NV + NV * NV + 2 * NK + NX + 2 * NV)
+    assert round(fused / 1e6, 1) == 226.3
 
 
 def test_recorded_traffic_follows_the_kernel_source(tmp_path, monkeypatch):
@@ -55,8 +60,11 @@ def test_committed_traffic_matches_the_committed_kernels():
     src = open(os.path.join(here, "paper_1604_01074_gb300", "csrc", "kernels.cu"), "rb").read()
     if hashlib.sha256(src).hexdigest()[:16] != rec["kernel_sha256_16"]:
         return  # kernels changed since the capture: bench.py reports traffic null
-    for key, stage in (("fp32_node_mv_dh", "node_mv_dh"), ("fp32_node_mv_gt", "node_mv_gt"),
-                       ("fp32_apg_iter_gt", "apg_iter_gt")):
-        if key in rec:
-            ratio = rec[key]["dram_bytes_per_launch"] / bench.stage_bytes(stage, N, NX, NU, NV, 1, False)
-            assert 1.0 <= ratio <= 1.08, (key, ratio)
+    for key, val in rec.items():
+        if not isinstance(val, dict):
+            continue
+        prec, rest = key.split("_", 1)
+        stage, n = rest.rsplit("_", 1)
+        ratio = val["dram_bytes_per_launch"] / bench.stage_bytes(stage, int(n), NX, NU, NV,
+                                                                 {"fp32": 1, "bf16": 2}[prec], False)
+        assert 1.0 <= ratio <= 1.08, (key, ratio)
