@@ -1705,25 +1705,18 @@ struct Bwd {
       for (int k = 0; k < V; ++k) dst[k] = acc[k];
     }
     __syncthreads();
-    reduce_part(C, out);
-  }
-  // out[j] = the sum of the P slices' partials of column j, j < C (C <= kBT / 4): four
-  // threads per column each add every fourth slice, then two shuffles (a fixed order, so
-  // the result is deterministic).
-  __device__ void reduce_part(int C, AT* out) {
-    const int t = threadIdx.x, j = t >> 2, q = t & 3;
-    const int P = bwd_slices<MT>(a.n_v);
-    AT v = 0;
-    if (j < C) {
-      AT w[5];
+    for (int j = t; j < C; j += kBT) {
+      AT v[20];
 #pragma unroll
-      for (int k = 0; k < 5; ++k) w[k] = q + 4 * k < P ? part[(q + 4 * k) * ld + j] : (AT)0;
+      for (int p = 0; p < 20; ++p) v[p] = p < P ? part[p * ld + j] : (AT)0;
+      AT s0 = 0, s1 = 0;
 #pragma unroll
-      for (int k = 0; k < 5; ++k) v += w[k];
+      for (int p = 0; p < 20; p += 2) {  // fixed order: deterministic
+        s0 += v[p];
+        s1 += v[p + 1];
+      }
+      out[j] = s0 + s1;
     }
-    v += __shfl_xor_sync(0xffffffffu, v, 1);
-    v += __shfl_xor_sync(0xffffffffu, v, 2);
-    if (j < C && q == 0) out[j] = v;
     __syncthreads();
   }
   // h of node m = A dv (R = n_k rows): two threads per row, each half of the columns,
@@ -2835,7 +2828,7 @@ LaunchCfg config_t(const IterArgs& a, int num_sms, int S_max, int schedule, int 
     c.smem_chain = bwd_smem_bytes<MT>(S, a.n_x, a.n_u, a.n_v);
     c.grid_chain = a.n_chains < num_sms ? a.n_chains : num_sms;
     if (c.grid_chain < 1) c.grid_chain = 1;
-    if (c.smem_chain + 256 > (size_t)optin || 2 * a.n_k > kBT || 4 * a.n_v > kBT) c.stages = 0;
+    if (c.smem_chain + 256 > (size_t)optin || 2 * a.n_k > kBT || a.n_v > kBT) c.stages = 0;
   }
   c.smem_prox = iter_smem_bytes<MT>(0, a.n_x, a.n_u, a.n_v);  // barriers + vectors, no pack slot
   c.smem_pstage = c.smem_prox + (size_t)kWarps * prox_stage_bytes<VT>(a.n_x, a.n_u);
