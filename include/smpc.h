@@ -165,6 +165,14 @@ typedef struct smpc_solve_opts {
    * solves with many different settings accumulate graphs: one per chunk and setting.
    * 0: plain launches.  smpc_solve only; smpc_solve_static ignores it. */
   int32_t use_graph;
+  /* 1: also keep the ergodic primal average of Sec. IV-A (after eq. apg-iteration),
+   * zbar^nu = (1 - theta_nu) zbar^{nu-1} + theta_nu z^nu with zbar^0 = z^0, over the
+   * iterates of this solve (theta restarts at every solve, warm or cold), in the vector
+   * type; a forest's tree stops averaging at its own stop.  Costs one read and write of
+   * zbar per node and iteration in the prox launch; the first such solve on a factor
+   * allocates its n_nodes * (n_x + n_u) entries.  Returned through smpc_result's xbar and
+   * ubar.  0: not kept.  smpc_solve_static refuses it (SMPC_EINVAL). */
+  int32_t ergodic;
 } smpc_solve_opts;
 
 /* Outputs.  Device pointers may be NULL (not copied).  Host outputs are filled
@@ -181,6 +189,8 @@ typedef struct smpc_result {
   int32_t launches;     /* out: kernel launches the solve enqueued (set on return) */
   double queue_ms;      /* out (smpc_poll only): submit to admission, host wall clock */
   double run_ms;        /* out (smpc_poll only): admission to completion, host wall clock */
+  void* ubar;           /* device, n_nodes * n_u: ergodic average of u (opts->ergodic = 1 only) */
+  void* xbar;           /* device, n_nodes * n_x: ergodic average of x (opts->ergodic = 1 only) */
 } smpc_result;
 
 typedef struct smpc_tree_info {

@@ -47,14 +47,14 @@ class smpc_step_data(ctypes.Structure):
 class smpc_solve_opts(ctypes.Structure):
     _fields_ = [("max_iters", ctypes.c_int32), ("tol", ctypes.c_double), ("warm_start", ctypes.c_int32),
                 ("check_every", ctypes.c_int32), ("sync", ctypes.c_int32), ("polish_iters", ctypes.c_int32),
-                ("anchor_every", ctypes.c_int32), ("use_graph", ctypes.c_int32)]
+                ("anchor_every", ctypes.c_int32), ("use_graph", ctypes.c_int32), ("ergodic", ctypes.c_int32)]
 
 
 class smpc_result(ctypes.Structure):
     _fields_ = [("u", ctypes.c_void_p), ("x", ctypes.c_void_p), ("y", ctypes.c_void_p), ("u0_host", _dp),
                 ("history_host", _dp), ("iterations", ctypes.c_int32), ("rho", ctypes.c_double),
                 ("rho_rel", ctypes.c_double), ("launches", ctypes.c_int32), ("queue_ms", ctypes.c_double),
-                ("run_ms", ctypes.c_double)]
+                ("run_ms", ctypes.c_double), ("ubar", ctypes.c_void_p), ("xbar", ctypes.c_void_p)]
 
 
 class smpc_tree_info(ctypes.Structure):
@@ -237,11 +237,12 @@ def smpc_factor_steps(fac, n, n_u):
 
 def smpc_solve(fac, p, q, dhat, alpha2, eps=None, max_iters=500, tol=0.0, warm_start=0, check_every=0, sync=1,
                u=None, x=None, y=None, u0_host=None, history_host=None, stream=None, polish_iters=0,
-               anchor_every=0, use_graph=0, _entry="smpc_solve"):
+               anchor_every=0, use_graph=0, ergodic=0, ubar=None, xbar=None, _entry="smpc_solve"):
     """u, x, y: optional torch device tensors (or raw device pointers) receiving the outputs.
     u0_host / history_host: optional numpy float64 arrays filled when sync=1.  use_graph=1
     enqueues each chunk of iterations as a CUDA graph, captured once per chunk and
-    settings and replayed by later solves of the factor."""
+    settings and replayed by later solves of the factor.  ergodic=1 keeps the ergodic
+    primal average, copied to the device tensors ubar and xbar."""
     k = _Keep()
 
     def arg(a):  # host array, or an int device address of float64 data
@@ -251,7 +252,7 @@ def smpc_solve(fac, p, q, dhat, alpha2, eps=None, max_iters=500, tol=0.0, warm_s
 
     D = smpc_step_data(arg(p), arg(q), arg(dhat), arg(eps), arg(alpha2))
     O = smpc_solve_opts(int(max_iters), float(tol), int(warm_start), int(check_every), int(sync), int(polish_iters),
-                        int(anchor_every), int(use_graph))
+                        int(anchor_every), int(use_graph), int(ergodic))
 
     def dptr(t):
         if t is None:
@@ -260,7 +261,8 @@ def smpc_solve(fac, p, q, dhat, alpha2, eps=None, max_iters=500, tol=0.0, warm_s
 
     R = smpc_result(dptr(u), dptr(x), dptr(y),
                     None if u0_host is None else u0_host.ctypes.data_as(_dp),
-                    None if history_host is None else history_host.ctypes.data_as(_dp), -1, 0.0, 0.0, 0)
+                    None if history_host is None else history_host.ctypes.data_as(_dp), -1, 0.0, 0.0, 0, 0.0, 0.0,
+                    dptr(ubar), dptr(xbar))
     if stream is None:
         s = None
     elif isinstance(stream, int):
@@ -273,13 +275,13 @@ def smpc_solve(fac, p, q, dhat, alpha2, eps=None, max_iters=500, tol=0.0, warm_s
 
 def smpc_solve_static(fac, p, q, dhat, alpha2, eps=None, max_iters=500, tol=0.0, warm_start=0, check_every=0,
                       sync=1, u=None, x=None, y=None, u0_host=None, history_host=None, stream=None, polish_iters=0,
-                      anchor_every=0):
+                      anchor_every=0, ergodic=0):
     """smpc_solve without memory allocation (scratch in the library's static device
-    array); same arguments and results as smpc_solve."""
+    array); same arguments and results as smpc_solve (ergodic=1 is refused)."""
     return smpc_solve(fac, p, q, dhat, alpha2, eps=eps, max_iters=max_iters, tol=tol, warm_start=warm_start,
                       check_every=check_every, sync=sync, u=u, x=x, y=y, u0_host=u0_host,
                       history_host=history_host, stream=stream, polish_iters=polish_iters,
-                      anchor_every=anchor_every, _entry="smpc_solve_static")
+                      anchor_every=anchor_every, ergodic=ergodic, _entry="smpc_solve_static")
 
 
 def smpc_profile_solve(fac, p, q, dhat, alpha2, eps=None, iters=50):
@@ -315,26 +317,27 @@ def smpc_server_destroy(server):
 
 
 def smpc_submit(server, fac, p, q, dhat, alpha2, eps=None, max_iters=500, tol=0.0, warm_start=0, check_every=0,
-                polish_iters=0, anchor_every=0, use_graph=0):
+                polish_iters=0, anchor_every=0, use_graph=0, ergodic=0):
     """Queues one solve; returns its ticket.  Step data: numpy float64 arrays.  use_graph=1:
     the slot runs the solve's iteration chunks as CUDA graphs (captured once per factor,
-    chunk and settings)."""
+    chunk and settings).  ergodic=1: keep the ergodic average (smpc_poll's ubar, xbar)."""
     k = _Keep()
     D = smpc_step_data(k(p), k(q), k(dhat), k(eps), k(alpha2))
     O = smpc_solve_opts(int(max_iters), float(tol), int(warm_start), int(check_every), 0, int(polish_iters),
-                        int(anchor_every), int(use_graph))
+                        int(anchor_every), int(use_graph), int(ergodic))
     t = ctypes.c_uint64()
     _check(lib().smpc_submit(server, fac, ctypes.byref(D), ctypes.byref(O), ctypes.byref(t)), "smpc_submit")
     return t.value
 
 
-def smpc_poll(server, ticket, u=None, x=None, y=None, u0_host=None, history_host=None):
+def smpc_poll(server, ticket, u=None, x=None, y=None, u0_host=None, history_host=None, ubar=None, xbar=None):
     """None while the ticket is queued or running; else the result dict (outputs copied)."""
     def dptr(t):
         return None if t is None else (t if isinstance(t, int) else t.data_ptr())
 
     R = smpc_result(dptr(u), dptr(x), dptr(y), None if u0_host is None else u0_host.ctypes.data_as(_dp),
-                    None if history_host is None else history_host.ctypes.data_as(_dp), -1, 0.0, 0.0, 0, 0.0, 0.0)
+                    None if history_host is None else history_host.ctypes.data_as(_dp), -1, 0.0, 0.0, 0, 0.0, 0.0,
+                    dptr(ubar), dptr(xbar))
     done = ctypes.c_int32()
     _check(lib().smpc_poll(server, ctypes.c_uint64(ticket), ctypes.byref(R), ctypes.byref(done)), "smpc_poll")
     if not done.value:
@@ -363,11 +366,13 @@ def smpc_batch_destroy(batch):
 
 
 def smpc_batch_solve(batch, steps, max_iters=500, tol=0.0, warm_start=0, check_every=0, sync=1, outputs=None,
-                     u0_host=None, stream=None, polish_iters=0, anchor_every=0, use_graph=0):
+                     u0_host=None, stream=None, polish_iters=0, anchor_every=0, use_graph=0, ergodic=0,
+                     bar_outputs=None):
     """steps: one dict (p, q, dhat, alpha2, eps) per factor of the batch (numpy float64 or int
     device addresses).  outputs: optional list of (u, x, y) device tensors per factor;
-    u0_host: optional list of numpy arrays (R * n_u per factor).  Returns one result dict per
-    factor."""
+    u0_host: optional list of numpy arrays (R * n_u per factor); with ergodic=1,
+    bar_outputs: optional list of (ubar, xbar) device tensors per factor.  Returns one
+    result dict per factor."""
     k = _Keep()
 
     def arg(a):
@@ -381,7 +386,7 @@ def smpc_batch_solve(batch, steps, max_iters=500, tol=0.0, warm_start=0, check_e
     D = (smpc_step_data * n)(*[smpc_step_data(arg(d["p"]), arg(d["q"]), arg(d["dhat"]), arg(d.get("eps")),
                                               arg(d["alpha2"])) for d in steps])
     O = smpc_solve_opts(int(max_iters), float(tol), int(warm_start), int(check_every), int(sync), int(polish_iters),
-                        int(anchor_every), int(use_graph))
+                        int(anchor_every), int(use_graph), int(ergodic))
 
     def dptr(t):
         return None if t is None else (t if isinstance(t, int) else t.data_ptr())
@@ -389,8 +394,9 @@ def smpc_batch_solve(batch, steps, max_iters=500, tol=0.0, warm_start=0, check_e
     R = (smpc_result * n)()
     for i in range(n):
         u, x, y = outputs[i] if outputs else (None, None, None)
+        ub, xb = bar_outputs[i] if bar_outputs else (None, None)
         R[i] = smpc_result(dptr(u), dptr(x), dptr(y), None if u0_host is None else u0_host[i].ctypes.data_as(_dp),
-                           None, -1, 0.0, 0.0, 0)
+                           None, -1, 0.0, 0.0, 0, 0.0, 0.0, dptr(ub), dptr(xb))
     s = None if stream is None else (stream if isinstance(stream, int) else stream.cuda_stream)
     _check(lib().smpc_batch_solve(batch, D, ctypes.byref(O), R, s), "smpc_batch_solve")
     return [{"iterations": r.iterations, "rho": r.rho, "rho_rel": r.rho_rel, "launches": r.launches} for r in R]

@@ -319,6 +319,8 @@ IterArgs make_args(const smpc_factor_t* f) {
   a.p0 = f->p0;
   a.gamma_d = f->gamma_d;
   a.cvec = f->cvec;
+  a.theta = f->theta;
+  a.xbar = a.ubar = nullptr;  // set by solves that keep the ergodic average
   a.res = f->res;
   a.counters = f->counters;
   a.flags = f->flags;
@@ -380,7 +382,9 @@ int ensure_capacity(smpc_factor_t* f, int iters) {
   double* cvec = nullptr;
   unsigned long long* res_tree = nullptr;
   TRY(f->alloc(&res, sizeof(unsigned long long) * 3 * (size_t)(cap + 2)));
+  double* theta = nullptr;
   TRY(f->alloc(&cvec, sizeof(double) * (size_t)(cap + 2)));
+  TRY(f->alloc(&theta, sizeof(double) * (size_t)(cap + 2)));
   if (f->R > 1) {  // forests: a residual per tree and iteration (each tree stops on its own)
     TRY(f->alloc(&res_tree, sizeof(unsigned long long) * 3 * (size_t)f->R * (size_t)(cap + 2)));
     CK(cudaMemset(res_tree, 0, sizeof(unsigned long long) * 3 * (size_t)f->R * (size_t)(cap + 2)));
@@ -389,23 +393,27 @@ int ensure_capacity(smpc_factor_t* f, int iters) {
   f->res = res;
   f->res_tree = res_tree;
   f->cvec = cvec;
+  f->theta = theta;
   f->cap = cap;
   f->cvec_for = -1;
   return SMPC_OK;
 }
 
-// c_nu = theta_nu (1/theta_{nu-1} - 1) with theta_0 = theta_{-1} = 1 (eq. optim:theta:update)
+// c_nu = theta_nu (1/theta_{nu-1} - 1) with theta_0 = theta_{-1} = 1 (eq. optim:theta:update),
+// and theta_nu itself (the weights of the ergodic average, Sec. IV-A)
 int upload_cvec(smpc_factor_t* f, int iters) {
   if (f->cvec_for >= iters) return SMPC_OK;
-  std::vector<double> c(iters + 2);
+  std::vector<double> c(iters + 2), th(iters + 2);
   double tp = 1.0, t = 1.0;
   for (int nu = 0; nu < iters + 2; ++nu) {
     c[nu] = t * (1.0 / tp - 1.0);
+    th[nu] = t;
     const double tn = 0.5 * (std::sqrt(t * t * t * t + 4.0 * t * t) - t * t);
     tp = t;
     t = tn;
   }
   CK(cudaMemcpy(f->cvec, c.data(), sizeof(double) * c.size(), cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(f->theta, th.data(), sizeof(double) * th.size(), cudaMemcpyHostToDevice));
   f->cvec_for = iters;
   return SMPC_OK;
 }
@@ -664,7 +672,7 @@ int chunk_mode(int nu) { return MODE_BWD | MODE_CHECK | (nu > 0 ? MODE_PROX : 0)
 // factor's capture stream the first time this key is seen, then launched on s.  A
 // capture or instantiation that fails turns graphs off for the factor and launches
 // the chunk directly (the same kernels with the same arguments).
-int launch_chunk_graph(smpc_factor_t* f, IterPlan& plan, int from, int to, const std::array<long long, 6>& key,
+int launch_chunk_graph(smpc_factor_t* f, IterPlan& plan, int from, int to, const std::array<long long, 7>& key,
                        cudaStream_t s) {
   auto it = f->graphs.find(key);
   if (it == f->graphs.end()) {
@@ -1154,6 +1162,12 @@ int solve_begin(smpc_factor_t* f, const smpc_step_data* data, const smpc_solve_o
   // refused for its options leaves the factor's duals as they were
   IterArgs a = make_args(f);
   a.tol = opts->tol;
+  if (opts->ergodic) {
+    if (!f->xbar) TRY(f->alloc(&f->xbar, (size_t)n * n_x * f->vs));
+    if (!f->ubar) TRY(f->alloc(&f->ubar, (size_t)n * n_u * f->vs));
+    a.xbar = f->xbar;
+    a.ubar = f->ubar;
+  }
   IterPlan& plan = *plan_out;
   TRY(plan_iters(f, a, *opts, &plan));
   // step data -> device (Alg. 2 steps 1-2)
@@ -1216,6 +1230,8 @@ int solve_end(smpc_factor_t* f, IterPlan& plan, const IterArgs& a, int launched,
   TRY(launch_copy_final_y(f->prec, a, launched, res->y, s));
   if (res->u) CK(cudaMemcpyAsync(res->u, f->uout, (size_t)n * n_u * f->vs, cudaMemcpyDefault, s));
   if (res->x) CK(cudaMemcpyAsync(res->x, f->xout, (size_t)n * n_x * f->vs, cudaMemcpyDefault, s));
+  if (res->ubar && a.ubar) CK(cudaMemcpyAsync(res->ubar, a.ubar, (size_t)n * n_u * f->vs, cudaMemcpyDefault, s));
+  if (res->xbar && a.xbar) CK(cudaMemcpyAsync(res->xbar, a.xbar, (size_t)n * n_x * f->vs, cudaMemcpyDefault, s));
   f->solved_once = true;
   f->last_static = false;
   f->last_stream = s;
@@ -1249,7 +1265,7 @@ int smpc_solve(smpc_factor_t* f, const smpc_step_data* data, const smpc_solve_op
     const int upto = std::min(iters, launched + chunk);
     if (graphs && !f->graphs_off) {
       TRY(launch_chunk_graph(f, plan, launched, upto, {launched, upto, iters, tol_bits, opts->polish_iters,
-                                                       opts->anchor_every}, s));
+                                                       opts->anchor_every, opts->ergodic ? 1 : 0}, s));
     } else {
       for (int nu = launched; nu < upto; ++nu) TRY(launch_planned(plan, nu, chunk_mode(nu), s));
     }

@@ -50,8 +50,8 @@ struct smpc_batch {
     cudaGraphExec_t exec = nullptr;
     std::vector<int> kernels;  // per factor
   };
-  // key: {first iteration, end, max_iters, tol bits, polish_iters, anchor_every}
-  std::map<std::array<long long, 6>, Graph> graphs;
+  // key: {first iteration, end, max_iters, tol bits, polish_iters, anchor_every, ergodic}
+  std::map<std::array<long long, 7>, Graph> graphs;
   std::vector<const void*> bufs;  // the factors' iteration buffers the graphs were captured with
   bool graphs_off = false;
 
@@ -83,7 +83,7 @@ struct smpc_batch {
   }
 
   // one chunk as one graph launch (captured the first time this key is seen)
-  int launch_chunk(std::vector<IterPlan>& plan, int from, int to, const std::array<long long, 6>& key,
+  int launch_chunk(std::vector<IterPlan>& plan, int from, int to, const std::array<long long, 7>& key,
                    cudaStream_t s) {
     auto it = graphs.find(key);
     if (it == graphs.end()) {
@@ -197,7 +197,7 @@ int smpc_batch_solve(smpc_batch* b, const smpc_step_data* data, const smpc_solve
     const int upto = std::min(iters, launched + chunk);
     if (graphs && !b->graphs_off)
       BTRY(b->launch_chunk(plan, launched, upto, {launched, upto, iters, tol_bits, opts->polish_iters,
-                                                  opts->anchor_every}, s));
+                                                  opts->anchor_every, opts->ergodic ? 1 : 0}, s));
     else
       BTRY(b->enqueue(plan, launched, upto, s));
     launched = upto;

@@ -548,6 +548,17 @@ struct Kern {
   __device__ VT* hb() const { return reinterpret_cast<VT*>(a.h); }
   __device__ const VT* cv(const void* p) const { return reinterpret_cast<const VT*>(p); }
   __device__ VT* mv(void* p) const { return reinterpret_cast<VT*>(p); }
+  // Ergodic primal average (Sec. IV-A): zbar^it = (1 - theta_it) zbar^{it-1} + theta_it z^it,
+  // zbar^0 = z^0 (theta_0 = 1; the previous contents are not read then).
+  __device__ void ergodic_put(void* buf, long long idx, AT z, int it) const {
+    VT* p = mv(buf) + idx;
+    if (it == 0) {
+      *p = (VT)z;
+    } else {
+      const AT th = (AT)a.theta[it];
+      *p = (VT)(((AT)1 - th) * (AT)*p + th * z);
+    }
+  }
   __device__ const MT* pack(int n) const {
     return reinterpret_cast<const MT*>(a.packs) + (long long)n * a.pack_stride;
   }
@@ -929,6 +940,7 @@ struct Kern {
               y2[e] = ysn;
               y2[a.n_x + e] = yzn;
               put_w(m, e, st_add(st_extrap(ysn, v1[r], cn), st_extrap(yzn, w1[r], cn)));
+              if (a.xbar) ergodic_put(a.xbar, (long long)m * a.n_x + e, x, it);
               rm = fmax(rm, fmax(fabs(es), fabs(ez)));
               hm = fmax(hm, fabs(x));
               tm = fmax(tm, fmax(fabs(x - es), fabs(x - ez)));
@@ -939,6 +951,7 @@ struct Kern {
               const AT ep = (AT)st_val(st_sub(ypn, wp)) * i1[r];
               y2[2 * a.n_x + i] = ypn;
               put_w(m, e, st_extrap(ypn, v1[r], cn));
+              if (a.ubar) ergodic_put(a.ubar, (long long)m * a.n_u + i, x, it);
               rm = fmax(rm, fabs(ep));
               hm = fmax(hm, fabs(x));
               tm = fmax(tm, fabs(x - ep));
@@ -1201,6 +1214,7 @@ struct Kern {
         y2[e] = ysn;
         y2[n_x + e] = yzn;
         put_w_at(mk + e, st_add(st_extrap(ysn, v1, cn), st_extrap(yzn, w1, cn)), wa_e);
+        if (a.xbar) ergodic_put(a.xbar, (long long)m * n_x + e, x, it);
         rm = fmax(rm, fmax(fabs(es), fabs(ez)));
         hm = fmax(hm, fabs(x));
         tm = fmax(tm, fmax(fabs(x - es), fabs(x - ez)));
@@ -1216,6 +1230,7 @@ struct Kern {
         const AT ep = (AT)st_val(st_sub(ypn, wp)) * (AT)IP[i];
         y2[2 * n_x + i] = ypn;
         put_w_at(mk + e, st_extrap(ypn, p1, cn), wa_e);
+        if (a.ubar) ergodic_put(a.ubar, (long long)m * n_u + i, u, it);
         rm = fmax(rm, fabs(ep));
         hm = fmax(hm, fabs(u));
         tm = fmax(tm, fabs(u - ep));

@@ -127,6 +127,10 @@ extern "C" int smpc_solve_static(smpc_factor_t* f, const smpc_step_data* data, c
     set_error("max_iters must be >= 1 and tol >= 0");
     return SMPC_EINVAL;
   }
+  if (opts->ergodic) {
+    set_error("smpc_solve_static does not keep the ergodic average (use smpc_solve)");
+    return SMPC_EINVAL;
+  }
   const int n = f->n, N = f->N, n_x = f->n_x, n_u = f->n_u, n_d = f->n_d;
   const int iters = opts->max_iters;
   const Layout L = layout(f, iters);

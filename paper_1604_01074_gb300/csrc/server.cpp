@@ -294,6 +294,12 @@ int smpc_poll(smpc_server* sv, uint64_t ticket, smpc_result* res, int32_t* done)
     if (res->u && cudaMemcpy(res->u, f->uout, (size_t)f->n * f->n_u * vs, cudaMemcpyDefault) != cudaSuccess) rc = SMPC_ECUDA;
     if (res->x && cudaMemcpy(res->x, f->xout, (size_t)f->n * f->n_x * vs, cudaMemcpyDefault) != cudaSuccess) rc = SMPC_ECUDA;
     if (res->y && rc == SMPC_OK) rc = copy_final_y(f, res->y);
+    if (r->opts.ergodic && f->ubar && res->ubar &&
+        cudaMemcpy(res->ubar, f->ubar, (size_t)f->n * f->n_u * vs, cudaMemcpyDefault) != cudaSuccess)
+      rc = SMPC_ECUDA;
+    if (r->opts.ergodic && f->xbar && res->xbar &&
+        cudaMemcpy(res->xbar, f->xbar, (size_t)f->n * f->n_x * vs, cudaMemcpyDefault) != cudaSuccess)
+      rc = SMPC_ECUDA;
     if (rc == SMPC_ECUDA) set_error("copying the outputs of ticket %llu failed", (unsigned long long)ticket);
   }
   {

@@ -126,6 +126,9 @@ struct IterArgs {
   const void* p0;                // n_x measured state
   double gamma_d;
   const double* cvec;            // extrapolation coefficients c_nu, nu = 0..max_iters
+  const double* theta;           // theta_nu, nu = 0..max_iters (the ergodic average's weights)
+  void* xbar;                    // ergodic average of x (n x n_x), or NULL (not kept)
+  void* ubar;                    // ergodic average of u (n x n_u), or NULL
   unsigned long long* res;       // per iteration: rho, ||Hz||, ||t|| as float64 bits
   int* counters;                 // per node arrival counters (top nodes)
   int* flags;                    // [0] iterations done (-1 running), [1] error code
@@ -325,6 +328,8 @@ struct smpc_factor_t {
   unsigned long long* res_tree = nullptr;  // forests: cap x R x 3 per-tree residuals
   int* tree_done = nullptr;                // forests: R per-tree iteration counts (-1 running)
   double* cvec = nullptr;
+  double* theta = nullptr;    // theta_nu beside cvec (ergodic average)
+  void *xbar = nullptr, *ubar = nullptr;  // ergodic averages, allocated by the first solve that asks
   int cap = 0;                // iterations the res/cvec buffers hold
   int cvec_for = -1;
   cudaEvent_t ev[2] = {nullptr, nullptr};
@@ -342,12 +347,12 @@ struct smpc_factor_t {
   // flags live in the static scratch, not in res / flags, so smpc_solve_info refuses it
   bool last_static = false;
   // captured iteration chunks (use_graph): key {first iteration, end, max_iters, tol bits,
-  // polish_iters, anchor_every} -> executable graph and its kernel count
+  // polish_iters, anchor_every, ergodic} -> executable graph and its kernel count
   struct ChunkGraph {
     cudaGraphExec_t exec = nullptr;
     int kernels = 0;
   };
-  std::map<std::array<long long, 6>, ChunkGraph> graphs;
+  std::map<std::array<long long, 7>, ChunkGraph> graphs;
   cudaStream_t capture_stream = nullptr;  // graphs are captured here, launched on the solve's stream
   bool graphs_off = false;                // a capture failed: plain launches from then on
   void drop_graphs() {

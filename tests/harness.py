@@ -111,19 +111,28 @@ class Gpu:
         self.x = torch.zeros((self.n, self.n_x), dtype=dt, device=dev)
         self.y = torch.zeros((self.n, 2 * self.n_x + self.n_u), dtype=dt, device=dev)
 
-    def solve(self, iters, tol=0.0, warm=0, eps=True, check_every=0):
+    def solve(self, iters, tol=0.0, warm=0, eps=True, check_every=0, ergodic=0, use_graph=0):
+        """ergodic=1: the ergodic averages land in self.ubar, self.xbar."""
         P = self.P
         hist = np.zeros((iters, 3))
         u0 = np.zeros(self.smpc.smpc_tree_info_get(self.tree)["n_trees"] * self.n_u)
+        if ergodic:
+            self.ubar = self.torch.full_like(self.u, float("nan"))
+            self.xbar = self.torch.full_like(self.x, float("nan"))
         info = self.smpc.smpc_solve(self.fac, P["p"], P["q"], P["dhat"], P["alpha2"], eps=P["eps"] if eps else None,
                                     max_iters=iters, tol=tol, warm_start=warm, check_every=check_every, sync=1,
-                                    u=self.u, x=self.x, y=self.y, u0_host=u0, history_host=hist)
+                                    u=self.u, x=self.x, y=self.y, u0_host=u0, history_host=hist,
+                                    ergodic=ergodic, use_graph=use_graph,
+                                    ubar=self.ubar if ergodic else None, xbar=self.xbar if ergodic else None)
         info["history"] = hist[:max(info["iterations"], 0)]
         info["u0"] = u0
         return info
 
     def arrays(self):
         return self.u.double().cpu().numpy(), self.x.double().cpu().numpy(), self.y.double().cpu().numpy()
+
+    def bars(self):
+        return self.ubar.double().cpu().numpy(), self.xbar.double().cpu().numpy()
 
     def steps(self):
         return self.smpc.smpc_factor_steps(self.fac, self.n, self.n_u)

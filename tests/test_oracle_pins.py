@@ -336,6 +336,84 @@ def test_jacobi_lipschitz_bounds_step():
     assert st["lambda"] > 0
 
 
+def kkt_dual_hessian(P):
+    """The dual Hessian column by column from the dense KKT solve of the whole problem
+    (independent of Algorithm 1): column k is -(Hz(e_k) - Hz(0))."""
+    tree = P["tree"]
+    n, n_x, n_u = len(tree["parent"]), P["net"]["n_x"], P["net"]["n_u"]
+    blk = 2 * n_x + n_u
+    zero = (np.zeros((n, n_x)), np.zeros((n, n_x)), np.zeros((n, n_u)))
+    x0, u0 = dr.kkt_solve(P, zero)
+    M = np.zeros((n * blk, n * blk))
+    for k in range(n * blk):
+        w = np.zeros((n, blk))
+        w.flat[k] = 1.0
+        x1, u1 = dr.kkt_solve(P, (w[:, :n_x], w[:, n_x:2 * n_x], w[:, 2 * n_x:]))
+        M[:, k] = -np.concatenate([x1 - x0, x1 - x0, u1 - u0], axis=1).ravel()
+    return M
+
+
+@pytest.mark.parametrize("mk", INSTANCES)
+def test_jacobi_steps_from_the_hand_diagonal(mk):
+    """Sec. IV-D reading: one scalar 1/mean(diag) per distance block, 1/diag per input entry
+    (an entry of zero curvature takes the mean of its node's other entries), and
+    lambda = 1 / largest eigenvalue of the scaled dual Hessian.  The diagonal comes from
+    the hand derivation for A = I and the eigenvalue from the dense KKT Hessian."""
+    P = mk()
+    tree, fac, cu = build(P)
+    st = jacobi_steps(fac, tree)
+    dx, du = closed_form_diagonal(fac, tree)
+    d_s = 1.0 / dx.mean(axis=1)
+    live = du > 1e-12 * du.max(axis=1, keepdims=True)
+    d_p = np.empty_like(du)
+    for m in range(tree.n):
+        fill = du[m, live[m]].mean()
+        d_p[m] = 1.0 / np.where(live[m], du[m], fill)
+    assert relerr(st["d_s"], d_s) < 1e-12 and relerr(st["d_z"], d_s) < 1e-12
+    assert relerr(st["d_p"], d_p) < 1e-12
+    dvec = np.concatenate([np.repeat(d_s[:, None], fac.n_x, 1), np.repeat(d_s[:, None], fac.n_x, 1), d_p],
+                          axis=1).ravel()
+    M = kkt_dual_hessian(P)
+    sq = np.sqrt(dvec)
+    lam = 1.0 / np.linalg.eigvalsh(sq[:, None] * M * sq[None, :]).max()
+    assert abs(st["lambda"] - lam) < 1e-9 * lam
+    assert relerr(st["s"], lam * d_s) < 1e-9 and relerr(st["p"], lam * d_p) < 1e-9
+
+
+def test_ergodic_average_is_the_theta_weighted_mean():
+    """Sec. IV-A: zbar^nu = (1 - theta_nu) zbar^{nu-1} + theta_nu z^nu with theta_0 = 1.  Since
+    (1 - theta_nu) / theta_nu^2 = 1 / theta_{nu-1}^2, unrolling gives the closed form
+    zbar^nu = theta_nu^2 sum_k z^k / theta_k, a convex combination (the weights telescope to
+    one), so zbar also meets the dynamics and the coupling."""
+    P = synth.random_instance(2)
+    tree, fac, cu = build(P)
+    steps = jacobi_steps(fac, tree)
+    K = 12
+    xs, us = [], []
+    for k in range(1, K + 1):               # z^{k-1} is the last primal iterate of a k-iteration run
+        Rk = apg(fac, tree, cu, P["cost"], P["p"], steps, k)
+        xs.append(Rk.x)
+        us.append(Rk.u)
+    R = apg(fac, tree, cu, P["cost"], P["p"], steps, K)
+    th = 1.0
+    thetas = [th]
+    for _ in range(K - 1):
+        th = 0.5 * th * (np.sqrt(th * th + 4.0) - th)
+        thetas.append(th)
+    wts = np.array([thetas[-1] ** 2 / t for t in thetas])
+    assert abs(wts.sum() - 1.0) < 1e-12
+    xbar = sum(wk * xk for wk, xk in zip(wts, xs))
+    ubar = sum(wk * uk for wk, uk in zip(wts, us))
+    assert relerr(R.xbar, xbar) < 1e-12 and relerr(R.ubar, ubar) < 1e-12
+    assert relerr(R.xbar, xs[-1]) > 1e-6                     # the average is not the last iterate
+    net = P["net"]
+    d = dr.demands(P)
+    xpar = np.where(tree.parent[:, None] >= 0, R.xbar[np.maximum(tree.parent, 0)], P["p"][None, :])
+    dyn = R.xbar - xpar @ net["A"].T - R.ubar @ net["B"].T - d @ net["Gd"].T
+    assert np.abs(dyn).max() < 1e-11 * (1 + np.abs(R.xbar).max())
+    assert np.abs(R.ubar @ net["E"].T + d @ net["Ed"].T).max() < 1e-11 * (1 + np.abs(R.ubar).max())
+
+
 # ---------------------------------------------------------------- the pins notice planted mistakes
 # ---------------------------------------------------------------- dual rate (Sec. IV-A)
 def dual_value(P, y, mu_s):
