@@ -76,11 +76,6 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
       "l"(src), "r"(bytes), "r"(smem_u32(b))
       : "memory");
 }
-// Bulk prefetch of [src, src + bytes) into L2 (a hint: no completion to wait for); src
-// 16-byte aligned, bytes a multiple of 16.
-__device__ __forceinline__ void bulk_prefetch_l2(const void* src, uint32_t bytes) {
-  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
-}
 // One 4- or 8-byte element copied into shared memory by cp.async: the copies of a
 // thread are issued back to back without holding registers and complete at
 // cp_async_wait_all, after which the issuing thread sees them (others after a barrier).
@@ -336,6 +331,17 @@ __device__ __forceinline__ void ldx(const float* p, float (&o)[8]) {
   const float4 a = *reinterpret_cast<const float4*>(p);
   const float4 b = *reinterpret_cast<const float4*>(p + 4);
   o[0] = a.x; o[1] = a.y; o[2] = a.z; o[3] = a.w; o[4] = b.x; o[5] = b.y; o[6] = b.z; o[7] = b.w;
+}
+// V accumulation-type entries to a 16-byte aligned vector (one or two vector stores)
+__device__ __forceinline__ void st16(float* p, const float (&v)[4]) {
+  *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+}
+__device__ __forceinline__ void st16(double* p, const double (&v)[2]) {
+  *reinterpret_cast<double2*>(p) = make_double2(v[0], v[1]);
+}
+__device__ __forceinline__ void st16(float* p, const float (&v)[8]) {
+  *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+  *reinterpret_cast<float4*>(p + 4) = make_float4(v[4], v[5], v[6], v[7]);
 }
 
 // out[j] = sum_i A[i*ld + j] x[i] for j < C (A' x), A with R rows.  Thread
@@ -1668,17 +1674,6 @@ struct Bwd {
     if (threadIdx.x == 0) a.flags[1] = SMPC_ETIMEOUT;
     abort_ = true;
   }
-  // the next load's slot; on timeout the load stays counted as in flight for drain()
-  __device__ int wait() {
-    const int slot = use % S;
-    const bool ok = mbar_wait(&bar[slot], (use / S) & 1);
-    if (__syncthreads_or(!ok)) {
-      fail();
-      return slot;
-    }
-    ++use;
-    return slot;
-  }
   __device__ void drain() {
     for (; use < iss; ++use) mbar_wait(&bar[use % S], (use / S) & 1);
     __syncthreads();
@@ -1692,102 +1687,124 @@ struct Bwd {
   }
 
   // ---------------------------------------------------------- mat-vecs from shared memory
-  // out[j] = sum_i A[i ld + j] x[i], j < C (A' x): thread (g, p) accumulates columns
-  // g V .. g V + V - 1 over the p-th row slice; slices are added in a fixed order.
-  __device__ void mtv_t(const MT* A, int R, int C, const AT* x, AT* out) {
+  // Partial column sums of A' x (A with R rows): thread (g, p) accumulates columns
+  // g V .. g V + V - 1 over the p-th row slice and stores them with one vector store into
+  // part (slice p, row stride ld); node_step adds the slices in a fixed order.
+  __device__ void mtv_t_part(const MT* A, int R, const AT* x) {
     constexpr int V = Vec<MT>::V;
     const int t = threadIdx.x;
     const int G = ld / V;
     const int P = bwd_slices<MT>(a.n_v);
     const int rc = (R + P - 1) / P;
-    if (t < P * G) {
-      const int g = t % G, p = t / G;
-      const int i0 = p * rc, i1 = min(R, i0 + rc);
-      AT acc[V];
+    if (t >= P * G) return;
+    const int g = t % G, p = t / G;
+    const int i0 = p * rc, i1 = min(R, i0 + rc);
+    AT acc[V];
 #pragma unroll
-      for (int k = 0; k < V; ++k) acc[k] = 0;
-      const MT* col = A + g * V;
+    for (int k = 0; k < V; ++k) acc[k] = 0;
+    const MT* col = A + g * V;
 #pragma unroll 4
-      for (int i = i0; i < i1; ++i) {
-        AT av[V];
-        ld16(col + (long long)i * ld, av);
-        const AT xi = x[i];
+    for (int i = i0; i < i1; ++i) {
+      AT av[V];
+      ld16(col + (long long)i * ld, av);
+      const AT xi = x[i];
 #pragma unroll
-        for (int k = 0; k < V; ++k) acc[k] += av[k] * xi;
-      }
-      AT* dst = part + p * ld + g * V;
-#pragma unroll
-      for (int k = 0; k < V; ++k) dst[k] = acc[k];
+      for (int k = 0; k < V; ++k) acc[k] += av[k] * xi;
     }
-    __syncthreads();
-    for (int j = t; j < C; j += kBT) {
+    st16(part + p * ld + g * V, acc);
+  }
+  // put(i, A_i . x) for the rows i < R of A (row stride ld; x zero beyond its entries up
+  // to ld).  Warp w takes rows 8 (w + 16 b) .. + 7, b = 0, 1, ...: lane l has row
+  // 8 (w + 16 b) + (l & 7) and the quarter q = l >> 3 of its 16-byte groups (q, q + 4, ...),
+  // so the eight lanes of a load phase read eight different rows (no bank conflicts) and
+  // the same piece of x (a broadcast); the quarters are added by two shuffles.
+  template <typename F>
+  __device__ void mv_rows(const MT* A, int R, const AT* x, F&& put) {
+    constexpr int V = Vec<MT>::V;
+    const int G = ld / V;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int q = lane >> 3;
+    for (int i0 = 8 * warp; i0 < R; i0 += 8 * (kBT / 32)) {  // warp-uniform
+      const int i = i0 + (lane & 7);
+      AT acc0 = 0, acc1 = 0;
+      if (i < R) {
+        const MT* row = A + (long long)i * ld;
+#pragma unroll 2
+        for (int g = q; g < G; g += 4) {
+          AT av[V], xv[V];
+          ld16(row + g * V, av);
+          ldx(x + g * V, xv);
+#pragma unroll
+          for (int k = 0; k < V; k += 2) {
+            acc0 += av[k] * xv[k];
+            acc1 += av[k + 1] * xv[k + 1];
+          }
+        }
+      }
+      AT v = acc0 + acc1;
+      v += __shfl_xor_sync(0xffffffffu, v, 8);
+      v += __shfl_xor_sync(0xffffffffu, v, 16);
+      if (i < R && q == 0) put(i, v);
+    }
+  }
+
+  // ---------------------------------------------------------- one node's backward step
+  // On entry yv holds [s; psi] of node m (visible to every thread) and thread j < n_v holds
+  // r_j (the children's r and beta) in rreg.  Four block barriers:
+  //   P1 partial column sums of g = [Bbar; L]' [s; psi]     | B1
+  //   P2 r = rreg + g (thread j); yv <- the next chain node's [s; psi] (when has_next), and
+  //      rreg += its beta after r is published              | B2
+  //   P3 delta = Lambda r (row dots; Lambda is symmetric)    | B3
+  //   P4 h = [Bbar; L] delta to global memory                | B4, then the slot is refilled.
+  // The slot's arrival is awaited by each thread before P1; a timeout is agreed on at B1.
+  __device__ void node_step(int m, AT& rreg, AT& sreg, bool has_next, AT wnext, AT bnext, bool refill) {
+    const int t = threadIdx.x;
+    const int slot = use % S;
+    const bool ok = mbar_wait(&bar[slot], (use / S) & 1);
+    mtv_t_part(K(slot), a.n_k, yv);
+    if (__syncthreads_or(!ok)) {  // B1
+      fail();
+      return;
+    }
+    ++use;
+    if (t < a.n_v) {
+      const int P = bwd_slices<MT>(a.n_v);
       AT v[20];
 #pragma unroll
-      for (int p = 0; p < 20; ++p) v[p] = p < P ? part[p * ld + j] : (AT)0;
+      for (int p = 0; p < 20; ++p) v[p] = p < P ? part[p * ld + t] : (AT)0;
       AT s0 = 0, s1 = 0;
 #pragma unroll
       for (int p = 0; p < 20; p += 2) {  // fixed order: deterministic
         s0 += v[p];
         s1 += v[p + 1];
       }
-      out[j] = s0 + s1;
-    }
-    __syncthreads();
-  }
-  // h of node m = A dv (R = n_k rows): two threads per row, each half of the columns,
-  // combined by a shuffle; written to global memory (anchor launches: to h_a, h = 0).
-  __device__ void mtv_n_out(const MT* A, int m) {
-    constexpr int V = Vec<MT>::V;
-    const int G = ld / V, Gh = (G + 1) / 2;
-    const int t = threadIdx.x, i = t >> 1, half = t & 1;
-    AT acc0 = 0, acc1 = 0;
-    if (i < a.n_k) {
-      const MT* row = A + (long long)i * ld;
-      const int g1 = min(G, (half + 1) * Gh);
-#pragma unroll 4
-      for (int g = half * Gh; g < g1; ++g) {
-        AT av[V], xv[V];
-        ld16(row + g * V, av);
-        ldx(dv + g * V, xv);
-#pragma unroll
-        for (int k = 0; k < V; k += 2) {
-          acc0 += av[k] * xv[k];
-          acc1 += av[k + 1] * xv[k + 1];
-        }
-      }
-    }
-    AT v = acc0 + acc1;
-    v += __shfl_xor_sync(0xffffffffu, v, 1);
-    if (i < a.n_k && half == 0) {
-      const long long q = (long long)m * a.n_k + i;
-      if (mode & MODE_ANCHOR) {  // h_a = h(w_a); the part on w - w_a starts at zero
-        mv(a.ha)[q] = (VT)v;
-        mv(a.h)[q] = (VT)0;
-      } else {
-        mv(a.h)[q] = (VT)v;
-      }
-    }
-    __syncthreads();
-  }
-
-  // ---------------------------------------------------------- one node's backward step
-  // yv holds [s; psi]; thread j < n_v holds r_j (children and beta) in rreg.
-  __device__ void node(int m, AT& rreg, bool refill) {
-    const int t = threadIdx.x;
-    const int slot = wait();
-    if (abort_) return;
-    mtv_t(K(slot), a.n_k, a.n_v, yv, gv);
-    if (t < a.n_v) {
-      rreg += gv[t];
+      rreg += s0 + s1;
       rv[t] = rreg;
+      if (has_next) rreg += bnext;
     }
-    __syncthreads();
-    mtv_t(Lm(slot), a.n_v, a.n_v, rv, dv);  // Lambda is symmetric
-    if (a.pscale) {  // shared pack: delta = (Lambda r) / (2 p_n)
-      if (t < a.n_v) dv[t] *= (AT)cv(a.pscale)[m];
-      __syncthreads();
+    if (has_next) {
+      if (t < a.n_x) {
+        sreg += wnext;
+        yv[t] = sreg;
+      } else if (t < a.n_k) {
+        yv[t] = wnext;
+      }
     }
-    mtv_n_out(K(slot), m);
+    __syncthreads();  // B2
+    const AT sc = a.pscale ? (AT)cv(a.pscale)[m] : (AT)1;  // shared pack: delta = (Lambda r) / (2 p_n)
+    mv_rows(Lm(slot), a.n_v, rv, [&](int i, AT v) { dv[i] = v * sc; });
+    __syncthreads();  // B3
+    const long long q0 = (long long)m * a.n_k;
+    const bool anchor = (mode & MODE_ANCHOR) != 0;
+    mv_rows(K(slot), a.n_k, dv, [&](int i, AT v) {
+      if (anchor) {  // h_a = h(w_a); the part on w - w_a starts at zero
+        mv(a.ha)[q0 + i] = (VT)v;
+        mv(a.h)[q0 + i] = (VT)0;
+      } else {
+        mv(a.h)[q0 + i] = (VT)v;
+      }
+    });
+    __syncthreads();  // B4: the slot's reads are done
     if (refill) issue();
   }
 
@@ -1799,34 +1816,33 @@ struct Bwd {
     // the chain's node ids into shared memory: per node only shared-memory reads lead to
     // the next node's vector loads
     const int* nodes = gnodes;
+    __syncthreads();  // the previous node step's reads of yv and the previous chain's ids are done
     if (len <= kChainIds) {
-      __syncthreads();  // the previous chain's ids are no longer read
       for (int q = e; q < len; q += kBT) cids[q] = gnodes[q];
-      __syncthreads();
       nodes = cids;
     }
-    int m = nodes[len - 1];
-    AT wcur = e < a.n_k ? (AT)wb[(long long)m * a.n_k + e] : (AT)0;
-    AT bcur = (e < a.n_v && !lin) ? (AT)cv(a.beta)[(long long)m * a.n_v + e] : (AT)0;
+    {  // the bottom node's [s; psi] and beta
+      const int m = gnodes[len - 1];
+      const AT w = e < a.n_k ? (AT)wb[(long long)m * a.n_k + e] : (AT)0;
+      if (e < a.n_x) {
+        sreg = w;
+        yv[e] = w;
+      } else if (e < a.n_k) {
+        yv[e] = w;
+      }
+      if (e < a.n_v && !lin) rreg = (AT)cv(a.beta)[(long long)m * a.n_v + e];
+    }
+    __syncthreads();
     for (int k = len - 1; k >= 0; --k) {
-      m = nodes[k];
+      const int m = nodes[k];
       AT wnext = 0, bnext = 0;
       if (k > 0) {  // the next node's vectors into registers while this node runs
         const int mn = nodes[k - 1];
         if (e < a.n_k) wnext = (AT)wb[(long long)mn * a.n_k + e];
         if (e < a.n_v && !lin) bnext = (AT)cv(a.beta)[(long long)mn * a.n_v + e];
       }
-      if (e < a.n_x) {
-        sreg += wcur;
-        yv[e] = sreg;
-      } else if (e < a.n_k) {
-        yv[e] = wcur;
-      }
-      rreg += bcur;
-      node(m, rreg, true);
+      node_step(m, rreg, sreg, k > 0, wnext, bnext, true);
       if (abort_) return;
-      wcur = wnext;
-      bcur = bnext;
     }
     const int head = nodes[0];
     if (e < a.n_x) mv(a.spub)[(long long)head * a.n_x + e] = (VT)sreg;
@@ -1873,7 +1889,8 @@ struct Bwd {
         rreg = lin ? (AT)0 : (AT)cv(a.beta)[(long long)t * a.n_v + e];
         for (int c = cb; c < cb + cc; ++c) rreg += (AT)ldcg(cv(a.rpub) + (long long)c * a.n_v + e);
       }
-      node(t, rreg, false);
+      __syncthreads();  // yv is complete
+      node_step(t, rreg, sreg, false, (AT)0, (AT)0, false);
       if (abort_) return;
       if (e < a.n_x) mv(a.spub)[(long long)t * a.n_x + e] = (VT)sreg;
       if (e < a.n_v) mv(a.rpub)[(long long)t * a.n_v + e] = (VT)rreg;
@@ -1885,7 +1902,7 @@ struct Bwd {
 
   __device__ void run() {
     const int tid = threadIdx.x;
-    for (int j = a.n_v + tid; j < ld; j += kBT) dv[j] = 0;
+    for (int j = a.n_v + tid; j < ld; j += kBT) dv[j] = rv[j] = 0;  // the row dots read x up to ld
     if (tid == 0) {
       for (int q = 0; q < S; ++q) mbar_init(&bar[q], 1);
       fence_barrier_init();
