@@ -1569,7 +1569,6 @@ __host__ __device__ inline int bwd_slices(int n_v) {
   return P > 20 ? 20 : P;
 }
 
-constexpr int kChainIds = 64;  // chain node ids kept in shared memory (longer chains: global)
 
 template <typename MT>
 __host__ __device__ inline size_t bwd_smem_bytes(int S, int n_x, int n_u, int n_v) {
@@ -1579,7 +1578,7 @@ __host__ __device__ inline size_t bwd_smem_bytes(int S, int n_x, int n_u, int n_
   m = round_up(m, 16) + 4 * sizeof(uint64_t);
   m = round_up(m, 16);
   m += ((size_t)3 * ld + round_up(n_k, 4) + (size_t)bwd_slices<MT>(n_v) * ld) * sizeof(AT);
-  m = round_up(m, 16) + (16 + kChainIds) * sizeof(int);
+  m = round_up(m, 16) + 16 * sizeof(int);
   return round_up(m, 128);
 }
 
@@ -1600,8 +1599,8 @@ struct Bwd {
     int chain, k, off;
   } cur;
   int cnode = -1;             // thread 0: the node id at cur
-  int* cids;                  // the current chain's node ids (kChainIds at most), top-down
   bool abort_ = false;
+  bool pending_ = false;  // the previous node's slot is to be refilled at the next B1
 
   __device__ Bwd(const IterArgs& args, unsigned char* smem, int S_, int nu_, int mode_)
       : a(args), S(S_), nu(nu_), mode(mode_), base(smem) {
@@ -1624,7 +1623,6 @@ struct Bwd {
     v += bwd_slices<MT>(a.n_v) * ld;
     off = round_up(reinterpret_cast<unsigned char*>(v) - base, 16);
     flag = reinterpret_cast<int*>(base + off);
-    cids = flag + 16;
   }
   __device__ MT* K(int s) const { return reinterpret_cast<MT*>(base + (size_t)s * (kbytes + lbytes)); }
   __device__ MT* Lm(int s) const { return reinterpret_cast<MT*>(base + (size_t)s * (kbytes + lbytes) + kbytes); }
@@ -1714,49 +1712,71 @@ struct Bwd {
     st16(part + p * ld + g * V, acc);
   }
   // put(i, A_i . x) for the rows i < R of A (row stride ld; x zero beyond its entries up
-  // to ld).  Warp w takes rows 8 (w + 16 b) .. + 7, b = 0, 1, ...: lane l has row
-  // 8 (w + 16 b) + (l & 7) and the quarter q = l >> 3 of its 16-byte groups (q, q + 4, ...),
-  // so the eight lanes of a load phase read eight different rows (no bank conflicts) and
-  // the same piece of x (a broadcast); the quarters are added by two shuffles.
-  template <typename F>
+  // to ld), Q lanes per row (Q = 2 or 4) and NR rows per lane (1 or 2).  A warp takes
+  // NR * 32 / Q consecutive rows per pass: lane l has rows r, r + 32 / Q, ... of them,
+  // r = l mod 32/Q, and the part q = l div (32/Q) of their 16-byte groups (q, q + Q, ...).
+  // The eight lanes of a load phase read eight different rows (no bank conflicts) and the
+  // same piece of x (a broadcast), which serves all NR rows of the lane; the Q parts are
+  // added by shuffles in a fixed order.
+  template <int Q, int NR, typename F>
   __device__ void mv_rows(const MT* A, int R, const AT* x, F&& put) {
-    constexpr int V = Vec<MT>::V;
+    constexpr int V = Vec<MT>::V, RW = 32 / Q;
     const int G = ld / V;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int q = lane >> 3;
-    for (int i0 = 8 * warp; i0 < R; i0 += 8 * (kBT / 32)) {  // warp-uniform
-      const int i = i0 + (lane & 7);
-      AT acc0 = 0, acc1 = 0;
+    const int q = lane / RW;
+    for (int i0 = NR * RW * warp; i0 < R; i0 += NR * RW * (kBT / 32)) {  // warp-uniform
+      const int i = i0 + lane % RW;
+      AT acc[NR][2];
+      const MT* row[NR];
+#pragma unroll
+      for (int n = 0; n < NR; ++n) {
+        acc[n][0] = acc[n][1] = 0;
+        const int in = i + n * RW;
+        row[n] = A + (long long)(in < R ? in : i) * ld;
+      }
       if (i < R) {
-        const MT* row = A + (long long)i * ld;
 #pragma unroll 2
-        for (int g = q; g < G; g += 4) {
-          AT av[V], xv[V];
-          ld16(row + g * V, av);
+        for (int g = q; g < G; g += Q) {
+          AT xv[V];
           ldx(x + g * V, xv);
 #pragma unroll
-          for (int k = 0; k < V; k += 2) {
-            acc0 += av[k] * xv[k];
-            acc1 += av[k + 1] * xv[k + 1];
+          for (int n = 0; n < NR; ++n) {
+            AT av[V];
+            ld16(row[n] + g * V, av);
+#pragma unroll
+            for (int k = 0; k < V; k += 2) {
+              acc[n][0] += av[k] * xv[k];
+              acc[n][1] += av[k + 1] * xv[k + 1];
+            }
           }
         }
       }
-      AT v = acc0 + acc1;
-      v += __shfl_xor_sync(0xffffffffu, v, 8);
-      v += __shfl_xor_sync(0xffffffffu, v, 16);
-      if (i < R && q == 0) put(i, v);
+#pragma unroll
+      for (int n = 0; n < NR; ++n) {
+        AT v = acc[n][0] + acc[n][1];
+#pragma unroll
+        for (int d = RW; d < 32; d *= 2) v += __shfl_xor_sync(0xffffffffu, v, d);
+        const int in = i + n * RW;
+        if (q == 0 && in < R) put(in, v);
+      }
     }
   }
+  // rows per lane of the row dots: two where a matrix entry is four or eight bytes (the
+  // vector loads are then shared), one for bfloat16 (whose row dots are shorter)
+  static constexpr int kNR = sizeof(MT) >= 4 ? 2 : 1;
 
   // ---------------------------------------------------------- one node's backward step
   // On entry yv holds [s; psi] of node m (visible to every thread) and thread j < n_v holds
-  // r_j (the children's r and beta) in rreg.  Four block barriers:
-  //   P1 partial column sums of g = [Bbar; L]' [s; psi]     | B1
+  // r_j (the children's r and beta) in rreg.  Three block barriers:
+  //   P1 partial column sums of g = [Bbar; L]' [s; psi]     | B1 (then the previous node's
+  //                                                          |    slot is refilled)
   //   P2 r = rreg + g (thread j); yv <- the next chain node's [s; psi] (when has_next), and
   //      rreg += its beta after r is published              | B2
   //   P3 delta = Lambda r (row dots; Lambda is symmetric)    | B3
-  //   P4 h = [Bbar; L] delta to global memory                | B4, then the slot is refilled.
+  //   P4 h = [Bbar; L] delta to global memory.
   // The slot's arrival is awaited by each thread before P1; a timeout is agreed on at B1.
+  // With refill, this node's slot is refilled at the next node's B1, or by the caller
+  // (at once behind a fourth barrier when there is one slot).
   __device__ void node_step(int m, AT& rreg, AT& sreg, bool has_next, AT wnext, AT bnext, bool refill) {
     const int t = threadIdx.x;
     const int slot = use % S;
@@ -1767,6 +1787,10 @@ struct Bwd {
       return;
     }
     ++use;
+    if (pending_) {  // the previous node's slot: its last reads (P4) ended before B1
+      issue();
+      pending_ = false;
+    }
     if (t < a.n_v) {
       const int P = bwd_slices<MT>(a.n_v);
       AT v[20];
@@ -1792,11 +1816,11 @@ struct Bwd {
     }
     __syncthreads();  // B2
     const AT sc = a.pscale ? (AT)cv(a.pscale)[m] : (AT)1;  // shared pack: delta = (Lambda r) / (2 p_n)
-    mv_rows(Lm(slot), a.n_v, rv, [&](int i, AT v) { dv[i] = v * sc; });
+    mv_rows<4, kNR>(Lm(slot), a.n_v, rv, [&](int i, AT v) { dv[i] = v * sc; });
     __syncthreads();  // B3
     const long long q0 = (long long)m * a.n_k;
     const bool anchor = (mode & MODE_ANCHOR) != 0;
-    mv_rows(K(slot), a.n_k, dv, [&](int i, AT v) {
+    mv_rows<kNR == 2 ? 4 : 2, kNR>(K(slot), a.n_k, dv, [&](int i, AT v) {
       if (anchor) {  // h_a = h(w_a); the part on w - w_a starts at zero
         mv(a.ha)[q0 + i] = (VT)v;
         mv(a.h)[q0 + i] = (VT)0;
@@ -1804,47 +1828,70 @@ struct Bwd {
         mv(a.h)[q0 + i] = (VT)v;
       }
     });
-    __syncthreads();  // B4: the slot's reads are done
-    if (refill) issue();
+    if (refill && S == 1) {  // one slot: the next node needs it, refill now
+      __syncthreads();
+      issue();
+    } else {
+      pending_ = refill;  // the slot is refilled at the next node's B1 (or at the chain's end)
+    }
   }
 
-  __device__ void chain(const int* gnodes, int len) {
-    const int e = threadIdx.x;
-    AT sreg = 0, rreg = 0;
-    const bool lin = no_affine();
-    const VT* wb = cv(a.wbuf);
-    // the chain's node ids into shared memory: per node only shared-memory reads lead to
-    // the next node's vector loads
-    const int* nodes = gnodes;
-    __syncthreads();  // the previous node step's reads of yv and the previous chain's ids are done
-    if (len <= kChainIds) {
-      for (int q = e; q < len; q += kBT) cids[q] = gnodes[q];
-      nodes = cids;
+  // The ids a chain starts with (offset, length, bottom node, the node above it),
+  // loaded one chain ahead so that no chain start waits for dependent global loads.
+  struct ChainIds {
+    int cb, len, m0, m1;
+  };
+  __device__ ChainIds chain_ids(int ch) const {
+    ChainIds c{0, 0, -1, -1};
+    if (ch < a.n_chains) {
+      c.cb = a.chain_off[ch];
+      c.len = a.chain_off[ch + 1] - c.cb;
+      c.m0 = a.chain_node[c.cb + c.len - 1];
+      c.m1 = c.len > 1 ? a.chain_node[c.cb + c.len - 2] : -1;
     }
-    {  // the bottom node's [s; psi] and beta
-      const int m = gnodes[len - 1];
-      const AT w = e < a.n_k ? (AT)wb[(long long)m * a.n_k + e] : (AT)0;
-      if (e < a.n_x) {
-        sreg = w;
-        yv[e] = w;
-      } else if (e < a.n_k) {
-        yv[e] = w;
-      }
-      if (e < a.n_v && !lin) rreg = (AT)cv(a.beta)[(long long)m * a.n_v + e];
+    return c;
+  }
+  // w and beta entries of thread e for node m (beta zero for the linear modes)
+  __device__ void node_vectors(int m, AT& w, AT& b) const {
+    const int e = threadIdx.x;
+    w = e < a.n_k ? (AT)cv(a.wbuf)[(long long)m * a.n_k + e] : (AT)0;
+    b = (e < a.n_v && !no_affine()) ? (AT)cv(a.beta)[(long long)m * a.n_v + e] : (AT)0;
+  }
+
+  // Chain c bottom-up.  wpre, bpre: on entry the bottom node's w and beta entries; on
+  // return those of the next chain's bottom node nx.m0 (loaded during the last node).
+  // Node ids are loaded two nodes ahead and each node's vectors one node ahead.
+  __device__ void chain(const ChainIds& c, const ChainIds& nx, AT& wpre, AT& bpre) {
+    const int e = threadIdx.x;
+    const int* gn = a.chain_node + c.cb;
+    AT sreg = 0, rreg = bpre;
+    __syncthreads();  // the previous node step's reads of yv are done
+    if (e < a.n_x) {
+      sreg = wpre;
+      yv[e] = wpre;
+    } else if (e < a.n_k) {
+      yv[e] = wpre;
     }
     __syncthreads();
-    for (int k = len - 1; k >= 0; --k) {
-      const int m = nodes[k];
+    int m = c.m0, m1 = c.m1, head = c.m0;
+    for (int k = c.len - 1; k >= 0; --k) {
+      const int m2 = k >= 2 ? gn[k - 2] : -1;
       AT wnext = 0, bnext = 0;
-      if (k > 0) {  // the next node's vectors into registers while this node runs
-        const int mn = nodes[k - 1];
-        if (e < a.n_k) wnext = (AT)wb[(long long)mn * a.n_k + e];
-        if (e < a.n_v && !lin) bnext = (AT)cv(a.beta)[(long long)mn * a.n_v + e];
-      }
+      if (k > 0)
+        node_vectors(m1, wnext, bnext);  // the next node's, while this node runs
+      else if (nx.m0 >= 0)
+        node_vectors(nx.m0, wpre, bpre);  // the next chain's bottom node
+      head = m;
       node_step(m, rreg, sreg, k > 0, wnext, bnext, true);
       if (abort_) return;
+      m = m1;
+      m1 = m2;
     }
-    const int head = nodes[0];
+    if (pending_) {  // the last node's slot
+      __syncthreads();
+      issue();
+      pending_ = false;
+    }
     if (e < a.n_x) mv(a.spub)[(long long)head * a.n_x + e] = (VT)sreg;
     if (e < a.n_v) mv(a.rpub)[(long long)head * a.n_v + e] = (VT)rreg;
   }
@@ -1915,12 +1962,16 @@ struct Bwd {
       const int t = a.top_nodes[ti];
       if (arrive(t)) process_top(t, chain_cursor(blockIdx.x));
     }
+    ChainIds c = chain_ids(blockIdx.x);
+    AT wpre = 0, bpre = 0;
+    if (c.m0 >= 0) node_vectors(c.m0, wpre, bpre);
     for (int ch = blockIdx.x; ch < a.n_chains && !abort_; ch += gridDim.x) {
-      const int cb = a.chain_off[ch], len = a.chain_off[ch + 1] - cb;
-      chain(a.chain_node + cb, len);
+      const int par = a.chain_parent[ch];  // read now, used after the chain
+      const ChainIds nx = chain_ids(ch + gridDim.x);
+      chain(c, nx, wpre, bpre);
       if (abort_) break;
+      c = nx;
       if (mode & MODE_NOCLIMB) continue;
-      const int par = a.chain_parent[ch];
       if (par >= 0 && arrive(par)) process_top(par, chain_cursor(ch + gridDim.x));
     }
     if (abort_) drain();
