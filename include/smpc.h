@@ -49,7 +49,7 @@ typedef enum smpc_status {
   SMPC_EBUSY = 4,     /* server: the request can never fit the memory budget or slots */
   SMPC_ETIMEOUT = 5,  /* a bounded device wait gave up; results are not valid */
   SMPC_EDIVERGED = 6, /* non-finite values in the iterates (e.g. infeasible coupling) */
-  SMPC_ENOTSUP = 7    /* valid request outside what this build implements (A != I) */
+  SMPC_ENOTSUP = 7    /* valid request outside what this build implements (e.g. A != I on schedule 4) */
 } smpc_status;
 
 typedef enum smpc_precision {
@@ -66,8 +66,11 @@ typedef struct smpc_shard smpc_shard;
 
 /* Flow-based network model x+ = A x + B u + G_d d, 0 = E u + E_d d (Sec. II-A,
  * eqs. model and demand-control).  A may be NULL for the identity (tank mass
- * balance); this build's GPU solve step requires A = I and returns SMPC_ENOTSUP
- * otherwise.  E and Ed may be NULL when n_e = 0.  E must have full row rank. */
+ * balance), the paper's network, which every iteration schedule handles.  A general
+ * A (App. B: s_n = xi_n + A' sum of the children's s, x_n = A x_parent + Bbar v_n +
+ * e_n) runs on the node-parallel schedule (2) only, with one n_x x n_x mat-vec per node
+ * in the s-scan and in the forward sweep.  E and Ed may be NULL when n_e = 0.  E must
+ * have full row rank. */
 typedef struct smpc_network {
   int32_t n_x, n_u, n_d, n_e;
   const double* A;  /* n_x * n_x or NULL (identity) */
@@ -216,7 +219,7 @@ void smpc_tree_destroy(smpc_tree* tree);
  * on the device, unless given).  An SMPC_BF16 factor also keeps float32 packs for
  * the anchor and polish iterations of smpc_solve_opts.  The tree must outlive the factor.
  * Errors: SMPC_EINVAL (sizes, NaN, E rank deficient, W_u not SPD),
- *         SMPC_ENOTSUP (A != I), SMPC_ENOMEM, SMPC_ECUDA. */
+ *         SMPC_ENOTSUP (A != I with a schedule other than 0 or 2), SMPC_ENOMEM, SMPC_ECUDA. */
 int smpc_factor(const smpc_tree* tree, const smpc_network* net, const smpc_cost* cost,
                 const smpc_factor_opts* opts, smpc_factor_t** out);
 void smpc_factor_destroy(smpc_factor_t* fac);

@@ -317,6 +317,7 @@ IterArgs make_args(const smpc_factor_t* f) {
   a.u_min = f->u_min;
   a.u_max = f->u_max;
   a.p0 = f->p0;
+  a.A = f->A;
   a.gamma_d = f->gamma_d;
   a.cvec = f->cvec;
   a.theta = f->theta;
@@ -821,13 +822,19 @@ int smpc_factor(const smpc_tree* tree, const smpc_network* net, const smpc_cost*
     set_error("network matrices contain non-finite values");
     return SMPC_EINVAL;
   }
+  bool general_A = false;  // A given and not the identity
   if (net->A) {
+    if (!finite_array(net->A, (size_t)n_x * n_x)) {
+      set_error("A contains non-finite values");
+      return SMPC_EINVAL;
+    }
     for (int i = 0; i < n_x; ++i)
       for (int j = 0; j < n_x; ++j)
-        if (net->A[i * n_x + j] != (i == j ? 1.0 : 0.0)) {
-          set_error("A != I: the GPU solve step of this build handles tank mass balance (A = I) only");
-          return SMPC_ENOTSUP;
-        }
+        if (net->A[i * n_x + j] != (i == j ? 1.0 : 0.0)) general_A = true;
+  }
+  if (general_A && o.schedule != 0 && o.schedule != SCHED_NODE) {
+    set_error("A != I runs on the node-parallel schedule (2) only");
+    return SMPC_ENOTSUP;
   }
   if (!cost->alpha1 || !cost->W_u || !cost->x_min || !cost->x_max || !cost->x_s || !cost->u_min || !cost->u_max) {
     set_error("cost pointers must not be NULL");
@@ -956,6 +963,8 @@ int smpc_factor(const smpc_tree* tree, const smpc_network* net, const smpc_cost*
       return fail(SMPC_ECUDA);
     }
   }
+  if (general_A && ((rc = f->alloc(&f->A, (size_t)n_x * n_x * vs)) || (rc = put_vec(f, f->A, net->A, (size_t)n_x * n_x))))
+    return fail(rc);
   if ((rc = f->alloc(&f->uhat64, sizeof(double) * (size_t)n * n_u)) || (rc = f->alloc(&f->abar, sizeof(double) * (size_t)f->N * n_v)) ||
       (rc = f->alloc(&f->d_p, sizeof(double) * tree->R * n_x)) || (rc = f->alloc(&f->d_q, sizeof(double) * tree->R * n_u)) ||
       (rc = f->alloc(&f->d_dhat, sizeof(double) * (size_t)f->N * std::max(n_d, 1))) ||
@@ -1005,7 +1014,9 @@ int smpc_factor(const smpc_tree* tree, const smpc_network* net, const smpc_cost*
     }
     f->lambda = 0;
   } else {
-    // Jacobi scaling: diagonal of the dual Hessian in closed form (A = I):
+    // Jacobi scaling: diagonal of the dual Hessian in closed form for A = I (with a general A
+    // the same diagonal is used as the scaling: any positive diagonal is a valid preconditioner,
+    // and lambda below comes from the scaled operator itself):
     //   x-blocks: diag(Bbar Rbar^-1 Bbar') * sum_{a in path(n)} k_a^2 / (2 p_a), k_a = path nodes from a to n
     //   inputs:   diag(L Rbar^-1 L') * sum_{a in path(n)} 1 / (2 p_a)
     // one scalar (mean) per distance block; zero-curvature inputs take their node's mean.

@@ -2020,6 +2020,7 @@ __global__ void __launch_bounds__(kThreads) fwd_scan(const __grid_constant__ Ite
   extern __shared__ __align__(128) unsigned char smem_raw[];
   __shared__ int flag[2];
   __shared__ int sid[KC];
+  __shared__ AT sX[kThreads];  // general A: the parent's state
   if (early_exit(a, nu, mode, flag, true)) return;
   const int n_k = a.n_k, e = threadIdx.x, i = e - a.n_x;
   const bool act = e < n_k, tank = e < a.n_x, lin = (mode & MODE_LINEAR) != 0;
@@ -2045,14 +2046,49 @@ __global__ void __launch_bounds__(kThreads) fwd_scan(const __grid_constant__ Ite
       __syncthreads();  // the previous chunk's node ids are consumed
       if (e < q) sid[e] = k0 + e < pl ? a.path_node[pb + k0 + e] : a.chain_node[cb + k0 + e - pl];
       __syncthreads();
-      if (!act) continue;
-      for (int r = 0; r < q; ++r) {
-        const long long m = sid[r];
-        cp_async_elem(sh + r * n_k + e, H + m * n_k + e);
-        if (HA) cp_async_elem(sa + r * n_k + e, HA + m * n_k + e);
-        if (!lin) cp_async_elem(se + r * n_k + e, tank ? E + m * a.n_x + e : UH + m * a.n_u + i);
+      if (act) {
+        for (int r = 0; r < q; ++r) {
+          const long long m = sid[r];
+          cp_async_elem(sh + r * n_k + e, H + m * n_k + e);
+          if (HA) cp_async_elem(sa + r * n_k + e, HA + m * n_k + e);
+          if (!lin) cp_async_elem(se + r * n_k + e, tank ? E + m * a.n_x + e : UH + m * a.n_u + i);
+        }
+        cp_async_wait_all();
       }
-      cp_async_wait_all();
+      if (a.A) {  // x_n = A x_parent + Bbar v_n + e_n (App. B): the state is shared per node
+        const VT* Am = reinterpret_cast<const VT*>(a.A);
+        for (int r = 0; r < q; ++r) {
+          const int k = k0 + r;
+          AT hv = 0, ev = 0;
+          if (act) {
+            hv = (AT)sh[r * n_k + e];
+            if (HA) hv += (AT)sa[r * n_k + e];
+            ev = lin ? (AT)0 : (AT)se[r * n_k + e];
+          }
+          __syncthreads();  // the previous node's reads of sX are done
+          if (act && tank) sX[e] = X;
+          __syncthreads();
+          if (act) {
+            if (tank) {
+              AT ax = 0;
+              for (int j = 0; j < a.n_x; ++j) ax += (AT)Am[(long long)e * a.n_x + j] * sX[j];
+              V += hv;
+              X = ax + V + ev;
+            } else {
+              U += hv;
+            }
+            if (k >= pl || (len == 0 && k == pl - 1)) {
+              const long long m = sid[r];
+              if (tank)
+                XO[m * a.n_x + e] = (VT)X;
+              else
+                UO[m * a.n_u + i] = (VT)(U + ev);
+            }
+          }
+        }
+        continue;
+      }
+      if (!act) continue;
       for (int r = 0; r < q; ++r) {
         const int k = k0 + r;
         AT hv = (AT)sh[r * n_k + e];
@@ -2143,6 +2179,66 @@ __global__ void __launch_bounds__(kThreads, 3) prox_node(const __grid_constant__
 // Subtree sums out_n = in_n (+ beta_n) + sum over children c of out_c.  One CTA per chain
 // (bottom-up in registers), then each top node is summed by the CTA whose arrival
 // completes its children.  which = 0: s from xi = w[:, :n_x]; which = 1: r from g, in place.
+// s of every node with a general A (App. B): s_n = xi_n + A' sum_{c in C(n)} s_c.  Along a
+// chain the sum from below is multiplied by A' at every node, so the running vector is shared
+// through shared memory and thread e forms entry e of A' s from column e of A (read through
+// the cache; A is the same for every node).  Top nodes as in scan_kernel: the CTA whose
+// arrival completes a node's children sums them and applies A'.
+template <typename VT>
+__device__ void scan_s_general_A(const IterArgs& a, int* flag) {
+  __shared__ VT sv[kThreads];
+  const int e = threadIdx.x, nx = a.n_x;
+  const VT* in = reinterpret_cast<const VT*>(a.wbuf);
+  VT* out = reinterpret_cast<VT*>(a.spub);
+  const VT* A = reinterpret_cast<const VT*>(a.A);
+  const long long is = a.n_k;
+  // own + (A' sv)_e, once sv holds the vector to multiply (all threads call it)
+  auto add_At = [&](VT own) {
+    VT acc = own;
+    if (e < nx)
+      for (int j = 0; j < nx; ++j) acc += A[(long long)j * nx + e] * sv[j];
+    return acc;
+  };
+  for (int ch = blockIdx.x; ch < a.n_chains; ch += gridDim.x) {
+    const int cb = a.chain_off[ch], len = a.chain_off[ch + 1] - cb;
+    int t = a.chain_parent[ch];
+    VT cur = 0;  // s of the chain node below (none below the bottom leaf)
+    for (int k = len - 1; k >= 0; --k) {
+      const int m = a.chain_node[cb + k];
+      const VT x = e < nx ? in[(long long)m * is + e] : (VT)0;
+      __syncthreads();  // the previous node's reads of sv are done
+      if (e < nx) sv[e] = cur;
+      __syncthreads();
+      cur = add_At(x);
+      if (e < nx) out[(long long)m * nx + e] = cur;
+    }
+    while (t >= 0) {
+      const int c0 = a.child_begin[t], cc = a.child_count[t], up = a.parent[t];
+      const VT x = e < nx ? in[(long long)t * is + e] : (VT)0;
+      __syncthreads();  // this CTA's outputs, then one fence, before its arrival
+      if (e == 0) {
+        fence_acq_rel_gpu();
+        const int last = atomicAdd(&a.counters[t], 1) == cc - 1;
+        if (last) {
+          a.counters[t] = 0;
+          fence_acq_rel_gpu();
+        }
+        flag[1] = last;
+      }
+      __syncthreads();
+      if (!flag[1]) break;
+      VT csum = 0;
+      if (e < nx)
+        for (int q = 0; q < cc; ++q) csum += ldcg(out + (long long)(c0 + q) * nx + e);
+      if (e < nx) sv[e] = csum;
+      __syncthreads();
+      const VT v = add_At(x);
+      if (e < nx) out[(long long)t * nx + e] = v;
+      t = up;
+    }
+  }
+}
+
 template <typename VT>
 __global__ void __launch_bounds__(kThreads) scan_kernel(const __grid_constant__ IterArgs a, int which, int nu,
                                                         int mode) {
@@ -2158,6 +2254,10 @@ __global__ void __launch_bounds__(kThreads) scan_kernel(const __grid_constant__ 
   const long long is = which == 0 ? a.n_k : a.n_v, os = W;
   constexpr int B = 32;  // chain nodes whose loads are in flight together
   constexpr int C = 8;   // children of a top node loaded together
+  if (which == 0 && a.A) {
+    scan_s_general_A<VT>(a, flag);
+    return;
+  }
   for (int ch = blockIdx.x; ch < a.n_chains; ch += gridDim.x) {
     const int cb = a.chain_off[ch], len = a.chain_off[ch + 1] - cb;
     int t = a.chain_parent[ch];
@@ -2891,7 +2991,7 @@ LaunchCfg config_t(const IterArgs& a, int num_sms, int S_max, int schedule, int 
     while (S > 1 && iter_smem_bytes<MT>(S, a.n_x, a.n_u, a.n_v) > (size_t)optin) --S;
     c.stages = S;
     c.smem = iter_smem_bytes<MT>(S, a.n_x, a.n_u, a.n_v);
-    if (c.smem > (size_t)optin || !fits_threads) c.stages = 0;
+    if (c.smem > (size_t)optin || !fits_threads || a.A) c.stages = 0;  // its chain pass has no A' step
     c.grid = a.n_chains < num_sms ? a.n_chains : num_sms;
     if (c.grid < 1) c.grid = 1;
     return c;
@@ -2911,7 +3011,7 @@ LaunchCfg config_t(const IterArgs& a, int num_sms, int S_max, int schedule, int 
     c.smem_chain = bwd_smem_bytes<MT>(S, a.n_x, a.n_u, a.n_v);
     c.grid_chain = a.n_chains < num_sms ? a.n_chains : num_sms;
     if (c.grid_chain < 1) c.grid_chain = 1;
-    if (c.smem_chain + 256 > (size_t)optin || 2 * a.n_k > kBT || a.n_v > kBT) c.stages = 0;
+    if (c.smem_chain + 256 > (size_t)optin || 2 * a.n_k > kBT || a.n_v > kBT || a.A) c.stages = 0;
   }
   c.smem_prox = iter_smem_bytes<MT>(0, a.n_x, a.n_u, a.n_v);  // barriers + vectors, no pack slot
   c.smem_pstage = c.smem_prox + (size_t)kWarps * prox_stage_bytes<VT>(a.n_x, a.n_u);

@@ -231,6 +231,7 @@ extern "C" int smpc_solve_static(smpc_factor_t* f, const smpc_step_data* data, c
   a.u_min = f->u_min;
   a.u_max = f->u_max;
   a.p0 = f->p0;
+  a.A = f->A;
   a.gamma_d = f->gamma_d;
   a.tol = opts->tol;
   a.wbuf = base + L.wbuf;

@@ -96,6 +96,10 @@ int smpc_shard_create(smpc_factor_t* f, int32_t chain_begin, int32_t chain_end, 
     set_error("shards run float64 and float32 factors (bfloat16 anchoring is not split)");
     return SMPC_ENOTSUP;
   }
+  if (f->A) {
+    set_error("shards run networks with A = I (the chain pass of a shard has no A' step)");
+    return SMPC_ENOTSUP;
+  }
   for (int c = 0; c < n_chains; ++c)
     if (t->chain_parent[c] < 0) {
       set_error("chain %d starts at a root: a tree split into shards needs top nodes above every chain", c);

@@ -124,6 +124,7 @@ struct IterArgs {
   const void* u_min;
   const void* u_max;
   const void* p0;                // n_x measured state
+  const void* A;                 // n_x x n_x dynamics matrix (row-major), or NULL for A = I
   double gamma_d;
   const double* cvec;            // extrapolation coefficients c_nu, nu = 0..max_iters
   const double* theta;           // theta_nu, nu = 0..max_iters (the ergodic average's weights)
@@ -320,6 +321,7 @@ struct smpc_factor_t {
   void *inv_s = nullptr, *inv_z = nullptr, *inv_p = nullptr;
   std::vector<double> mu_host;
   void *x_s = nullptr, *x_min = nullptr, *x_max = nullptr, *u_min = nullptr, *u_max = nullptr, *p0 = nullptr;
+  void* A = nullptr;  // dynamics matrix in the vector type, NULL for A = I (tank mass balance)
   double gamma_d = 0;
   int* counters = nullptr;
   int* flags = nullptr;

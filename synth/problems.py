@@ -112,6 +112,23 @@ def custom(seed, n_x, n_u, n_d, n_e, tree, dt=1.0, weights=(1.0, 1.0, 10.0, 100.
                     name="custom")
 
 
+def general_dynamics(P, seed=0, leak=0.05, exchange=0.03):
+    """A copy of instance P whose state matrix is not the identity: tanks that lose a
+    fraction of their volume per step and exchange water with the others,
+    A = (1 - leak) I + exchange R with R random, zero diagonal and rows summing to one
+    (so every row of A sums to 1 - leak + exchange and the dynamics stay bounded)."""
+    rng = np.random.default_rng(9000 + seed)
+    n_x = P["net"]["n_x"]
+    R = rng.uniform(0.0, 1.0, size=(n_x, n_x))
+    np.fill_diagonal(R, 0.0)
+    if n_x > 1:
+        R /= R.sum(axis=1, keepdims=True)
+    A = (1.0 - leak) * np.eye(n_x) + exchange * R
+    Q = dict(P)
+    Q["net"] = {**P["net"], "A": A}
+    return Q
+
+
 def random_instance(seed, n_x=3, n_u=5, n_d=3, n_e=1, horizon=5, max_children=3):
     rng = np.random.default_rng(seed + 1000)
     tree = random_tree(rng, horizon, max_children=max_children)

@@ -150,10 +150,14 @@ def test_not_supported_and_invalid_on_device():
     tree = smpc.smpc_tree_create(t["parent"], t["prob"])
     try:
         net = dict(P["net"])
-        net["A"] = 0.9 * np.eye(net["n_x"])
+        net["A"] = 0.9 * np.eye(net["n_x"])  # A != I: the fused chain pass has no A' step
+        with pytest.raises(smpc.SmpcError) as ei:
+            smpc.smpc_factor(tree, net, P["cost"], schedule=4)
+        assert ei.value.code == smpc.SMPC_ENOTSUP
+        net["A"][0, 0] = np.nan
         with pytest.raises(smpc.SmpcError) as ei:
             smpc.smpc_factor(tree, net, P["cost"])
-        assert ei.value.code == smpc.SMPC_ENOTSUP
+        assert ei.value.code == smpc.SMPC_EINVAL
         net = dict(P["net"])
         net["E"] = np.vstack([net["E"], net["E"]])
         net["Ed"] = np.vstack([net["Ed"], net["Ed"]])

@@ -34,6 +34,8 @@ def relerr(a, b):
 
 INSTANCES = [lambda: synth.tiny(0), lambda: synth.random_instance(1), lambda: synth.random_instance(2),
              lambda: synth.custom(3, 2, 4, 2, 1, synth.make_tree([1], 6))]
+# a general state matrix (App. B: q_n = A' s_n in the backward sweep, x_n = A x_parent + ... forward)
+GENERAL_A = [lambda: synth.general_dynamics(synth.tiny(0)), lambda: synth.general_dynamics(synth.random_instance(2), 1)]
 
 
 # ---------------------------------------------------------------- prox (App. C)
@@ -141,7 +143,7 @@ def test_beta_by_cost_expansion(mk):
 
 
 # ---------------------------------------------------------------- Algorithm 1 vs dense KKT
-@pytest.mark.parametrize("mk", INSTANCES)
+@pytest.mark.parametrize("mk", INSTANCES + GENERAL_A)
 def test_solve_step_equals_dense_kkt(mk):
     P = mk()
     tree, fac, cu = build(P)
@@ -163,7 +165,7 @@ def test_reduced_form_equals_three_term_form():
     assert relerr(red, inn["delta"]) < 1e-12
 
 
-@pytest.mark.parametrize("mk", INSTANCES)
+@pytest.mark.parametrize("mk", INSTANCES + GENERAL_A)
 def test_invariants_dynamics_coupling_nonanticipativity(mk):
     P = mk()
     tree, fac, cu = build(P)
@@ -276,9 +278,11 @@ def micro_instance(seed):
                         weights=(1.0, 1.0, 4.0, 20.0))
 
 
-@pytest.mark.parametrize("seed", [0, 1, 2])
-def test_apg_converges_to_bruteforce_optimum(seed):
+@pytest.mark.parametrize("seed,a", [(0, None), (1, None), (2, None), (3, 0.9)])
+def test_apg_converges_to_bruteforce_optimum(seed, a):
     P = micro_instance(seed)
+    if a is not None:  # a leaking tank: x+ = a x + B u + G d
+        P["net"] = {**P["net"], "A": np.array([[a]])}
     # push the states against their bounds so several pieces are active
     P["p"] = np.array([2.0 + seed])
     tree, fac, cu = build(P)
@@ -444,7 +448,7 @@ def _dual_rate_setup(P):
     return tree, fac, cu, L, tree.prob * P["cost"]["W_x"]
 
 
-@pytest.mark.parametrize("mk", INSTANCES[:2])
+@pytest.mark.parametrize("mk", INSTANCES[:2] + GENERAL_A[:1])
 def test_apg_dual_rate_and_zero_duality_gap(mk):
     """With the scalar step 1/L_D the iteration is the accelerated proximal gradient method
     on the dual: D* - D(y^nu) <= 2 L_D ||y^0 - y*||^2 / (nu + 1)^2.  Every iterate lies in
@@ -518,6 +522,16 @@ def test_pins_catch_planted_mistakes():
                                np.full(n, lam), np.full(n, lam))
         y = [y[0] + lam * (x - t_s), y[1] + lam * (x - t_z), y[2] + lam * (u - t_p)]
     assert d_star - dual_value(Pt, y, mu_t)[0] > 2 * L * r2 / (nu + 1) ** 2
+    # with a general A, an oracle that drops A (q_n = s_n, x_n = x_parent + ...) fails the dense KKT
+    Pa = synth.general_dynamics(synth.random_instance(2), 1)
+    tree_a, fac_a, cu_a = build(Pa)
+    wa = rand_w(np.random.default_rng(4), tree_a, fac_a, 3.0)
+    xr_a, ur_a = dr.kkt_solve(Pa, wa)
+    x_ok, u_ok = solve_step(fac_a, tree_a, cu_a, *wa, Pa["p"])
+    assert max(relerr(x_ok, xr_a), relerr(u_ok, ur_a)) < 1e-10
+    no_a = SimpleNamespace(**{**vars(fac_a), "A": np.eye(fac_a.n_x)})
+    x_bad, u_bad = solve_step(no_a, tree_a, cu_a, *wa, Pa["p"])
+    assert max(relerr(x_bad, xr_a), relerr(u_bad, ur_a)) > 1e-6
     # theta with the wrong sign fails the identity
     a = 0.5
     b = 0.5 * (np.sqrt(a ** 4 + 4 * a ** 2) + a ** 2)
