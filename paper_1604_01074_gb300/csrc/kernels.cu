@@ -2009,8 +2009,10 @@ __global__ void __launch_bounds__(kBT, 1)
 // and stores x (tank entries) or u (inputs) of the segment's own nodes.
 template <typename VT>
 __host__ __device__ constexpr int fwd_chunk() { return sizeof(VT) == 4 ? 32 : 16; }
+// h and e (or u_hat) of a chunk, and h_a behind them for anchored solves only, so that
+// plain solves fit one more CTA per SM
 template <typename VT>
-size_t fwd_smem_bytes(int n_k) { return (size_t)3 * fwd_chunk<VT>() * n_k * sizeof(VT); }
+size_t fwd_smem_bytes(int n_k, bool anchored) { return (size_t)(anchored ? 3 : 2) * fwd_chunk<VT>() * n_k * sizeof(VT); }
 
 template <typename VT, typename MT>
 __global__ void __launch_bounds__(kThreads) fwd_scan(const __grid_constant__ IterArgs a, int nu, int mode) {
@@ -2024,9 +2026,9 @@ __global__ void __launch_bounds__(kThreads) fwd_scan(const __grid_constant__ Ite
   if (early_exit(a, nu, mode, flag, true)) return;
   const int n_k = a.n_k, e = threadIdx.x, i = e - a.n_x;
   const bool act = e < n_k, tank = e < a.n_x, lin = (mode & MODE_LINEAR) != 0;
-  VT* sh = reinterpret_cast<VT*>(smem_raw);  // KC x n_k each: h, h_a, e or u_hat
-  VT* sa = sh + KC * n_k;
-  VT* se = sa + KC * n_k;
+  VT* sh = reinterpret_cast<VT*>(smem_raw);  // KC x n_k each: h, e or u_hat, h_a (anchored solves)
+  VT* se = sh + KC * n_k;
+  VT* sa = se + KC * n_k;
   const VT* H = reinterpret_cast<const VT*>(a.h);
   const VT* HA = reinterpret_cast<const VT*>(a.ha);
   const VT* E = reinterpret_cast<const VT*>(a.e);
@@ -3022,7 +3024,9 @@ LaunchCfg config_t(const IterArgs& a, int num_sms, int S_max, int schedule, int 
   c.grid_fwd = a.n_top + a.n_chains < 8 * num_sms ? a.n_top + a.n_chains : 8 * num_sms;
   c.grid_mv = a.n < num_sms ? a.n : num_sms;
   if (c.grid_scan < 1) c.grid_scan = 1;
-  c.smem_fwd = fwd_smem_bytes<VT>(a.n_k);
+  // launches with h_a (anchored solves) come from bfloat16 factors' configurations, or from
+  // configurations made with a.ha set
+  c.smem_fwd = fwd_smem_bytes<VT>(a.n_k, std::is_same<MT, __nv_bfloat16>::value || a.ha != nullptr);
   if (c.smem_fwd + 1024 > (size_t)optin) c.stages = 0;
   int S = kMaxSlots;
   while (S > 0 && iter_smem_bytes<MT>(S, a.n_x, a.n_u, a.n_v, false) > (size_t)optin) --S;
