@@ -281,6 +281,14 @@ template <typename ST, typename AT>
 __device__ __forceinline__ ST st_extrap(ST y1, ST y2, AT c) {
   return st_add(y1, st_scale(st_sub(y1, y2), c));
 }
+// The same extrapolation rounded to the vector type, for a w that is stored in it: the
+// difference of the two states and the product in single operations, within about one
+// unit in the last place of the float result (float64 state: exact up to rounding).
+__device__ __forceinline__ float st_extrap_val(DS y1, DS y2, float c) {
+  const float d = __fadd_rn(__fsub_rn(y1.hi, y2.hi), __fsub_rn(y1.lo, y2.lo));
+  return __fadd_rn(y1.hi, __fmaf_rn(c, d, y1.lo));
+}
+__device__ __forceinline__ double st_extrap_val(double y1, double y2, double c) { return fma(c, y1 - y2, y1); }
 // lambda r of a box block (App. C): with q_hi = w + lambda (x - hi) and
 // q_lo = w + lambda (x - lo) (q_hi <= q_lo), lambda r = q_hi where q_hi > 0,
 // q_lo where q_lo < 0, and 0 inside the box.
@@ -600,6 +608,12 @@ struct Kern {
       wb()[q] = v;
       if (anchor()) mv(a.wa)[q] = v;
     }
+  }
+  // w already rounded (plain and anchor launches)
+  __device__ void put_wv_at(long long q, AT w) const {
+    const VT v = (VT)w;
+    wb()[q] = v;
+    if (anchor()) mv(a.wa)[q] = v;
   }
   // stores w^nu (entry e of node m) for the backward sweep of this launch
   __device__ void put_w(long long m, int e, ST w) const {
@@ -1219,7 +1233,10 @@ struct Kern {
         const AT ez = (AT)st_val(st_sub(yzn, wz)) * iz;
         y2[e] = ysn;
         y2[n_x + e] = yzn;
-        put_w_at(mk + e, st_add(st_extrap(ysn, v1, cn), st_extrap(yzn, w1, cn)), wa_e);
+        if (dl)  // w - w_a must keep its own digits: the exact sum in the state type
+          put_w_at(mk + e, st_add(st_extrap(ysn, v1, cn), st_extrap(yzn, w1, cn)), wa_e);
+        else
+          put_wv_at(mk + e, st_extrap_val(ysn, v1, cn) + st_extrap_val(yzn, w1, cn));
         if (a.xbar) ergodic_put(a.xbar, (long long)m * n_x + e, x, it);
         rm = fmax(rm, fmax(fabs(es), fabs(ez)));
         hm = fmax(hm, fabs(x));
@@ -1235,7 +1252,10 @@ struct Kern {
         const ST ypn = box_lr(st_axpy(wp, lp, u - bnd[3 * kThreads + i]), st_axpy(wp, lp, u - bnd[4 * kThreads + i]));
         const AT ep = (AT)st_val(st_sub(ypn, wp)) * (AT)IP[i];
         y2[2 * n_x + i] = ypn;
-        put_w_at(mk + e, st_extrap(ypn, p1, cn), wa_e);
+        if (dl)
+          put_w_at(mk + e, st_extrap(ypn, p1, cn), wa_e);
+        else
+          put_wv_at(mk + e, st_extrap_val(ypn, p1, cn));
         if (a.ubar) ergodic_put(a.ubar, (long long)m * n_u + i, u, it);
         rm = fmax(rm, fabs(ep));
         hm = fmax(hm, fabs(u));
