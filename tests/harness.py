@@ -69,6 +69,8 @@ def full_size_steps(P, power_iters=40):
 
 def coupling_residual(P, u):
     """max |E u_n + E_d d_n| over the nodes (the demand coupling of eq. demand-control)."""
+    if P["net"]["E"].shape[0] == 0:  # no junction: nothing couples the inputs
+        return 0.0
     d = P["dhat"][P["tree"]["stage"]] + P["eps"]
     return float(np.abs(u @ P["net"]["E"].T + d @ P["net"]["Ed"].T).max())
 

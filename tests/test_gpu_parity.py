@@ -215,7 +215,7 @@ def test_device_resident_step_data_matches_host_inputs():
 
 @pytest.mark.parametrize("precision", [0, 1, 2])
 def test_schedules_agree_full_size(barcelona_case, precision):
-    """The two iteration schedules compute the same iterates up to rounding."""
+    """The iteration schedules compute the same iterates up to rounding."""
     P, steps = barcelona_case
     out = []
     for schedule in SCHEDULES:
@@ -226,12 +226,17 @@ def test_schedules_agree_full_size(barcelona_case, precision):
             out.append((info["rho_rel"],) + g.arrays())
         finally:
             g.close()
-    diffs = [H.relerr(a, b) for a, b in zip(out[0][1:], out[1][1:])]
-    if precision == 0:  # float64: the two summation orders agree to rounding
-        assert abs(out[0][0] - out[1][0]) <= 1e-9
-        assert max(diffs) <= 1e-9, diffs
-    else:  # reduced precision: the stated residual tolerance; arrays reported
-        assert abs(out[0][0] - out[1][0]) <= 1e-4, (out[0][0], out[1][0], diffs)
+    # every schedule against the first.  float64: the summation orders differ (chains, subtree
+    # scans, row slices), and 200 iterations grow their rounding differences past the 1e-9 of
+    # the oracle bars at 1 / 10 / 60 iterations (1.2e-9 measured between schedules 1 and 4),
+    # hence 1e-8 here; reduced precision: the stated residual tolerance, arrays reported.
+    for k in range(1, len(out)):
+        diffs = [H.relerr(a, b) for a, b in zip(out[0][1:], out[k][1:])]
+        if precision == 0:
+            assert abs(out[0][0] - out[k][0]) <= 1e-9, SCHEDULES[k]
+            assert max(diffs) <= 1e-8, (SCHEDULES[k], diffs)
+        else:
+            assert abs(out[0][0] - out[k][0]) <= 1e-4, (SCHEDULES[k], out[0][0], out[k][0], diffs)
 
 
 def test_auto_schedule_times_both():

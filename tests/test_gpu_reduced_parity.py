@@ -164,3 +164,18 @@ def test_converged_solution_matches_oracle(precision):
     assert R.rho_rel[-1] <= 1e-3
     assert abs(k - k_o) <= 0.15 * k_o, msg
     assert max(eu, ex, ey) <= CONVERGED_BOUND, msg
+
+
+@pytest.mark.parametrize("name", list(H.edge_instances()))
+@pytest.mark.parametrize("precision", [1, 2])
+def test_edge_trees_fused_chain_pass(name, precision):
+    """The fused chain pass (schedule 4) in reduced precision on the ragged and degenerate
+    trees (a single node, one chain, chains of one and of mixed lengths under branching
+    nodes, forests of top nodes): with bfloat16 packs these small networks fit three or
+    more pack slots, so consecutive chain nodes run overlapped, which the full-size trees
+    (two float32 slots) do not exercise at these chain lengths."""
+    import oracle
+    P = H.edge_instances()[name]
+    tree, fac, _ = H.oracle_build(P)
+    P = dict(P, name="edge_" + name)
+    _compare(P, oracle.jacobi_steps(fac, tree), 60, precision, schedule=4)
