@@ -143,8 +143,13 @@ typedef struct smpc_step_data {
   const double* alpha2; /* (N_0 + ... + N_{R-1}) * n_u time-varying price, rows as dhat */
 } smpc_step_data;
 
+/* Largest iteration cap a solve accepts: the per-iteration tables a solve keeps (the
+ * extrapolation coefficients on the host and the device, the residual history) grow with
+ * it, and larger caps are refused with SMPC_EINVAL before anything is allocated. */
+#define SMPC_MAX_ITERS (1 << 26)
+
 typedef struct smpc_solve_opts {
-  int32_t max_iters;    /* iteration cap (> 0) */
+  int32_t max_iters;    /* iteration cap, 1 .. SMPC_MAX_ITERS */
   double tol;           /* stop at the first iterate with rho_rel <= tol (0: run max_iters) */
   int32_t warm_start;   /* 1: start from the duals the previous solve left on the device */
   int32_t check_every;  /* host polls the stop flag every this many iterations (0: 128) */
@@ -332,7 +337,7 @@ int smpc_shard_finish(smpc_shard* shard, int32_t launched, smpc_result* res);
 void smpc_shard_destroy(smpc_shard* shard);
 
 /* Diagnostics; the paper has no counterpart.  Runs one cold-start solve of `iters`
- * iterations (tol 0, legacy default stream) with a CUDA event between consecutive kernels
+ * iterations (2 .. 4096; tol 0, legacy default stream) with a CUDA event between consecutive kernels
  * of every full iteration, and writes the mean device time in ms
  * of each kernel of an iteration to stage_ms[0 .. min(n, max_stages)).  n = 1 for schedule 1
  * (apg_iter), 6 for schedule 2 (forward sweep, prox and dual update, subtree scan of s,

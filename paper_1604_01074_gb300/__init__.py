@@ -16,6 +16,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libsmpc.so")
 
 SMPC_OK, SMPC_EINVAL, SMPC_ENOMEM, SMPC_ECUDA, SMPC_EBUSY, SMPC_ETIMEOUT, SMPC_EDIVERGED, SMPC_ENOTSUP = range(8)
+SMPC_MAX_ITERS = 1 << 26  # include/smpc.h: the largest max_iters a solve accepts
 SMPC_FP64, SMPC_FP32, SMPC_BF16 = 0, 1, 2
 
 _dp = ctypes.POINTER(ctypes.c_double)

@@ -1154,8 +1154,8 @@ int solve_begin(smpc_factor_t* f, const smpc_step_data* data, const smpc_solve_o
     set_error("step data needs p, q, dhat and alpha2");
     return SMPC_EINVAL;
   }
-  if (opts->max_iters < 1 || !(opts->tol >= 0)) {
-    set_error("max_iters must be >= 1 and tol >= 0");
+  if (opts->max_iters < 1 || opts->max_iters > SMPC_MAX_ITERS || !(opts->tol >= 0)) {
+    set_error("max_iters must be in [1, %d] and tol >= 0", SMPC_MAX_ITERS);
     return SMPC_EINVAL;
   }
   const int n = f->n, N = f->N, n_x = f->n_x, n_u = f->n_u, n_d = f->n_d;
@@ -1299,8 +1299,9 @@ int smpc_solve(smpc_factor_t* f, const smpc_step_data* data, const smpc_solve_op
 
 int smpc_profile_solve(smpc_factor_t* f, const smpc_step_data* data, int32_t iters, double* stage_ms,
                        int32_t max_stages) {
-  if (!f || !data || !stage_ms || max_stages < 1 || iters < 2) {
-    set_error("smpc_profile_solve needs a factor, step data, iters >= 2 and room for the stage times");
+  if (!f || !data || !stage_ms || max_stages < 1 || iters < 2 || iters > kProfileMaxIters) {
+    set_error("smpc_profile_solve needs a factor, step data, 2 <= iters <= %d and room for the stage times",
+              kProfileMaxIters);
     return -SMPC_EINVAL;
   }
   Profile P;

@@ -123,8 +123,8 @@ extern "C" int smpc_solve_static(smpc_factor_t* f, const smpc_step_data* data, c
     set_error("step data needs p, q, dhat and alpha2");
     return SMPC_EINVAL;
   }
-  if (opts->max_iters < 1 || !(opts->tol >= 0)) {
-    set_error("max_iters must be >= 1 and tol >= 0");
+  if (opts->max_iters < 1 || opts->max_iters > SMPC_MAX_ITERS || !(opts->tol >= 0)) {
+    set_error("max_iters must be in [1, %d] and tol >= 0", SMPC_MAX_ITERS);
     return SMPC_EINVAL;
   }
   if (opts->ergodic) {

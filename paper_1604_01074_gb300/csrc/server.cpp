@@ -17,6 +17,7 @@
 #include <cstring>
 #include <deque>
 #include <mutex>
+#include <new>
 #include <string>
 #include <thread>
 #include <unordered_map>
@@ -131,15 +132,23 @@ void smpc_server::worker(int slot) {
     d.dhat = stage(2, r->dhat);
     d.eps = r->has_eps ? stage(3, r->eps) : nullptr;
     d.alpha2 = stage(4, r->alpha2);
-    r->u0.assign((size_t)r->f->R * r->f->n_u, 0.0);
-    r->history.assign((size_t)r->opts.max_iters * 3, 0.0);
+    bool host_ok = true;  // no exception leaves the worker: a failed allocation is the request's status
+    try {
+      r->u0.assign((size_t)r->f->R * r->f->n_u, 0.0);
+      r->history.assign((size_t)r->opts.max_iters * 3, 0.0);
+    } catch (const std::bad_alloc&) {
+      host_ok = false;
+    }
     smpc_result res{};
     res.u0_host = r->u0.data();
     res.history_host = r->history.data();
     smpc_solve_opts o = r->opts;
     o.sync = 1;  // this worker waits; the other slots keep running
     int rc = SMPC_OK;
-    if ((r->p.size() && !d.p) || (r->alpha2.size() && !d.alpha2)) {
+    if (!host_ok) {
+      rc = SMPC_ENOMEM;
+      r->error = "host allocation of the residual history failed";
+    } else if ((r->p.size() && !d.p) || (r->alpha2.size() && !d.alpha2)) {
       rc = SMPC_ENOMEM;
       r->error = "pinned staging allocation failed";
     } else {
@@ -218,8 +227,8 @@ int smpc_submit(smpc_server* sv, smpc_factor_t* f, const smpc_step_data* data, c
     return SMPC_EINVAL;
   }
   if (!data->p || !data->q || !data->alpha2 || (f->n_d > 0 && !data->dhat) || opts->max_iters < 1 ||
-      !(opts->tol >= 0)) {
-    set_error("step data needs p, q, dhat and alpha2; max_iters >= 1 and tol >= 0");
+      opts->max_iters > SMPC_MAX_ITERS || !(opts->tol >= 0)) {
+    set_error("step data needs p, q, dhat and alpha2; max_iters in [1, %d] and tol >= 0", SMPC_MAX_ITERS);
     return SMPC_EINVAL;
   }
   if (f->device_bytes > sv->budget) {

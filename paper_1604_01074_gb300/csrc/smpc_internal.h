@@ -252,6 +252,7 @@ size_t vec_size(int prec);
 
 // Per-kernel timing of full iterations (smpc_profile_solve): kStageEvents events per
 // iteration, read once the solve has finished so that launches still run ahead.
+constexpr int kProfileMaxIters = 4096;  // iterations of one profiling solve (events per iteration below)
 struct Profile {
   static constexpr int kStageEvents = 7;
   std::vector<cudaEvent_t> ev;  // capacity x kStageEvents

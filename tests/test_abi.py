@@ -81,7 +81,8 @@ def test_valid_tree_without_device_is_a_cuda_error(lib):
 
 def test_binding_structs_match_the_header_layout(tmp_path):
     """Every ctypes mirror of a struct in include/smpc.h has the C compiler's size and field
-    offsets (a field added, dropped or reordered on one side only fails here)."""
+    offsets (a field added, dropped or reordered on one side only fails here), and the
+    binding's status codes and iteration limit are the header's."""
     import shutil
     import subprocess
     cc = shutil.which("gcc") or shutil.which("cc")
@@ -97,6 +98,10 @@ def test_binding_structs_match_the_header_layout(tmp_path):
         for name, _ in s._fields_:
             c = cname.get(name, name)
             lines.append(f'  printf("{t} {name} %zu\\n", offsetof({t}, {c}));')
+    lines.append('  printf("const SMPC_MAX_ITERS %d\\n", (int)SMPC_MAX_ITERS);')
+    for code in ("SMPC_OK", "SMPC_EINVAL", "SMPC_ENOMEM", "SMPC_ECUDA", "SMPC_EBUSY", "SMPC_ETIMEOUT",
+                 "SMPC_EDIVERGED", "SMPC_ENOTSUP", "SMPC_FP64", "SMPC_FP32", "SMPC_BF16"):
+        lines.append(f'  printf("const {code} %d\\n", (int){code});')
     lines += ["  return 0;", "}"]
     src = tmp_path / "layout.c"
     src.write_text("\n".join(lines) + "\n")
@@ -106,6 +111,9 @@ def test_binding_structs_match_the_header_layout(tmp_path):
     for line in subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.splitlines():
         t, field, val = line.split()
         got[(t, field)] = int(val)
+    for (t, name), val in got.items():  # the binding's constants are the header's
+        if t == "const":
+            assert getattr(smpc, name) == val, name
     for s in structs:
         t = s.__name__
         assert got[(t, "sizeof")] == ctypes.sizeof(s), t

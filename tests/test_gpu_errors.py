@@ -12,6 +12,9 @@
   whose copy has not landed yet give up;
   the CTA records the error, lets its copies in flight land under the normal 2 s
   bound and returns, and the other kernels of the solve see the error flag and exit.
+* SMPC_EINVAL for an iteration cap above SMPC_MAX_ITERS (the per-iteration tables would
+  be sized from it), from smpc_solve, smpc_submit and smpc_profile_solve (above 4096),
+  before any allocation.
 After each, the same process solves a fresh factor normally.
 """
 import os
@@ -122,6 +125,32 @@ def test_pipeline_wait_that_gives_up_reports_etimeout():
     g = H.Gpu(P, steps=steps, precision=1, schedule=2)  # the normal bound again
     try:
         assert g.solve(10)["iterations"] == 10
+    finally:
+        g.close()
+    _healthy_after()
+
+
+def test_iteration_cap_beyond_the_limit_is_refused():
+    import paper_1604_01074_gb300 as smpc
+    P = synth.tiny(0)
+    g = H.Gpu(P, steps=H.tiny_steps(P))
+    try:
+        with pytest.raises(smpc.SmpcError) as ei:
+            smpc.smpc_solve(g.fac, P["p"], P["q"], P["dhat"], P["alpha2"], eps=P["eps"],
+                            max_iters=smpc.SMPC_MAX_ITERS + 1, sync=1)
+        assert ei.value.code == smpc.SMPC_EINVAL, ei.value
+        with pytest.raises(smpc.SmpcError) as ei:
+            smpc.smpc_profile_solve(g.fac, P["p"], P["q"], P["dhat"], P["alpha2"], eps=P["eps"], iters=4097)
+        assert ei.value.code == smpc.SMPC_EINVAL, ei.value
+        server = smpc.smpc_server_create(1 << 30, 1)
+        try:
+            with pytest.raises(smpc.SmpcError) as ei:
+                smpc.smpc_submit(server, g.fac, P["p"], P["q"], P["dhat"], P["alpha2"], eps=P["eps"],
+                                 max_iters=smpc.SMPC_MAX_ITERS + 1)
+            assert ei.value.code == smpc.SMPC_EINVAL, ei.value
+        finally:
+            smpc.smpc_server_destroy(server)
+        assert g.solve(20)["iterations"] == 20  # the factor is untouched
     finally:
         g.close()
     _healthy_after()
