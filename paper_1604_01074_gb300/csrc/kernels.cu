@@ -2819,9 +2819,11 @@ constexpr int kTcMaxN = 64;     // nodes per GEMM (the N of the MMA): 16, 32 or 
 constexpr int kTcCore = 128;    // bytes per core matrix
 
 __host__ __device__ inline int tc_kp(int n_v) { return (n_v + 15) / 16 * 16; }
+// float32 R block of one batch (tn nodes' r, contiguous in rpub), staged by a bulk copy
+__host__ __device__ inline size_t tc_stage_bytes(int n_v, int tn) { return (size_t)tn * n_v * sizeof(float); }
 __host__ __device__ inline size_t tc_smem_bytes(int n_v, int tn) {
   const size_t sbo = (size_t)tc_kp(n_v) / 8 * kTcCore;  // bytes per 8-row group
-  return (128 / 8) * sbo + (256 / 8) * sbo + 2 * (size_t)(tn / 8) * sbo + 64;
+  return (128 / 8) * sbo + (256 / 8) * sbo + 2 * (size_t)(tn / 8) * sbo + 64 + 2 * tc_stage_bytes(n_v, tn);
 }
 __host__ __device__ inline bool tc_fits(int n_x, int n_u, int n_v) { return n_v <= 128 && n_x + n_u <= 256; }
 
@@ -2875,8 +2877,15 @@ __global__ void __launch_bounds__(128, 1) node_mv_tc(const __grid_constant__ Ite
   unsigned char* A2 = A1 + 16 * sbo;              // [Bbar; L], 256 rows
   unsigned char* B1 = A2 + 32 * sbo;              // R (tn rows)
   unsigned char* B2 = B1 + (tn / 8) * sbo;        // delta (tn rows)
-  uint64_t* bar = reinterpret_cast<uint64_t*>(B2 + (tn / 8) * sbo);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(B2 + (tn / 8) * sbo);  // MMA completion
   uint32_t* tslot = reinterpret_cast<uint32_t*>(bar + 1);
+  uint64_t* sbar = bar + 2;  // the two R staging buffers' copies
+  // R of a whole batch is tn consecutive rows of rpub (tn n_v floats, a 16-byte multiple at a
+  // 16-byte aligned offset): one bulk copy per batch, issued one batch ahead into the other
+  // buffer, so that a batch's R is on chip when its MMAs are due (the last batch of a tree
+  // with fewer than tn nodes left reads its rows with plain loads)
+  const uint32_t sbytes = (uint32_t)tc_stage_bytes(n_v, tn);
+  unsigned char* stage0 = B2 + (tn / 8) * sbo + 64;  // buffer sb at stage0 + sb * sbytes
   // pack -> core-matrix layout, zero padding (16-byte chunks; the pack's rows are ld >= n_v wide)
   const __nv_bfloat16* pk = reinterpret_cast<const __nv_bfloat16*>(a.packs);
   const long long kp = kpad<__nv_bfloat16>(n_k, n_v);
@@ -2899,6 +2908,8 @@ __global__ void __launch_bounds__(128, 1) node_mv_tc(const __grid_constant__ Ite
     reinterpret_cast<uint4*>(B1)[q] = make_uint4(0, 0, 0, 0);
   if (tid == 0) {
     mbar_init(bar, 1);
+    mbar_init(&sbar[0], 1);
+    mbar_init(&sbar[1], 1);
     fence_barrier_init();
   }
   if (warp == 0) {  // 3 tn accumulator columns: D1, D2 rows 0-127, D2 rows 128-255 (tn <= 64)
@@ -2916,13 +2927,43 @@ __global__ void __launch_bounds__(128, 1) node_mv_tc(const __grid_constant__ Ite
   uint32_t phase = 0;
   bool failed = false;
   const int batches = (a.n + tn - 1) / tn;
-  for (int bt = blockIdx.x; bt < batches && !failed; bt += gridDim.x) {
+  auto full = [&](int bt) { return bt < batches && (long long)(bt + 1) * tn <= a.n; };
+  uint32_t sphase = 0;   // bit sb: the phase of buffer sb's barrier to wait for
+  uint32_t pending = 0;  // bit sb: a copy into buffer sb issued and not yet awaited
+  auto stage_copy = [&](int bt, int sb) {
+    if (tid == 0) {
+      fence_proxy_async();  // the buffer's last reads (generic) before the copy's writes (async)
+      mbar_expect_tx(&sbar[sb], sbytes);
+      bulk_g2s(stage0 + (size_t)sb * sbytes, rp + (long long)bt * tn * n_v, sbytes, &sbar[sb]);
+    }
+    pending |= 1u << sb;
+  };
+  if (full(blockIdx.x)) stage_copy(blockIdx.x, 0);
+  int it = 0;
+  for (int bt = blockIdx.x; bt < batches && !failed; bt += gridDim.x, ++it) {
     const long long m0 = (long long)bt * tn;
     const int nb = min(tn, a.n - (int)m0);
+    const int sb = it & 1;
+    const bool staged = full(bt);
+    // the next batch's R into the other buffer, whose last reads ended at the previous batch's barriers
+    if (full(bt + (int)gridDim.x)) stage_copy(bt + (int)gridDim.x, sb ^ 1);
+    if (staged) {
+      if (mbar_wait(&sbar[sb], (sphase >> sb) & 1u)) {
+        sphase ^= 1u << sb;
+        pending &= ~(1u << sb);
+      } else {
+        failed = true;
+      }
+      if (__syncthreads_or(failed)) {
+        failed = true;
+        break;
+      }
+    }
     // R: row b = node m0 + b, bfloat16
+    const float* sr = reinterpret_cast<const float*>(stage0 + (size_t)sb * sbytes);
     for (int q = tid; q < tn * n_v; q += blockDim.x) {
       const int b = q / n_v, j = q % n_v;
-      const float v = b < nb ? (float)rp[(m0 + b) * n_v + j] : 0.f;
+      const float v = staged ? sr[q] : (b < nb ? (float)rp[(m0 + b) * n_v + j] : 0.f);
       *reinterpret_cast<__nv_bfloat16*>(B1 + tc_off(b, j, sbo)) = __float2bfloat16_rn(v);
     }
     fence_proxy_async();
@@ -2990,6 +3031,9 @@ __global__ void __launch_bounds__(128, 1) node_mv_tc(const __grid_constant__ Ite
     a.flags[1] = SMPC_ETIMEOUT;
     mbar_wait(bar, phase ^ 1);  // bounded: let the MMAs in flight finish before freeing tensor memory
   }
+  if (failed)  // bounded: let the staging copies in flight land before the CTA's shared memory goes
+    for (int sb = 0; sb < 2; ++sb)
+      if ((pending >> sb) & 1u) mbar_wait(&sbar[sb], (sphase >> sb) & 1u);
   tc_sync();
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(256));
 }
