@@ -3038,6 +3038,165 @@ __global__ void __launch_bounds__(128, 1) node_mv_tc(const __grid_constant__ Ite
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(256));
 }
 
+// [Bbar; L]' y of the delta launches of a bfloat16 shared pack (the node-parallel schedule's
+// second launch) as GEMMs on the tensor cores, tn nodes at a time:
+//   D = Kt_pad (128 x Kq) . Y (Kq x tn),   Kt = [Bbar; L]' (n_v x n_k),  Kq = n_k rounded up to 16,
+// y_b = [s_b; psi_b] (the subtree sum s from the scan, psi from w) rounded to bfloat16 - in a
+// delta launch they are changes since the anchor, as in node_mv_tc - and g_b = D[:, b] to
+// rpub, where the scan of r adds beta and the children.  Kt is built once per CTA by
+// transposing the pack's rows in shared memory.  A batch's s and w rows (contiguous, 16-byte
+// multiples at 16-byte aligned offsets) arrive by two bulk copies issued one batch ahead into
+// the other of two staging buffers.  Every wait is bounded.
+__host__ __device__ inline int tc_kq(int n_k) { return (n_k + 15) / 16 * 16; }
+__host__ __device__ inline size_t gt_stage_bytes(int n_x, int n_k, int tn) {
+  return (size_t)tn * (n_x + n_k) * sizeof(float);
+}
+__host__ __device__ inline size_t gt_smem_bytes(int n_x, int n_k, int tn) {
+  const size_t sbo = (size_t)tc_kq(n_k) / 8 * kTcCore;  // bytes per 8-row group
+  return (128 / 8) * sbo + (size_t)(tn / 8) * sbo + 64 + 2 * gt_stage_bytes(n_x, n_k, tn);
+}
+// element t (0..7) of the 8 bfloat16 values in v, as its 16 bits
+__device__ __forceinline__ unsigned short bf16_bits(const uint4& v, int t) {
+  const uint32_t w = t < 2 ? v.x : t < 4 ? v.y : t < 6 ? v.z : v.w;
+  return (unsigned short)((t & 1) ? (w >> 16) : (w & 0xffffu));
+}
+
+template <typename VT>
+__global__ void __launch_bounds__(128, 1) node_gt_tc(const __grid_constant__ IterArgs a, int tn, int nu, int mode) {
+  grid_dep_sync();
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  __shared__ int flag[2];
+  if (early_exit(a, nu, mode, flag, false)) return;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int n_x = a.n_x, n_k = a.n_k, n_v = a.n_v, Kq = tc_kq(n_k), ld = row_stride<__nv_bfloat16>(n_v);
+  const int sbo = Kq / 8 * kTcCore;
+  unsigned char* At = smem_raw;                                    // Kt: 128 rows (n_v used), Kq columns
+  unsigned char* Bm = At + 16 * sbo;                               // Y: tn rows
+  uint64_t* bar = reinterpret_cast<uint64_t*>(Bm + (tn / 8) * sbo);  // MMA completion
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(bar + 1);
+  uint64_t* sbar = bar + 2;                                        // the two staging buffers' copies
+  const uint32_t sx = (uint32_t)((size_t)tn * n_x * sizeof(float));  // s rows, then w rows
+  const uint32_t sbytes = (uint32_t)gt_stage_bytes(n_x, n_k, tn);
+  unsigned char* stage0 = Bm + (tn / 8) * sbo + 64;               // buffer sb at stage0 + sb * sbytes
+  for (int q = tid; q < (16 + tn / 8) * sbo / 16; q += blockDim.x) reinterpret_cast<uint4*>(At)[q] = make_uint4(0, 0, 0, 0);
+  __syncthreads();  // zero padding (rows n_v .. 127, columns n_k .. Kq - 1) before the scattered writes
+  // Kt[j][i] = [Bbar; L][i][j]: 16-byte chunks of the pack's rows, each spread over 8 rows of Kt
+  const __nv_bfloat16* pk = reinterpret_cast<const __nv_bfloat16*>(a.packs);
+  const int kc = ld / 8;
+  for (int q = tid; q < n_k * kc; q += blockDim.x) {
+    const int i = q / kc, c = q % kc;
+    const uint4 v = *reinterpret_cast<const uint4*>(pk + (long long)i * ld + 8 * c);
+#pragma unroll
+    for (int t = 0; t < 8; ++t) {
+      const int j = 8 * c + t;
+      if (j < n_v) *reinterpret_cast<unsigned short*>(At + tc_off(j, i, sbo)) = bf16_bits(v, t);
+    }
+  }
+  if (tid == 0) {
+    mbar_init(bar, 1);
+    mbar_init(&sbar[0], 1);
+    mbar_init(&sbar[1], 1);
+    fence_barrier_init();
+  }
+  if (warp == 0) {  // tn <= 64 accumulator columns
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)), "r"(64));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  fence_proxy_async();
+  tc_sync();
+  const uint32_t tmem = *tslot;
+  const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(tn >> 3) << 17) | (8u << 24);
+  const VT* sp = reinterpret_cast<const VT*>(a.spub);
+  const VT* wb = reinterpret_cast<const VT*>(a.wbuf);
+  VT* rp = reinterpret_cast<VT*>(a.rpub);
+  uint32_t phase = 0;
+  bool failed = false;
+  const int batches = (a.n + tn - 1) / tn;
+  auto full = [&](int bt) { return bt < batches && (long long)(bt + 1) * tn <= a.n; };
+  uint32_t sphase = 0;   // bit sb: the phase of buffer sb's barrier to wait for
+  uint32_t pending = 0;  // bit sb: a copy into buffer sb issued and not yet awaited
+  auto stage_copy = [&](int bt, int sb) {
+    if (tid == 0) {
+      fence_proxy_async();  // the buffer's last reads (generic) before the copies' writes (async)
+      unsigned char* dst = stage0 + (size_t)sb * sbytes;
+      mbar_expect_tx(&sbar[sb], sbytes);
+      bulk_g2s(dst, sp + (long long)bt * tn * n_x, sx, &sbar[sb]);
+      bulk_g2s(dst + sx, wb + (long long)bt * tn * n_k, sbytes - sx, &sbar[sb]);
+    }
+    pending |= 1u << sb;
+  };
+  if (full(blockIdx.x)) stage_copy(blockIdx.x, 0);
+  int it = 0;
+  for (int bt = blockIdx.x; bt < batches && !failed; bt += gridDim.x, ++it) {
+    const long long m0 = (long long)bt * tn;
+    const int nb = min(tn, a.n - (int)m0);
+    const int sb = it & 1;
+    const bool staged = full(bt);
+    // the next batch's rows into the other buffer, whose last reads ended at the previous batch's barriers
+    if (full(bt + (int)gridDim.x)) stage_copy(bt + (int)gridDim.x, sb ^ 1);
+    if (staged) {
+      if (mbar_wait(&sbar[sb], (sphase >> sb) & 1u)) {
+        sphase ^= 1u << sb;
+        pending &= ~(1u << sb);
+      } else {
+        failed = true;
+      }
+      if (__syncthreads_or(failed)) {
+        failed = true;
+        break;
+      }
+    }
+    // Y: row b = [s; psi] of node m0 + b, bfloat16 (columns n_k .. Kq - 1 stay zero)
+    const float* ss = reinterpret_cast<const float*>(stage0 + (size_t)sb * sbytes);
+    const float* sw = reinterpret_cast<const float*>(stage0 + (size_t)sb * sbytes + sx);
+    for (int q = tid; q < tn * n_k; q += blockDim.x) {
+      const int b = q / n_k, i = q % n_k;
+      float v;
+      if (staged)
+        v = i < n_x ? ss[b * n_x + i] : sw[q];
+      else
+        v = b < nb ? (float)(i < n_x ? sp[(m0 + b) * n_x + i] : wb[(m0 + b) * n_k + i]) : 0.f;
+      *reinterpret_cast<__nv_bfloat16*>(Bm + tc_off(b, i, sbo)) = __float2bfloat16_rn(v);
+    }
+    fence_proxy_async();
+    tc_sync();
+    if (tid == 0) {
+      for (int ks = 0; ks < Kq / 16; ++ks)
+        umma_bf16(tmem, umma_desc(smem_u32(At) + ks * 2 * kTcCore, kTcCore, sbo),
+                  umma_desc(smem_u32(Bm) + ks * 2 * kTcCore, kTcCore, sbo), idesc, ks > 0);
+      umma_commit(bar);
+    }
+    if (!mbar_wait(bar, phase)) failed = true;
+    phase ^= 1;
+    if (__syncthreads_or(failed)) {
+      failed = true;
+      break;
+    }
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    // g: warp w holds rows 32w .. 32w + 31 of D (the entries of g), one column per node
+    const int j = 32 * warp + lane;
+    for (int c0 = 0; c0 < tn; c0 += 16) {
+      float v[16];
+      tmem_ld16(tmem + ((uint32_t)(32 * warp) << 16) + c0, v);
+      if (j < n_v) {
+#pragma unroll
+        for (int t = 0; t < 16; ++t)
+          if (c0 + t < nb) rp[(m0 + c0 + t) * n_v + j] = (VT)v[t];
+      }
+    }
+    tc_sync();  // Y and the accumulators are free for the next batch
+  }
+  if (failed && tid == 0) {
+    a.flags[1] = SMPC_ETIMEOUT;
+    mbar_wait(bar, phase ^ 1);  // bounded: let the MMAs in flight finish before freeing tensor memory
+  }
+  if (failed)  // bounded: let the staging copies in flight land before the CTA's shared memory goes
+    for (int sb = 0; sb < 2; ++sb)
+      if ((pending >> sb) & 1u) mbar_wait(&sbar[sb], (sphase >> sb) & 1u);
+  tc_sync();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(64));
+}
+
 int optin_smem() {
   int dev = 0, optin = 0;
   cudaGetDevice(&dev);
@@ -3117,6 +3276,8 @@ LaunchCfg config_t(const IterArgs& a, int num_sms, int S_max, int schedule, int 
     c.smem_tc = tc_smem_bytes(a.n_v, c.tn);
     const int batches = (a.n + c.tn - 1) / c.tn;
     c.grid_tc = batches < num_sms ? batches : num_sms;
+    c.smem_gt_tc = gt_smem_bytes(a.n_x, a.n_k, c.tn);  // [Bbar; L]' y on the tensor cores when it fits
+    c.tc_gt = c.smem_gt_tc + 256 <= (size_t)optin;
   }
   if (a.pack_stride == 0) {
     c.smem_mgt = multi_smem_bytes<MT>(a.n_x, a.n_u, a.n_v, false);
@@ -3165,7 +3326,10 @@ int launch_t(const IterArgs& a, const LaunchCfg& c, int nu, int mode, cudaStream
     allow(fwd_scan<VT, MT>);
     allow(node_mv_shared<VT, MT, false>);
     allow(node_mv_shared<VT, MT, true>);
-    if constexpr (std::is_same<MT, __nv_bfloat16>::value) allow(node_mv_tc<VT>);
+    if constexpr (std::is_same<MT, __nv_bfloat16>::value) {
+      allow(node_mv_tc<VT>);
+      allow(node_gt_tc<VT>);
+    }
     cudaGetLastError();  // a refused attribute surfaces at the launch, not here
     return true;
   }();
@@ -3216,7 +3380,16 @@ int launch_t(const IterArgs& a, const LaunchCfg& c, int nu, int mode, cudaStream
   } else if (mode & MODE_BWD) {
     launch_dep(scan_kernel<VT>, c.grid_scan, c.block, 0, s, dep, a, 0, nu, mode);
     mark();
-    if (c.multi_gt)
+    bool gt_done = false;
+    if constexpr (std::is_same<MT, __nv_bfloat16>::value) {
+      if (c.tc && c.tc_gt && (mode & MODE_DELTA)) {
+        launch_dep(node_gt_tc<VT>, c.grid_tc, 128, c.smem_gt_tc, s, dep, a, c.tn, nu, mode);
+        gt_done = true;
+      }
+    }
+    if (gt_done)
+      ;
+    else if (c.multi_gt)
       launch_dep(node_mv_shared<VT, MT, false>, c.grid_multi, c.block, c.smem_mgt, s, dep, a, nu, mode);
     else
       launch_dep(node_mv<VT, MT, false>, c.grid_mv, c.block, c.smem_gt, s, dep, a, c.s_gt, nu, mode);

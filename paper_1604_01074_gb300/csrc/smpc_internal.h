@@ -185,6 +185,8 @@ struct LaunchCfg {
   int s_gt = 0, s_dh = 0;   // pack slots of the two mat-vec launches (0: does not fit)
   bool multi_gt = false, multi_dh = false;  // shared pack: several nodes per pass over it
   bool tc = false;          // bfloat16 shared pack: Lambda / [Bbar; L] of delta launches on tensor cores
+  bool tc_gt = false;       // ... and [Bbar; L]' y of delta launches (node-parallel schedule)
+  size_t smem_gt_tc = 0;
   size_t smem_tc = 0;
   int grid_tc = 1, tn = 64;  // tensor-core launch: CTAs, nodes per GEMM
   size_t smem_mgt = 0, smem_mdh = 0;
