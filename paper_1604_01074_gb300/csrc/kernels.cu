@@ -2817,6 +2817,10 @@ __global__ void __launch_bounds__(kThreads, 1) node_mv_shared(const __grid_const
 // whose rounding is an error proportional to |w - w_a| (the anchors run in float32).
 constexpr int kTcMaxN = 64;     // nodes per GEMM (the N of the MMA): 16, 32 or 64
 constexpr int kTcCore = 128;    // bytes per core matrix
+// threads of a tensor-core CTA: eight warps share the vector work (conversions, layout
+// scatters, result write-back); warp w reads tensor-memory lanes 32 (w mod 4) .. + 31 (the
+// quarter a warp may access) and the 16-column chunks c0 = 16 (w div 4), + 32, ...
+constexpr int kTcThreads = 256;
 
 __host__ __device__ inline int tc_kp(int n_v) { return (n_v + 15) / 16 * 16; }
 // float32 R block of one batch (tn nodes' r, contiguous in rpub), staged by a bulk copy
@@ -2865,12 +2869,13 @@ __device__ __forceinline__ int tc_off(int r, int k, int sbo) {
 }
 
 template <typename VT>
-__global__ void __launch_bounds__(128, 1) node_mv_tc(const __grid_constant__ IterArgs a, int tn, int nu, int mode) {
+__global__ void __launch_bounds__(kTcThreads, 1) node_mv_tc(const __grid_constant__ IterArgs a, int tn, int nu, int mode) {
   grid_dep_sync();
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   __shared__ int flag[2];
   if (early_exit(a, nu, mode, flag, false)) return;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int qw = warp & 3, hc = warp >> 2;  // tensor-memory lane quarter, column-chunk parity
   const int n_k = a.n_k, n_v = a.n_v, Kp = tc_kp(n_v), ld = row_stride<__nv_bfloat16>(n_v);
   const int sbo = Kp / 8 * kTcCore;
   unsigned char* A1 = smem_raw;                   // Lambda, 128 rows
@@ -2981,12 +2986,12 @@ __global__ void __launch_bounds__(128, 1) node_mv_tc(const __grid_constant__ Ite
       break;
     }
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    // delta = D1 / (2 p_b): warp w holds rows 32w..32w+31 (the entries of delta)
+    // delta = D1 / (2 p_b): warp w reads rows 32 (w mod 4) .. + 31 (the entries of delta)
     {
-      const int i = 32 * warp + lane;
-      for (int c0 = 0; c0 < tn; c0 += 16) {
+      const int i = 32 * qw + lane;
+      for (int c0 = 16 * hc; c0 < tn; c0 += 32) {
         float v[16];
-        tmem_ld16(d1 + ((uint32_t)(32 * warp) << 16) + c0, v);
+        tmem_ld16(d1 + ((uint32_t)(32 * qw) << 16) + c0, v);
         if (i < Kp) {
 #pragma unroll
           for (int j = 0; j < 16; ++j) {
@@ -3014,10 +3019,10 @@ __global__ void __launch_bounds__(128, 1) node_mv_tc(const __grid_constant__ Ite
     }
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     for (int t = 0; t < 2; ++t) {
-      const int i = 128 * t + 32 * warp + lane;  // row of [Bbar; L], entry of h
-      for (int c0 = 0; c0 < tn; c0 += 16) {
+      const int i = 128 * t + 32 * qw + lane;  // row of [Bbar; L], entry of h
+      for (int c0 = 16 * hc; c0 < tn; c0 += 32) {
         float v[16];
-        tmem_ld16((t ? d2b : d2a) + ((uint32_t)(32 * warp) << 16) + c0, v);
+        tmem_ld16((t ? d2b : d2a) + ((uint32_t)(32 * qw) << 16) + c0, v);
         if (i < n_k) {
 #pragma unroll
           for (int j = 0; j < 16; ++j)
@@ -3062,12 +3067,13 @@ __device__ __forceinline__ unsigned short bf16_bits(const uint4& v, int t) {
 }
 
 template <typename VT>
-__global__ void __launch_bounds__(128, 1) node_gt_tc(const __grid_constant__ IterArgs a, int tn, int nu, int mode) {
+__global__ void __launch_bounds__(kTcThreads, 1) node_gt_tc(const __grid_constant__ IterArgs a, int tn, int nu, int mode) {
   grid_dep_sync();
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   __shared__ int flag[2];
   if (early_exit(a, nu, mode, flag, false)) return;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int qw = warp & 3, hc = warp >> 2;  // tensor-memory lane quarter, column-chunk parity
   const int n_x = a.n_x, n_k = a.n_k, n_v = a.n_v, Kq = tc_kq(n_k), ld = row_stride<__nv_bfloat16>(n_v);
   const int sbo = Kq / 8 * kTcCore;
   unsigned char* At = smem_raw;                                    // Kt: 128 rows (n_v used), Kq columns
@@ -3173,11 +3179,11 @@ __global__ void __launch_bounds__(128, 1) node_gt_tc(const __grid_constant__ Ite
       break;
     }
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    // g: warp w holds rows 32w .. 32w + 31 of D (the entries of g), one column per node
-    const int j = 32 * warp + lane;
-    for (int c0 = 0; c0 < tn; c0 += 16) {
+    // g: warp w reads rows 32 (w mod 4) .. + 31 of D (the entries of g), one column per node
+    const int j = 32 * qw + lane;
+    for (int c0 = 16 * hc; c0 < tn; c0 += 32) {
       float v[16];
-      tmem_ld16(tmem + ((uint32_t)(32 * warp) << 16) + c0, v);
+      tmem_ld16(tmem + ((uint32_t)(32 * qw) << 16) + c0, v);
       if (j < n_v) {
 #pragma unroll
         for (int t = 0; t < 16; ++t)
@@ -3364,7 +3370,7 @@ int launch_t(const IterArgs& a, const LaunchCfg& c, int nu, int mode, cudaStream
     mark();
     if constexpr (std::is_same<MT, __nv_bfloat16>::value) {
       if (c.tc && (mode & MODE_DELTA)) {
-        launch_dep(node_mv_tc<VT>, c.grid_tc, 128, c.smem_tc, s, dep, a, c.tn, nu, mode);
+        launch_dep(node_mv_tc<VT>, c.grid_tc, kTcThreads, c.smem_tc, s, dep, a, c.tn, nu, mode);
       } else if (c.multi_dh) {
         launch_dep(node_mv_shared<VT, MT, true>, c.grid_multi, c.block, c.smem_mdh, s, dep, a, nu, mode);
       } else {
@@ -3383,7 +3389,7 @@ int launch_t(const IterArgs& a, const LaunchCfg& c, int nu, int mode, cudaStream
     bool gt_done = false;
     if constexpr (std::is_same<MT, __nv_bfloat16>::value) {
       if (c.tc && c.tc_gt && (mode & MODE_DELTA)) {
-        launch_dep(node_gt_tc<VT>, c.grid_tc, 128, c.smem_gt_tc, s, dep, a, c.tn, nu, mode);
+        launch_dep(node_gt_tc<VT>, c.grid_tc, kTcThreads, c.smem_gt_tc, s, dep, a, c.tn, nu, mode);
         gt_done = true;
       }
     }
@@ -3398,7 +3404,7 @@ int launch_t(const IterArgs& a, const LaunchCfg& c, int nu, int mode, cudaStream
     mark();
     if constexpr (std::is_same<MT, __nv_bfloat16>::value) {
       if (c.tc && (mode & MODE_DELTA)) {
-        launch_dep(node_mv_tc<VT>, c.grid_tc, 128, c.smem_tc, s, dep, a, c.tn, nu, mode);
+        launch_dep(node_mv_tc<VT>, c.grid_tc, kTcThreads, c.smem_tc, s, dep, a, c.tn, nu, mode);
       } else if (c.multi_dh) {
         launch_dep(node_mv_shared<VT, MT, true>, c.grid_multi, c.block, c.smem_mdh, s, dep, a, nu, mode);
       } else {
