@@ -1,5 +1,6 @@
 """Oracle pin on the probability weighting: splitting a subtree into two identical copies,
-each with half the probability, leaves the problem - and so its solution - unchanged.
+each with half the probability, leaves the problem - and so its solution - unchanged; and,
+taken to its end, a tree of identical scenarios is the certainty-equivalent chain.
 
 The SMPC cost is an expectation over the scenarios (Sec. III-D, eq. Sc-MPC): the stage
 costs and the safety penalty of a node are weighted by its probability p_n, and the
@@ -117,3 +118,29 @@ def test_split_subtree_pin_catches_planted_probability_mistakes(plant, name):
     P = _instance(name)
     R, R2, orig, _ = _solve_both(P, ITERS[name], plant)
     assert _gap(R, R2, orig) > 100 * BAR, plant
+
+
+@pytest.mark.parametrize("name", ["exact", "soft"])
+def test_identical_scenarios_give_the_certainty_equivalent_solution(name):
+    """Sec. III / Table 1: with one scenario the problem is certainty-equivalent MPC on a chain.
+    A tree whose nodes of a stage all carry the same forecast deviation is that chain with
+    each node split into identical copies (the probabilities of a stage still summing to
+    one), so every node's converged inputs and states are the chain's at its stage."""
+    P = _instance(name)
+    tree = P["tree"]
+    stage = np.asarray(tree["stage"])
+    N = int(stage.max()) + 1
+    chain = synth.make_tree([1], N)
+    eps_chain = P["eps"][[int(np.flatnonzero(stage == j)[0]) for j in range(N)]]
+    Pc = dict(P, tree=chain, eps=eps_chain)
+    Pt = dict(P, eps=eps_chain[stage])  # every node of stage j: the chain's deviation at j
+
+    def converged(Q):
+        T = oracle.Tree(Q["tree"]["parent"], Q["tree"]["prob"])
+        fac = oracle.factor(Q["net"], Q["cost"])
+        cu = oracle.cost_update(fac, Q["cost"], T, Q["alpha2"], Q["dhat"], Q["eps"], Q["q"])
+        return oracle.apg(fac, T, cu, Q["cost"], Q["p"], oracle.jacobi_steps(fac, T), ITERS[name])
+
+    Rc, Rt = converged(Pc), converged(Pt)
+    assert Rc.rho_rel[-1] < 1e-6 and Rt.rho_rel[-1] < 1e-6
+    assert _gap(Rc, Rt, stage) <= BAR
