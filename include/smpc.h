@@ -125,9 +125,10 @@ typedef struct smpc_factor_opts {
    * fastest.  Results agree to rounding. */
   int32_t schedule;
   /* SMPC_BF16 with shared_packs = 1: the Lambda and [Bbar; L] products of the delta
-   * iterations run on the tensor cores as GEMMs over tc_width nodes at a time (16, 32 or
-   * 64); 0 = time the three widths on this GPU when the factor is built and keep the
-   * fastest.  Ignored otherwise.  Results are the same for every width. */
+   * iterations (and, on the node-parallel schedule 2, their [Bbar; L]' products) run on the
+   * tensor cores as GEMMs over tc_width nodes at a time (16, 32 or 64), with the vectors
+   * rounded to bfloat16; 0 = time the three widths on this GPU when the factor is built and
+   * keep the fastest.  Ignored otherwise.  Results are the same for every width. */
   int32_t tc_width;
 } smpc_factor_opts;
 
