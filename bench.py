@@ -670,15 +670,49 @@ SERVE_WORKLOAD = ("64 closed-loop MPC sessions on 4 networks (n_x, n_u) in {(20,
                   "N in {12,18,24}, 10-500 scenarios (249,644 nodes in all); Poisson arrivals")
 
 
+def _session_prices(P, k):
+    """The time-varying prices alpha_2 of MPC step k of a session: the instance's own
+    prices shifted by k hours (one row per stage of the horizon)."""
+    from synth.problems import day_night_price
+    N = P["tree"]["horizon"]
+    base = P["alpha2"] / np.maximum(day_night_price(N, 0)[:, None], 1e-300)
+    return day_night_price(N, t0=k)[:, None] * base
+
+
 def _session_request(P, k, x, q):
     """MPC step k of a session: measured state x, previous input q, forecast and prices
     shifted by k hours from the instance's own start hour."""
     import synth
-    from synth.problems import day_night_price
     N = P["tree"]["horizon"]
     dhat = synth.demand_forecast(P["net"], N, t0=k)
-    base = P["alpha2"] / np.maximum(day_night_price(N, 0)[:, None], 1e-300)
-    return {"p": x, "q": q, "dhat": dhat, "alpha2": day_night_price(N, t0=k)[:, None] * base}
+    return {"p": x, "q": q, "dhat": dhat, "alpha2": _session_prices(P, k)}
+
+
+def closed_loop_kpis(u, x, alpha, u_before, x_s):
+    """The closed-loop key performance indicators of Sec. V over H_s steps: u (H_s x n_u)
+    the applied inputs, x (H_s x n_x) the states they led to, alpha (H_s x n_u) the prices
+    alpha_1 + alpha_2,k of each step, u_before the input applied before the first step (for
+    its Delta u), x_s the safety levels.
+      KPI_E   = (1/H_s) sum_k (alpha_1 + alpha_2,k)' |u_k|         (average economic cost)
+      KPI_dU  = (1/H_s) sum_k ||u_k - u_{k-1}||^2                  (smoothness of the inputs)
+      KPI_S   = sum_k ||[x_s - x_k]_+||_1                          (water below the safety levels)
+      KPI_R   = ||x_s||_1 / ((1/H_s) sum_k ||x_k||_1) x 100 %      (safety level against the mean storage)"""
+    u, x, alpha = (np.asarray(a, float) for a in (u, x, alpha))
+    H = u.shape[0]
+    du = np.diff(np.vstack([np.asarray(u_before, float)[None, :], u]), axis=0)
+    return {"KPI_E": float(np.sum(alpha * np.abs(u)) / H),
+            "KPI_dU": float(np.sum(du ** 2) / H),
+            "KPI_S": float(np.sum(np.maximum(np.asarray(x_s, float)[None, :] - x, 0.0))),
+            "KPI_R_pct": float(np.abs(x_s).sum() / (np.abs(x).sum(axis=1).mean()) * 100.0),
+            "steps": int(H)}
+
+
+def _record_step(s_, k, u0):
+    """Applies a session's step-k input to its plant and keeps the closed-loop trajectory
+    (input, resulting state, prices of the step) for the KPIs."""
+    P = s_["P"]
+    s_["x"] = _plant_step(P, s_["x"], u0, k, s_["rng"])
+    s_["traj"].append((u0.copy(), s_["x"].copy(), P["cost"]["alpha1"] + _session_prices(P, k)[0]))
 
 
 def _plant_step(P, x, u0, k, rng):
@@ -714,7 +748,7 @@ def _serve_window(smpc, server, sess, rate, seconds, drain, args, rng):
                 run_ms.append(r["run_ms"])
                 its.append(r["iterations"])
                 rho.append(r["rho_rel"])
-                s_["x"] = _plant_step(s_["P"], s_["x"], u0, k, s_["rng"])
+                _record_step(s_, k, u0)
                 s_["q"] = u0
 
     while True:
@@ -747,6 +781,27 @@ def _serve_window(smpc, server, sess, rate, seconds, drain, args, rng):
             "iterations_mean": float(np.mean(its)) if its else None}
 
 
+def serve_kpis(sess):
+    """Each session's closed-loop KPIs over the steps it completed (the requests are solved
+    in order per session), and their mean and range over the sessions."""
+    per = []
+    for s_ in sess:
+        if not s_["traj"]:
+            continue
+        u, x, a = (np.array([t[i] for t in s_["traj"]]) for i in range(3))
+        per.append(closed_loop_kpis(u, x, a, s_["q_start"], s_["P"]["cost"]["x_s"]))
+    if not per:
+        return None
+    out = {"sessions": len(per), "steps_per_session_mean": float(np.mean([p["steps"] for p in per])),
+           "definitions": "Sec. V: KPI_E average economic cost (alpha_1 + alpha_2,k)'|u_k|; KPI_dU average "
+                          "||u_k - u_(k-1)||^2; KPI_S total ||[x_s - x_k]_+||_1; KPI_R ||x_s||_1 over the mean "
+                          "||x_k||_1, in %; per session over its completed steps, then over the sessions"}
+    for key in ("KPI_E", "KPI_dU", "KPI_S", "KPI_R_pct"):
+        v = np.array([p[key] for p in per])
+        out[key] = {"mean": float(v.mean()), "min": float(v.min()), "max": float(v.max())}
+    return out
+
+
 def run_serve(args):
     """Closed-loop serving (Alg. 2 for 64 controllers): Poisson arrivals at a sweep of
     offered rates, each request a warm-started solve to rho_rel <= tol (no effective
@@ -768,7 +823,8 @@ def run_serve(args):
         prec = 1 if i % 2 == 0 else 2  # float32 and bfloat16 packs, mixed
         fac = smpc.smpc_factor(tree, P["net"], P["cost"], precision=prec, precondition=1, shared_packs=1)
         sess.append({"P": P, "tree": tree, "fac": fac, "prec": prec, "x": P["p"].copy(), "q": P["q"].copy(),
-                     "k": 0, "pending": [], "rng": np.random.default_rng(100 + i)})
+                     "k": 0, "pending": [], "rng": np.random.default_rng(100 + i), "traj": [],
+                     "q_start": P["q"].copy()})
     total_bytes = sum(smpc.smpc_factor_device_bytes(s_["fac"]) for s_ in sess)
     log("serve: factors ready,", total_bytes / 1e9, "GB")
     budget = int(args.serve_budget_gb * 1e9)
@@ -791,7 +847,7 @@ def run_serve(args):
                 r = smpc.smpc_poll(server, tk, u0_host=u0)
                 if r is not None:
                     s_["pending"].pop(0)
-                    s_["x"] = _plant_step(s_["P"], s_["x"], u0, k, s_["rng"])
+                    _record_step(s_, k, u0)
                     s_["q"] = u0
                     n_cold += 1
                     log("serve: cold step", n_cold, "of", len(sess), "session", sess.index(s_), "nodes",
@@ -822,6 +878,7 @@ def run_serve(args):
                    "max_iters": args.serve_max_iters, "tol": args.tol, "warm_start": "each session's previous step",
                    "launch": "plain launches, 64-iteration chunks between stop checks", "rates": args.serve_rates,
                    "window_s": args.serve_seconds}}
+    result["closed_loop_kpis"] = serve_kpis(sess)
     # baseline: the plain per-request FP64 solve (one pack per node), one at a time, on a
     # sample of sessions continuing their closed loops (warm-started steps, same tol)
     base, base_it = [], []
